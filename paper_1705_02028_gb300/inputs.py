@@ -1,0 +1,257 @@
+"""Seeded synthetic inputs: periodic triangulations and initial states.
+
+This module only builds inputs (meshes and conserved states).  It contains
+none of the residual-distribution arithmetic, and both the CUDA library and the
+CPU oracle are fed from it, so that the two sides see bit-identical inputs.
+
+Meshes
+------
+``periodic_grid`` builds the structured triangulation of Sec. 2.1 (Eq. eqCart):
+vertex (i, j) at (i Lx/Nx, j Ly/Ny), each cell a=(i,j), b=(i+1,j), c=(i+1,j+1),
+d=(i,j+1) split along the diagonal a-c into the counter-clockwise triangles
+(a,b,c) and (a,c,d).  Indices wrap periodically; a corner reached across the
+periodic boundary carries an image shift (in periods) so that every triangle
+has its true geometry (periodic boundaries "handled by the mesh", Sec. 3.5).
+Every vertex has valence 6.  ``relabel_seed`` applies a seeded random
+permutation to vertex and triangle labels, standing in for the unstructured
+Delaunay meshes of Sec. 4.1 (whose locality has to be restored by reordering).
+
+States
+------
+W is returned component-major, shape (4, nv): rho, rho u, rho v, e
+(e = rho |v|^2 / 2 + p / (gamma - 1), Sec. 3).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+GAMMA = 1.4
+
+
+@dataclass
+class Mesh:
+    xy: np.ndarray        # (nv, 2) float64
+    tri: np.ndarray       # (nt, 3) int32, counter-clockwise
+    shift: np.ndarray     # (nt, 3, 2) int8, periodic image of each corner
+    Lx: float
+    Ly: float
+    orig_vertex: np.ndarray  # (nv,) int64: structured id j*Nx+i of each vertex
+    Nx: int = 0
+    Ny: int = 0
+
+    @property
+    def nv(self) -> int:
+        return int(self.xy.shape[0])
+
+    @property
+    def nt(self) -> int:
+        return int(self.tri.shape[0])
+
+
+def periodic_grid(Nx: int, Ny: int | None = None, Lx: float = 1.0, Ly: float | None = None,
+                  relabel_seed: int | None = None) -> Mesh:
+    """Regular periodic triangulation with Nx*Ny vertices and 2*Nx*Ny triangles."""
+    if Ny is None:
+        Ny = Nx
+    if Ly is None:
+        Ly = Lx * Ny / Nx
+    if Nx < 2 or Ny < 2:
+        raise ValueError("periodic_grid needs at least 2 vertices per side")
+    i = np.arange(Nx, dtype=np.int64)
+    j = np.arange(Ny, dtype=np.int64)
+    jj, ii = np.meshgrid(j, i, indexing="ij")           # (Ny, Nx)
+    vid = (jj * Nx + ii).ravel()
+    xy = np.stack([ii.ravel() * (Lx / Nx), jj.ravel() * (Ly / Ny)], axis=1).astype(np.float64)
+
+    ip = (ii + 1) % Nx
+    jp = (jj + 1) % Ny
+    sx = (ii + 1 == Nx).astype(np.int8)
+    sy = (jj + 1 == Ny).astype(np.int8)
+    a = jj * Nx + ii
+    b = jj * Nx + ip
+    c = jp * Nx + ip
+    d = jp * Nx + ii
+    z = np.zeros_like(sx)
+    t1 = np.stack([a, b, c], axis=-1).reshape(-1, 3)
+    t2 = np.stack([a, c, d], axis=-1).reshape(-1, 3)
+    s1 = np.stack([np.stack([z, z], -1), np.stack([sx, z], -1), np.stack([sx, sy], -1)], axis=-2).reshape(-1, 3, 2)
+    s2 = np.stack([np.stack([z, z], -1), np.stack([sx, sy], -1), np.stack([z, sy], -1)], axis=-2).reshape(-1, 3, 2)
+    tri = np.empty((2 * Nx * Ny, 3), dtype=np.int64)
+    shift = np.empty((2 * Nx * Ny, 3, 2), dtype=np.int8)
+    tri[0::2], tri[1::2] = t1, t2
+    shift[0::2], shift[1::2] = s1, s2
+    orig = vid.copy()
+
+    if relabel_seed is not None:
+        rng = np.random.default_rng(relabel_seed)
+        vperm = rng.permutation(Nx * Ny)          # new label of old vertex
+        inv = np.empty_like(vperm)
+        inv[vperm] = np.arange(Nx * Ny)
+        xy = xy[inv]
+        orig = orig[inv]
+        tri = vperm[tri]
+        tperm = rng.permutation(tri.shape[0])
+        tri = tri[tperm]
+        shift = shift[tperm]
+        # rotate the corner order of each triangle (keeps orientation)
+        rot = rng.integers(0, 3, size=tri.shape[0])
+        idx = (np.arange(3)[None, :] + rot[:, None]) % 3
+        tri = np.take_along_axis(tri, idx, axis=1)
+        shift = np.take_along_axis(shift, idx[:, :, None], axis=1)
+    return Mesh(xy=np.ascontiguousarray(xy), tri=np.ascontiguousarray(tri.astype(np.int32)),
+                shift=np.ascontiguousarray(shift), Lx=float(Lx), Ly=float(Ly),
+                orig_vertex=orig, Nx=Nx, Ny=Ny)
+
+
+# ---------------------------------------------------------------------------
+# conserved state from primitives
+# ---------------------------------------------------------------------------
+def conserved(rho, u, v, p, gamma: float = GAMMA) -> np.ndarray:
+    rho = np.asarray(rho, dtype=np.float64)
+    u = np.broadcast_to(np.asarray(u, dtype=np.float64), rho.shape)
+    v = np.broadcast_to(np.asarray(v, dtype=np.float64), rho.shape)
+    p = np.broadcast_to(np.asarray(p, dtype=np.float64), rho.shape)
+    e = 0.5 * rho * (u * u + v * v) + p / (gamma - 1.0)
+    return np.ascontiguousarray(np.stack([rho, rho * u, rho * v, e]))
+
+
+def primitives(W: np.ndarray, gamma: float = GAMMA):
+    rho = W[0]
+    u = W[1] / rho
+    v = W[2] / rho
+    p = (gamma - 1.0) * (W[3] - 0.5 * rho * (u * u + v * v))
+    return rho, u, v, p
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """SplitMix64 output function (Steele, Lea & Flood 2014) on uint64 counters."""
+    z = (np.asarray(x, dtype=np.uint64) + np.uint64(0x9E3779B97F4A7C15))
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def uniform01(seed: int, counters: np.ndarray) -> np.ndarray:
+    """U[0,1) from the top 53 bits of SplitMix64(seed xor counter)."""
+    z = splitmix64(np.uint64(seed) ^ np.asarray(counters, dtype=np.uint64))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+# ---------------------------------------------------------------------------
+# initial states
+# ---------------------------------------------------------------------------
+def uniform_state(mesh: Mesh, rho=1.0, u=0.0, v=0.0, p=1.0, gamma=GAMMA) -> np.ndarray:
+    one = np.ones(mesh.nv)
+    return conserved(rho * one, u * one, v * one, p * one, gamma)
+
+
+def vortex_primitives(x, y, t=0.0, beta=5.0, scale=10.0, u0=1.0, v0=1.0, Lx=1.0, Ly=1.0,
+                      gamma=GAMMA, xc=0.5, yc=0.5):
+    """Isentropic vortex of Sec. 5.2.1 translated by (u0, v0) t on a periodic box.
+
+    The paper's setup (box [0,10]^2, beta=5, centre (5,5), p_inf=rho_inf=K=1) is
+    mapped onto the box [0,Lx)x[0,Ly) by lengths/scale; velocities are unchanged.
+    The nearest periodic image of the centre is used.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    cx = xc + u0 * t
+    cy = yc + v0 * t
+    dx = (x - cx) - Lx * np.round((x - cx) / Lx)
+    dy = (y - cy) - Ly * np.round((y - cy) / Ly)
+    dx = dx * scale
+    dy = dy * scale
+    r2 = dx * dx + dy * dy
+    omega = beta * np.exp((1.0 - r2) / 2.0) / (2.0 * np.pi)
+    T = 1.0 - (gamma - 1.0) / gamma * beta ** 2 / (8.0 * np.pi ** 2) * np.exp(1.0 - r2)
+    rho = T ** (1.0 / (gamma - 1.0))
+    p = rho ** gamma
+    u = u0 - omega * dy
+    v = v0 + omega * dx
+    return rho, u, v, p
+
+
+def vortex_state(mesh: Mesh, t=0.0, beta=5.0, u0=1.0, v0=1.0, gamma=GAMMA, scale=None) -> np.ndarray:
+    if scale is None:
+        scale = 10.0 / mesh.Lx
+    rho, u, v, p = vortex_primitives(mesh.xy[:, 0], mesh.xy[:, 1], t=t, beta=beta, scale=scale,
+                                     u0=u0, v0=v0, Lx=mesh.Lx, Ly=mesh.Ly, gamma=gamma,
+                                     xc=0.5 * mesh.Lx, yc=0.5 * mesh.Ly)
+    return conserved(rho, u, v, p, gamma)
+
+
+def sod_like_state(mesh: Mesh, amp=0.01, gamma=GAMMA) -> np.ndarray:
+    """Left (rho=1, p=1) where x < 0.5 + amp sin(2 pi y), right (0.125, 0.1) elsewhere; at rest."""
+    x, y = mesh.xy[:, 0], mesh.xy[:, 1]
+    left = x < 0.5 + amp * np.sin(2.0 * np.pi * y)
+    rho = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 0.1)
+    return conserved(rho, 0.0, 0.0, p, gamma)
+
+
+def sod_strip_state(mesh: Mesh, gamma=GAMMA) -> np.ndarray:
+    """Sod tube on a periodic strip x in [0, 2): left state for x < 0.5 or x >= 1.5."""
+    x = mesh.xy[:, 0]
+    left = (x < 0.5) | (x >= 1.5)
+    rho = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 0.1)
+    return conserved(rho, 0.0, 0.0, p, gamma)
+
+
+def khi_state(mesh: Mesh, seed=1, amp=0.01, gamma=GAMMA) -> np.ndarray:
+    """Shear layer: rho=2, u=+0.5 for |y-0.5|<0.25; rho=1, u=-0.5 elsewhere; p=2.5;
+    v = amp (2U-1), U from SplitMix64(seed xor structured vertex id)."""
+    y = mesh.xy[:, 1]
+    inner = np.abs(y - 0.5) < 0.25
+    rho = np.where(inner, 2.0, 1.0)
+    u = np.where(inner, 0.5, -0.5)
+    U = uniform01(seed, mesh.orig_vertex)
+    v = amp * (2.0 * U - 1.0)
+    return conserved(rho, u, v, 2.5, gamma)
+
+
+def smooth_density_state(mesh: Mesh, seed=3, amp=0.05, n_modes=16, kmax=4, gamma=GAMMA) -> np.ndarray:
+    """rho = 1 + amp f / max|f|, f a sum of n_modes seeded Fourier modes with |k| <= kmax;
+    p = 1, u = v = 1."""
+    rng = np.random.default_rng(seed)
+    ks = [(kx, ky) for kx in range(-kmax, kmax + 1) for ky in range(-kmax, kmax + 1)
+          if 0 < kx * kx + ky * ky <= kmax * kmax]
+    pick = rng.choice(len(ks), size=n_modes, replace=False)
+    amps = rng.normal(size=n_modes)
+    phases = rng.uniform(0.0, 2.0 * np.pi, size=n_modes)
+    x, y = mesh.xy[:, 0] / mesh.Lx, mesh.xy[:, 1] / mesh.Ly
+    f = np.zeros(mesh.nv)
+    for m, (a, ph) in enumerate(zip(amps, phases)):
+        kx, ky = ks[pick[m]]
+        f += a * np.cos(2.0 * np.pi * (kx * x + ky * y) + ph)
+    rho = 1.0 + amp * f / np.max(np.abs(f))
+    return conserved(rho, 1.0, 1.0, 1.0, gamma)
+
+
+def sound_wave_state(mesh: Mesh, amp=1e-4, t=0.0, gamma=GAMMA) -> np.ndarray:
+    """Right-moving linear sound wave in rho=1, v=0, c=1 (Sec. 5.1.1), wavelength Lx."""
+    x = mesh.xy[:, 0]
+    c = 1.0
+    p0 = 1.0 / gamma
+    d = amp * np.sin(2.0 * np.pi * (x - c * t) / mesh.Lx)
+    return conserved(1.0 + d, c * d, 0.0, p0 + c * c * d, gamma)
+
+
+def batch_workload(n_mesh=64, seed=2, smin=128, smax=1024, relabel_seed=None):
+    """64 periodic meshes with sides ~ U{smin..smax}; each gets a vortex or shear state (50/50)."""
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(smin, smax + 1, size=n_mesh)
+    kinds = rng.integers(0, 2, size=n_mesh)
+    out = []
+    for m in range(n_mesh):
+        mesh = periodic_grid(int(sides[m]), relabel_seed=relabel_seed)
+        if kinds[m] == 0:
+            W = vortex_state(mesh)
+        else:
+            W = khi_state(mesh, seed=seed * 1000 + m)
+        out.append((mesh, W, "vortex" if kinds[m] == 0 else "shear"))
+    return out
