@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the residual-distribution Euler step on GB300.
+
+Default workload: the 4096 x 4096-vertex periodic mesh (33,554,432 triangles)
+with the Kelvin-Helmholtz shear-layer state, blended B scheme with the
+two-stage update (B2), CFL 0.8, FP64.  One "step" is one full time step of
+every triangle (both stages and the CFL reduction); the metric is
+triangle-updates per second.  Inputs are synthetic (seeded) and larger than
+L2 (537 MB of FP64 vertex state), so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain FP64 reference of the
+method, on the host cores) on a bounded sample of the same workload.
+Under torchrun every rank advances its own replica (weak scaling, no
+data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "triangle-updates/s FP64/FP32 & % HBM roofline; batched & adjoint vs plain step"
+UNIT = "triangle-updates/s"
+WORKLOADS = {
+    # name: (side, state, scheme)
+    "khi4096_B2": (4096, "khi", "B2"),
+    "khi2048_B2": (2048, "khi", "B2"),
+    "sod1024_B2": (1024, "sod", "B2"),
+    "vortex64_N1": (64, "vortex", "N1"),
+}
+# algorithmic HBM bytes of one triangle-update (whole step) for the two-stage
+# scheme: W^n, xy, V read and R1, sigma written in the first pass; W^n, R1, V,
+# xy read and R2 written in the second; W^n, R1, R2, V read and W^{n+1}
+# written in the last: 44 words per vertex and 2 x 12 B of connectivity per
+# triangle, N_v = N_t / 2 -> 22 s + 24 bytes (s = word size).
+ALG_BYTES_STEP = {("B2", 8): 200.0, ("B2", 4): 112.0, ("N1", 8): 112.0, ("N1", 4): 62.0}
+
+
+def kernel_alg_bytes(kernel: str, scheme: str, s: int) -> float:
+    """Algorithmic bytes per triangle of one kernel launch: every input read once,
+    every output written once; vertex arrays count N_v / N_t = 1/2 per triangle."""
+    geo = 11 * s + 12                     # 3 unit normals + 3 half lengths + area + l_max, 3 corner ids
+    if kernel == "tri_stage1":
+        rec = 16 * s if scheme != "N1" else 0
+        return geo + 0.5 * 5 * s + 12 * s + rec + s      # Z, |v|+c in; shares, rec, cfl out
+    if kernel == "tri_stage2":
+        return geo + 0.5 * 12 * s + 16 * s + 12 * s      # Z*, W^n, W* in; rec in; shares out
+    raise KeyError(kernel)
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="khi4096_B2")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 companion measurement")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def build_inputs(workload):
+    from paper_1705_02028_gb300 import inputs
+    side, state, scheme = WORKLOADS[workload]
+    mesh = inputs.periodic_grid(side)
+    W0 = {"khi": inputs.khi_state, "sod": inputs.sod_like_state, "vortex": inputs.vortex_state}[state](mesh)
+    return mesh, W0, scheme
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop_and_keep(self):
+        self.result = self.stop()
+
+    result = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        import statistics
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("rd_kernels.cuh", "rd_api.cu"):
+        with open(os.path.join(ROOT, "paper_1705_02028_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload, precision, kernel, nt):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, scaled to nt
+    triangles; None when missing or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    e = d.get(f"{workload}:{precision}:{kernel}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return float(e["dram_bytes_per_triangle"]) * nt
+
+
+def run_state_timing(binding, mesh_dev, W0, scheme, precision, steps, warmup, ws, clocks=None):
+    import torch
+    s = binding.State(mesh_dev, W0, scheme=scheme, precision=precision)
+    s.run(warmup)
+    st = mesh_dev.stream
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.start()
+    barrier(ws)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    per_kernel, launches = s.profile(steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier(ws)
+    if clocks is not None:
+        clocks.stop_and_keep()
+    ms_total = e0.elapsed_time(e1)
+    return s, ms_total, per_kernel, launches
+
+
+def ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1705_02028_gb300 import binding
+
+    torch.cuda.set_device(local)
+    mesh, W0, scheme = build_inputs(args.workload)
+    nt, nv = mesh.nt, mesh.nv
+    m = binding.Mesh(mesh, reorder="morton")
+    s_bytes = 8 if args.precision == "fp64" else 4
+
+    clocks = ClockSampler(local)
+    s, ms_total, per_kernel, launches = run_state_timing(binding, m, W0, scheme, args.precision,
+                                                         args.steps, args.warmup, ws, clocks)
+    clk = clocks.result
+    ms_step = max_over_ranks(ms_total / args.steps, ws)
+    value = ws * nt / (ms_step * 1e-3)
+
+    # graph-replayed product path (rd_run), same state, for reference
+    st = m.stream
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(st)
+    s.run(args.steps)
+    g1.record(st)
+    torch.cuda.synchronize()
+    ms_graph = g0.elapsed_time(g1) / args.steps
+
+    # roofline of the dominant kernel
+    dom = max(per_kernel, key=per_kernel.get)
+    dom_ms = per_kernel[dom]
+    stage = 1 if dom == "tri_stage1" else 2
+    if args.precision == "fp64" and dom in ("tri_stage1", "tri_stage2"):
+        fl = binding.count_flops(scheme, stage)["total"]
+        peak = binding.probe_fma_peak("fp64")
+        achieved = fl * nt / (dom_ms * 1e-3)
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / peak, "flops_per_triangle": fl,
+                "peak_source": "measured FP64 FMA probe (rd_probe_fma_peak), same GPU, same run",
+                "traffic": ncu_traffic(args.workload, args.precision, dom, nt)}
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        bpt = kernel_alg_bytes(dom, scheme, s_bytes) if dom.startswith("tri_") else None
+        achieved = bpt * nt / (dom_ms * 1e-3) / 1e9 if bpt else None
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm if achieved else None, "bytes_per_triangle": bpt,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
+                "traffic": ncu_traffic(args.workload, args.precision, dom, nt)}
+    step_bytes = ALG_BYTES_STEP.get((scheme, s_bytes))
+    hbm_peak = 6765.0
+    try:
+        hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        pass
+    step_hbm = {"alg_bytes_per_triangle": step_bytes,
+                "achieved_gbs": step_bytes * nt / (ms_step * 1e-3) / 1e9 if step_bytes else None,
+                "frac_of_measured_hbm": (step_bytes * nt / (ms_step * 1e-3) / 1e9) / hbm_peak if step_bytes else None}
+
+    # end to end through the public API with host buffers (pinned), every step
+    Wh = torch.empty((4, nv), dtype=torch.float64, pin_memory=True).numpy()
+    Wo = torch.empty((4, nv), dtype=torch.float64, pin_memory=True).numpy()
+    Wh[:] = s.get()
+    e2e_steps = max(2, min(args.steps, 5))
+    s.set(Wh)
+    s.step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set(Wh)
+        s.step()
+        s.get(out=Wo)
+    t_e2e = max_over_ranks((time.perf_counter() - t0) / e2e_steps, ws)
+    e2e = {"value": ws * nt / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(Wh.nbytes),
+           "d2h_bytes_per_step": int(Wo.nbytes), "ms_per_step": t_e2e * 1e3,
+           "path": "rd_state_set (pinned host W) + rd_step + rd_get_state (pinned host W)"}
+    s.close()
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+            "data": "synthetic (seeded KHI shear layer / generated periodic triangulation)",
+            "config": {"workload": args.workload, "triangles": nt, "vertices": nv, "scheme": scheme,
+                       "cfl": 0.8, "precision": args.precision, "reorder": "morton",
+                       "l2": "inputs larger than L2 (%.0f MB vertex state)" % (4 * nv * s_bytes / 1e6),
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "ms_per_step_graph": ms_graph, "per_kernel_ms": per_kernel,
+            "roofline": roof, "step_hbm": step_hbm, "e2e": e2e,
+            "gpu_launches": launches * args.steps + 1,
+            "clocks": clk}
+
+    # FP32 companion measurement on the same mesh
+    if not args.no_fp32 and args.precision == "fp64":
+        s32, ms32, pk32, _ = run_state_timing(binding, m, W0, scheme, "fp32", max(args.steps, 20),
+                                              args.warmup, ws)
+        ms32 = max_over_ranks(ms32 / max(args.steps, 20), ws)
+        d32 = max(pk32, key=pk32.get)
+        hbm = hbm_peak
+        b32 = kernel_alg_bytes(d32, scheme, 4) if d32.startswith("tri_") else None
+        a32 = b32 * nt / (pk32[d32] * 1e-3) / 1e9 if b32 else None
+        sb32 = ALG_BYTES_STEP.get((scheme, 4))
+        line["fp32"] = {"value": ws * nt / (ms32 * 1e-3), "ms_per_step": ms32, "per_kernel_ms": pk32,
+                        "roofline": {"bound": "hbm", "kernel": d32, "achieved": a32, "peak": hbm, "unit": "GB/s",
+                                     "frac": a32 / hbm if a32 else None, "bytes_per_triangle": b32,
+                                     "traffic": ncu_traffic(args.workload, "fp32", d32, nt)},
+                        "step_hbm_frac_of_measured": sb32 * nt / (ms32 * 1e-3) / 1e9 / hbm}
+        s32.close()
+    m.close()
+
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    return line
+
+
+def oracle_sample_rate(scheme, steps, nthreads):
+    """Oracle triangle-updates/s on the sample: the KHI state on a 1024^2 periodic mesh
+    (1/16 of the 4096^2 workload's triangles), `steps` full steps."""
+    import oracle
+    from paper_1705_02028_gb300 import inputs
+    mesh = inputs.periodic_grid(1024)
+    W0 = inputs.khi_state(mesh)
+    t0 = time.perf_counter()
+    oracle.run(mesh, W0, scheme, nsteps=steps, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return mesh.nt * steps / dt, dt, mesh.nt
+
+
+def cpu_baseline(args):
+    import oracle
+    scheme = WORKLOADS[args.workload][2]
+    nth = os.cpu_count() or 1
+    oracle.build()
+    rate, secs, nts = oracle_sample_rate(scheme, 2, nth)
+    if secs < 8.0:  # aim for ~10-30 s of CPU work
+        extra = max(1, int(10.0 / max(secs / 2, 1e-3)))
+        rate, secs, nts = oracle_sample_rate(scheme, min(extra, 40), nth)
+    return {"value": rate, "unit": UNIT, "cores": nth, "kind": "oracle", "seconds": secs,
+            "sample": f"{scheme} steps of the KHI state on a 1024x1024 periodic mesh ({nts} triangles, "
+                      f"1/16 of the workload), FP64 C++ oracle, OpenMP over {nth} host threads"}
+
+
+def reference(args, ws, rank):
+    import oracle
+    if rank != 0:
+        return None
+    scheme = WORKLOADS[args.workload][2]
+    nth = os.cpu_count() or 1
+    oracle.build()
+    from paper_1705_02028_gb300 import inputs
+    mesh = inputs.periodic_grid(1024)
+    W = inputs.khi_state(mesh)
+    for _ in range(args.warmup):
+        W, _ = oracle.run(mesh, W, scheme, nsteps=1, nthreads=nth)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        W, _ = oracle.run(mesh, W, scheme, nsteps=1, nthreads=nth)
+    secs = time.perf_counter() - t0
+    ms_step = secs / args.steps * 1e3
+    value = mesh.nt / (ms_step * 1e-3)
+    sample = (f"each step: one {scheme} step of the KHI state on a 1024x1024 periodic mesh "
+              f"({mesh.nt} triangles, 1/16 of the 4096^2 workload), FP64 C++ oracle on {nth} host threads")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "triangles_per_sample_step": mesh.nt, "scheme": scheme},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nth, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        line = reference(args, ws, rank)
+    else:
+        line = ours(args, ws, rank, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

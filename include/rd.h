@@ -1,0 +1,182 @@
+/*
+ * rd.h -- C ABI of the GB300 residual-distribution Euler solver.
+ *
+ * The library advances the two-dimensional Euler equations of an ideal gas
+ * (Paardekooper 2017, Sec. 3) on a triangular mesh with the multidimensional
+ * upwind residual-distribution schemes of Sec. 3.3 (N, LDA and the blended B
+ * scheme) and either the forward-Euler update of Eq. (eqUpdate) or the
+ * explicit two-stage scheme of Sec. 3.4 (Eqs. eqRK1, eqRK2).
+ *
+ * Conventions (every function):
+ *   - Return value: RD_OK (0) or one of the RD_E* codes below; rd_strerror()
+ *     gives a message.  No C++ exception crosses this boundary.
+ *   - Host arrays passed in are owned by the caller and only read (or, for
+ *     *_out arguments, written) during the call.
+ *   - The library owns every device buffer and every opaque handle; device
+ *     memory comes from the allocator installed with rd_set_allocator()
+ *     (default: cudaMalloc/cudaFree) and is released by the *_destroy calls.
+ *   - All device work of a mesh and of the states / batches built on it is
+ *     ordered on the CUDA stream given to rd_mesh_create().
+ *   - Conserved state arrays are component-major ("SoA"): W[k * n_vertex + i]
+ *     for component k in (rho, rho u, rho v, e) and vertex i, in the caller's
+ *     vertex order.  e = rho |v|^2 / 2 + p / (gamma - 1)  (Sec. 3).
+ */
+#ifndef RD_H
+#define RD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define RD_OK 0
+#define RD_EINVAL 1        /* bad argument, index, orientation or zero area   */
+#define RD_ENOMEM 2        /* device or host allocation failed                */
+#define RD_ECUDA 3         /* a CUDA runtime call failed                      */
+#define RD_ENONPHYSICAL 4  /* rho<=0, p<=0, Roe c^2<=0, singular N^ or NaN;
+                              the state stays at the last good step           */
+#define RD_ETIMEOUT 5      /* a bounded device-side wait expired              */
+#define RD_ENOTSUP 6       /* option not supported by this build              */
+
+/* ---- schemes (Sec. 3.3, Sec. 3.4; labels as in the paper's figures) ------ */
+#define RD_N1 0   /* N scheme, forward Euler (first order in space and time)    */
+#define RD_B2 1   /* blended B scheme, two-stage update, m^LDA, global lumping */
+#define RD_LDA2 2 /* LDA scheme, two-stage update                               */
+
+/* ---- arithmetic precision of the device path --------------------------- */
+#define RD_FP64 0
+#define RD_FP32 1
+
+/* ---- vertex / triangle reordering applied inside the mesh store -------- */
+#define RD_ORDER_NONE 0
+#define RD_ORDER_MORTON 1 /* Morton (Z-order) of vertex coordinates (Sec. 4.1.4) */
+#define RD_ORDER_RCM 2    /* reverse Cuthill-McKee of the vertex graph           */
+
+typedef struct rd_mesh rd_mesh;
+typedef struct rd_state rd_state;
+typedef struct rd_batch rd_batch;
+
+/* Scheme parameters.
+ *   scheme    RD_N1 | RD_B2 | RD_LDA2
+ *   precision RD_FP64 | RD_FP32
+ *   cfl       Courant number multiplying the stability bound of Sec. 3.2:
+ *             dt = cfl * min_i 2 V_i / sum_{T containing i} l_max^T lambda_max^T
+ *   gamma     ratio of specific heats (Sec. 3)
+ *   eps_fix   |lambda| is replaced below delta = eps_fix * c * |n_i| / 2 by
+ *             (lambda^2 + delta^2) / (2 delta) so that N^ = (sum_j K_j^-)^-1
+ *             (Sec. 3.3.1) exists at stagnation; 0 disables it.             */
+typedef struct {
+  int32_t scheme;
+  int32_t precision;
+  double cfl;
+  double gamma;
+  double eps_fix;
+} rd_params;
+
+/* Device allocator hook: alloc(bytes, cuda_stream, ctx) returns a device
+ * pointer (NULL on failure); free(ptr, ctx) releases it.  Installed
+ * process-wide; affects buffers allocated after the call.  Passing NULL for
+ * both restores cudaMalloc/cudaFree. */
+typedef void *(*rd_alloc_fn)(size_t bytes, void *cuda_stream, void *ctx);
+typedef void (*rd_free_fn)(void *ptr, void *ctx);
+int rd_set_allocator(rd_alloc_fn alloc, rd_free_fn free_fn, void *ctx);
+
+const char *rd_strerror(int status);
+int rd_version(void);
+
+/* ---- mesh store -----------------------------------------------------------
+ * rd_mesh_create: validate a triangulation, compute its geometry, reorder it
+ * and upload it.
+ *   n_vertex, xy      vertex coordinates, xy[2*i], xy[2*i+1] (host)
+ *   n_tri, tri        corners of each triangle, tri[3*t + c], counter-clockwise
+ *                     (Sec. 4.1.2 "triangleVertices")
+ *   image_shift       NULL, or per corner the periodic image (dx, dy) in
+ *                     {-1,0,1} periods: the corner sits at
+ *                     xy[v] + (dx*Lx, dy*Ly).  Periodic boundaries are
+ *                     "handled by the mesh" (Sec. 3.5).
+ *   Lx, Ly            periods used with image_shift
+ *   reorder           RD_ORDER_NONE | RD_ORDER_MORTON | RD_ORDER_RCM
+ *   cuda_stream       cudaStream_t for all device work of this mesh (NULL:
+ *                     the library creates a non-blocking stream)
+ * Geometry per triangle: inward normals n_i of the edge opposite corner i
+ * with |n_i| = edge length, area |T|, longest edge l_max; nodal volume
+ * V_i = sum |T|/3 (Sec. 3.2).  A vertex -> (triangle, corner) CSR replaces the
+ * atomic accumulation of Sec. 4.2.1 by a deterministic gather.
+ * Errors: RD_EINVAL for an index out of range, a shift outside {-1,0,1}, a
+ * clockwise or zero-area triangle, or a vertex in no triangle.             */
+int rd_mesh_create(int32_t n_vertex, const double *xy, int32_t n_tri, const int32_t *tri,
+                   const int8_t *image_shift, double Lx, double Ly, int32_t reorder,
+                   void *cuda_stream, rd_mesh **out);
+void rd_mesh_destroy(rd_mesh *m);
+/* Internal order chosen by the reorder: vertex_perm[new] = caller vertex,
+ * tri_perm[new] = caller triangle (either pointer may be NULL). */
+int rd_mesh_permutation(const rd_mesh *m, int32_t *vertex_perm, int32_t *tri_perm);
+int rd_mesh_sizes(const rd_mesh *m, int32_t *n_vertex, int32_t *n_tri);
+
+/* ---- solver state ---------------------------------------------------------
+ * rd_state_init: allocate the device state of one mesh and upload W (host,
+ * component-major, caller order).  Errors: RD_EINVAL (bad params),
+ * RD_ENONPHYSICAL (rho<=0 or p<=0 or non-finite in W), RD_ENOMEM, RD_ECUDA. */
+int rd_state_init(rd_mesh *m, const double *W, const rd_params *p, rd_state **out);
+/* Replace the state by W (host); time and step counters are kept. */
+int rd_state_set(rd_state *s, const double *W);
+/* One full time step (both stages for RD_B2 / RD_LDA2).  dt_out (nullable):
+ * if non-NULL the call synchronises and returns the step's dt. */
+int rd_step(rd_state *s, double *dt_out);
+/* n_steps steps, replayed from a captured CUDA graph, dt and the stop test
+ * kept on the device.  t_end > 0 clips the last dt so that t reaches t_end
+ * exactly and stops there.  steps_done (nullable) receives the number of
+ * steps completed; the call synchronises once at the end. */
+int rd_run(rd_state *s, int32_t n_steps, double t_end, int32_t *steps_done);
+/* Device -> host copy of the current state in caller order. */
+int rd_get_state(const rd_state *s, double *W_out);
+/* sum_i V_i W_i per component, accumulated in double in a fixed order. */
+int rd_conserved_totals(const rd_state *s, double out[4]);
+int rd_get_time(const rd_state *s, double *t, int64_t *steps);
+/* dt of the last completed step. */
+int rd_get_dt(const rd_state *s, double *dt);
+void rd_state_destroy(rd_state *s);
+
+/* ---- per-triangle residuals (inspection / parity) ---------------------------
+ * Stage-1 shares of every triangle at the current state (Sec. 3.3):
+ * out[(t*3 + c)*4 + k] for caller triangle t, corner c, component k.
+ * which = 0: phi^N_i, 1: phi^LDA_i, 2: phi^B_i.  Also returns, if non-NULL,
+ * cfl_term[t] = l_max^T lambda_max^T (Sec. 3.2). */
+int rd_state_triangle_shares(rd_state *s, int32_t which, double *out, double *cfl_term);
+
+/* ---- measurement ------------------------------------------------------------
+ * rd_state_profile: n_steps steps with CUDA events recorded on the mesh stream
+ * around every kernel; ms_per_launch[6] receives the mean duration of
+ * (stage-1 triangle, dt gather, stage-1 update, stage-2 triangle, final
+ * update, commit) per step (zeros for kernels a scheme does not launch);
+ * launches_per_step (nullable) the number of kernels one step launches.
+ * The steps are real steps: the state advances. */
+int rd_state_profile(rd_state *s, int32_t n_steps, double *ms_per_launch, int32_t *launches_per_step);
+/* Floating-point operations of one triangle in the stage-1 (stage=1) or
+ * stage-2 (stage=2) triangle kernel of a scheme, counted by running the
+ * kernels' own per-triangle code on a counting scalar type (host only):
+ * out = {add/sub, mul, div, sqrt}.  An FMA counts as one add and one mul. */
+int rd_count_flops(int32_t scheme, int32_t stage, double out[4]);
+/* FMA throughput of the current device (flop/s, 2 per FMA) measured with a
+ * dependent-chain-free FMA kernel; precision RD_FP64 or RD_FP32. */
+int rd_probe_fma_peak(int32_t precision, double *flops_per_s);
+
+/* ---- batched form: many independent meshes, one graph launch -------------
+ * rd_batch_create: n_mesh meshes (all on the same stream) with their own
+ * initial states W0[m] (host, component-major, caller order of mesh m).
+ * Each mesh keeps its own dt.  Only RD_FP64/RD_FP32 with RD_B2/RD_N1/RD_LDA2. */
+int rd_batch_create(int32_t n_mesh, rd_mesh *const *meshes, const double *const *W0,
+                    const rd_params *p, rd_batch **out);
+/* n_steps steps of every mesh as one CUDA-graph launch. */
+int rd_batch_run(rd_batch *b, int32_t n_steps);
+int rd_batch_get_state(const rd_batch *b, int32_t mesh, double *W_out);
+int rd_batch_get_dt(const rd_batch *b, double *dt_out /* [n_mesh] */);
+void rd_batch_destroy(rd_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RD_H */

@@ -67,6 +67,7 @@ def lib():
         _lib.ora_time_step.argtypes = mesh_args + [dp, ctypes.c_double, ctypes.c_double, dp]
         _lib.ora_geometry.argtypes = mesh_args + [dp, dp, dp, dp]
         _lib.ora_triangle_terms.argtypes = mesh_args + [dp, ctypes.c_double, ctypes.c_double] + [dp] * 8
+        _lib.ora_triangle_terms_ld.argtypes = mesh_args + [dp, ctypes.c_double, ctypes.c_double] + [dp] * 4
         _lib.ora_stage2_terms.argtypes = mesh_args + [dp, dp, ctypes.c_double, ctypes.c_double,
                                                       ctypes.c_double, ctypes.c_int] + [dp] * 5
         _lib.ora_eigensystem.argtypes = [ctypes.c_double] * 6 + [dp] * 4
@@ -162,6 +163,20 @@ def triangle_terms(mesh, W, gamma=1.4, eps=1e-6):
                                   _p(out["phiLDA"]), _p(out["phiB"]), _p(out["beta"]),
                                   _p(out["theta"]), _p(out["Kp"]), _p(out["Km"]))
     _check(rc, "ora_triangle_terms")
+    del keep
+    return out
+
+
+def triangle_terms_ld(mesh, W, gamma=1.4, eps=1e-6):
+    """phi^T, phi^N, phi^LDA, phi^B evaluated in long double (returned as double)."""
+    keep, margs = _mesh_args(mesh)
+    nt = mesh.nt
+    Wc = np.ascontiguousarray(W, dtype=np.float64)
+    out = dict(phiT=np.zeros((nt, 4)), phiN=np.zeros((nt, 3, 4)), phiLDA=np.zeros((nt, 3, 4)),
+               phiB=np.zeros((nt, 3, 4)))
+    rc = lib().ora_triangle_terms_ld(*margs, _p(Wc), gamma, eps, _p(out["phiT"]), _p(out["phiN"]),
+                                     _p(out["phiLDA"]), _p(out["phiB"]))
+    _check(rc, "ora_triangle_terms_ld")
     del keep
     return out
 

@@ -737,6 +737,48 @@ int ora_geometry(int32_t nv, const double* xy, int32_t nt, const int32_t* tri,
   return ora::OK;
 }
 
+}  // extern "C"
+
+template <class S>
+int triangle_terms_impl(int32_t nv, const double* xy, int32_t nt, const int32_t* tri, const int8_t* shift,
+                        double Lx, double Ly, const double* W, double gamma, double eps, double* phiT,
+                        double* phiN, double* phiLDA, double* phiB) {
+  ora::Mesh<S> m;
+  int e = ora::build_mesh(nv, xy, nt, tri, shift, Lx, Ly, m);
+  if (e) return e;
+  std::vector<S> Wv, Zv;
+  ora::soa_to_aos(W, nv, Wv);
+  e = ora::all_Z(m, Wv, S(gamma), Zv);
+  if (e) return e;
+  for (int32_t t = 0; t < nt; ++t) {
+    S Z[3][4], n[3][2];
+    ora::tri_Z(m, Zv, t, Z, n);
+    ora::TriLin<S> o;
+    e = ora::linearise(Z, n, S(gamma), S(eps), o);
+    if (e) return e;
+    for (int k = 0; k < 4; ++k)
+      if (phiT) phiT[4 * (size_t)t + k] = ora::val(o.phiT[k]);
+    for (int c = 0; c < 3; ++c)
+      for (int k = 0; k < 4; ++k) {
+        size_t ix = 12 * (size_t)t + 4 * c + k;
+        if (phiN) phiN[ix] = ora::val(o.phiN[c][k]);
+        if (phiLDA) phiLDA[ix] = ora::val(o.phiLDA[c][k]);
+        if (phiB) phiB[ix] = ora::val(o.phiB[c][k]);
+      }
+  }
+  return ora::OK;
+}
+
+extern "C" {
+
+// Stage-1 shares evaluated in long double (round-off floor of the per-triangle terms).
+int ora_triangle_terms_ld(int32_t nv, const double* xy, int32_t nt, const int32_t* tri,
+                          const int8_t* shift, double Lx, double Ly, const double* W, double gamma,
+                          double eps, double* phiT, double* phiN, double* phiLDA, double* phiB) {
+  return triangle_terms_impl<long double>(nv, xy, nt, tri, shift, Lx, Ly, W, gamma, eps, phiT, phiN,
+                                          phiLDA, phiB);
+}
+
 // Stage-1 quantities of every triangle at state W (component-major):
 // phiT [nt][4], phiN/phiLDA/phiB [nt][3][4], beta [nt][3][4][4], theta [nt][4],
 // Kp/Km [nt][3][4][4].  Any output pointer may be NULL.

@@ -1,0 +1,286 @@
+"""Thin Python binding of the C ABI in include/rd.h (argument marshalling only).
+
+Every step of the solver runs in the CUDA library ``_lib/librd.so``; this
+module converts numpy arrays to pointers, installs PyTorch's caching allocator
+as the library's device allocator, and hands the library a PyTorch CUDA stream.
+There is no CPU fallback: if the library or a GPU is missing, every entry point
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RD_OK, RD_EINVAL, RD_ENOMEM, RD_ECUDA, RD_ENONPHYSICAL, RD_ETIMEOUT, RD_ENOTSUP = range(7)
+SCHEMES = {"N1": 0, "B2": 1, "LDA2": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1}
+ORDERS = {"none": 0, "morton": 1, "rcm": 2}
+
+_lib = None
+_alloc_refs = None
+
+
+class RDError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        msg = _lib.rd_strerror(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{what}: {msg} (status {status})")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int32), ("precision", ctypes.c_int32), ("cfl", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("eps_fix", ctypes.c_double)]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i8p = ctypes.POINTER(ctypes.c_int8)
+_vp = ctypes.c_void_p
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "rd_set_allocator": (ctypes.c_int, [ALLOC_FN, FREE_FN, _vp]),
+    "rd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "rd_version": (ctypes.c_int, []),
+    "rd_mesh_create": (ctypes.c_int, [ctypes.c_int32, _dp, ctypes.c_int32, _i32p, _i8p, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_int32, _vp, ctypes.POINTER(_vp)]),
+    "rd_mesh_destroy": (None, [_vp]),
+    "rd_mesh_permutation": (ctypes.c_int, [_vp, _i32p, _i32p]),
+    "rd_mesh_sizes": (ctypes.c_int, [_vp, _i32p, _i32p]),
+    "rd_state_init": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(Params), ctypes.POINTER(_vp)]),
+    "rd_state_set": (ctypes.c_int, [_vp, _dp]),
+    "rd_step": (ctypes.c_int, [_vp, _dp]),
+    "rd_run": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_double, _i32p]),
+    "rd_get_state": (ctypes.c_int, [_vp, _dp]),
+    "rd_conserved_totals": (ctypes.c_int, [_vp, _dp]),
+    "rd_get_time": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_int64)]),
+    "rd_get_dt": (ctypes.c_int, [_vp, _dp]),
+    "rd_state_destroy": (None, [_vp]),
+    "rd_state_triangle_shares": (ctypes.c_int, [_vp, ctypes.c_int32, _dp, _dp]),
+    "rd_state_profile": (ctypes.c_int, [_vp, ctypes.c_int32, _dp, _i32p]),
+    "rd_count_flops": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _dp]),
+    "rd_probe_fma_peak": (ctypes.c_int, [ctypes.c_int32, _dp]),
+    "rd_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(_vp), ctypes.POINTER(_dp),
+                                       ctypes.POINTER(Params), ctypes.POINTER(_vp)]),
+    "rd_batch_run": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "rd_batch_get_state": (ctypes.c_int, [_vp, ctypes.c_int32, _dp]),
+    "rd_batch_get_dt": (ctypes.c_int, [_vp, _dp]),
+    "rd_batch_destroy": (None, [_vp]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load librd.so (building it in-tree if needed).  Raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB) or not _build.up_to_date():
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library {_build.LIB} is missing; run build() first")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc, what):
+    if rc != RD_OK:
+        raise RDError(rc, what)
+
+
+def _ptr(a, ct=ctypes.c_double):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _require_gpu():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("the residual-distribution library needs a CUDA GPU; none is available")
+    return torch
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through PyTorch's caching allocator."""
+    global _alloc_refs
+    if _alloc_refs is not None:
+        return
+    torch = _require_gpu()
+    lib = load()
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    refs = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _check(lib.rd_set_allocator(refs[0], refs[1], None), "rd_set_allocator")
+    _alloc_refs = refs
+
+
+def count_flops(scheme: str, stage: int):
+    """Counted (add, mul, div, sqrt) of one triangle in a stage's triangle kernel."""
+    lib = load()
+    out = np.zeros(4)
+    _check(lib.rd_count_flops(SCHEMES[scheme], int(stage), _ptr(out)), "rd_count_flops")
+    return dict(add=out[0], mul=out[1], div=out[2], sqrt=out[3], total=float(out.sum()))
+
+
+def probe_fma_peak(precision: str = "fp64") -> float:
+    """Measured FMA throughput of the current GPU in flop/s."""
+    _require_gpu()
+    lib = load()
+    out = ctypes.c_double()
+    _check(lib.rd_probe_fma_peak(PRECISIONS[precision], ctypes.byref(out)), "rd_probe_fma_peak")
+    return out.value
+
+
+def _params(scheme, precision, cfl, gamma, eps_fix) -> Params:
+    return Params(SCHEMES[scheme] if isinstance(scheme, str) else int(scheme),
+                  PRECISIONS[precision] if isinstance(precision, str) else int(precision),
+                  float(cfl), float(gamma), float(eps_fix))
+
+
+class Mesh:
+    """Device mesh store (rd_mesh_create) built from an inputs.Mesh-like object."""
+
+    def __init__(self, mesh, reorder: str = "morton", stream=None, allocator: str = "torch"):
+        torch = _require_gpu()
+        lib = load()
+        if allocator == "torch":
+            use_torch_allocator()
+        self._stream = stream if stream is not None else torch.cuda.Stream()
+        self.nv, self.nt = int(mesh.nv), int(mesh.nt)
+        xy = np.ascontiguousarray(mesh.xy, dtype=np.float64)
+        tri = np.ascontiguousarray(mesh.tri, dtype=np.int32)
+        sh = None if mesh.shift is None else np.ascontiguousarray(mesh.shift, dtype=np.int8)
+        h = _vp()
+        rc = lib.rd_mesh_create(self.nv, _ptr(xy), self.nt, _ptr(tri, ctypes.c_int32), _ptr(sh, ctypes.c_int8),
+                                float(mesh.Lx), float(mesh.Ly), ORDERS[reorder],
+                                _vp(self._stream.cuda_stream), ctypes.byref(h))
+        _check(rc, "rd_mesh_create")
+        self.handle = h
+        self.states = []
+
+    @property
+    def stream(self):
+        return self._stream
+
+    def permutation(self):
+        vp = np.empty(self.nv, dtype=np.int32)
+        tp = np.empty(self.nt, dtype=np.int32)
+        _check(_lib.rd_mesh_permutation(self.handle, _ptr(vp, ctypes.c_int32), _ptr(tp, ctypes.c_int32)),
+               "rd_mesh_permutation")
+        return vp, tp
+
+    def close(self):
+        if getattr(self, "handle", None):
+            for s in list(self.states):
+                s.close()
+            _lib.rd_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class State:
+    """Solver state on one mesh (rd_state_init ... rd_state_destroy)."""
+
+    def __init__(self, mesh: Mesh, W, scheme="B2", precision="fp64", cfl=0.8, gamma=1.4, eps_fix=1e-6):
+        load()
+        self.mesh = mesh
+        self.params = _params(scheme, precision, cfl, gamma, eps_fix)
+        Wc = np.ascontiguousarray(W, dtype=np.float64)
+        if Wc.shape != (4, mesh.nv):
+            raise ValueError(f"W must have shape (4, {mesh.nv})")
+        h = _vp()
+        _check(_lib.rd_state_init(mesh.handle, _ptr(Wc), ctypes.byref(self.params), ctypes.byref(h)),
+               "rd_state_init")
+        self.handle = h
+        mesh.states.append(self)
+
+    def step(self, return_dt: bool = False):
+        dt = ctypes.c_double(0.0)
+        _check(_lib.rd_step(self.handle, ctypes.byref(dt) if return_dt else None), "rd_step")
+        return dt.value if return_dt else None
+
+    def run(self, n_steps: int, t_end: float = 0.0) -> int:
+        done = ctypes.c_int32(0)
+        _check(_lib.rd_run(self.handle, int(n_steps), float(t_end), ctypes.byref(done)), "rd_run")
+        return done.value
+
+    def get(self, out=None) -> np.ndarray:
+        W = out if out is not None else np.empty((4, self.mesh.nv), dtype=np.float64)
+        _check(_lib.rd_get_state(self.handle, _ptr(W)), "rd_get_state")
+        return W
+
+    def set(self, W):
+        Wc = np.ascontiguousarray(W, dtype=np.float64)
+        _check(_lib.rd_state_set(self.handle, _ptr(Wc)), "rd_state_set")
+
+    def conserved(self) -> np.ndarray:
+        out = np.zeros(4)
+        _check(_lib.rd_conserved_totals(self.handle, _ptr(out)), "rd_conserved_totals")
+        return out
+
+    def time(self):
+        t = ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(_lib.rd_get_time(self.handle, ctypes.byref(t), ctypes.byref(n)), "rd_get_time")
+        return t.value, n.value
+
+    def dt(self) -> float:
+        d = ctypes.c_double()
+        _check(_lib.rd_get_dt(self.handle, ctypes.byref(d)), "rd_get_dt")
+        return d.value
+
+    def triangle_shares(self, which: str = "B"):
+        w = {"N": 0, "LDA": 1, "B": 2}[which]
+        out = np.empty((self.mesh.nt, 3, 4))
+        cfl = np.empty(self.mesh.nt)
+        _check(_lib.rd_state_triangle_shares(self.handle, w, _ptr(out), _ptr(cfl)), "rd_state_triangle_shares")
+        return out, cfl
+
+    def profile(self, n_steps: int):
+        """Mean per-kernel milliseconds over n_steps real steps (CUDA events on the mesh stream)."""
+        ms = np.zeros(6)
+        n = ctypes.c_int32(0)
+        _check(_lib.rd_state_profile(self.handle, int(n_steps), _ptr(ms), ctypes.byref(n)), "rd_state_profile")
+        names = ("tri_stage1", "gather_cfl", "update1", "tri_stage2", "update2", "commit")
+        return dict(zip(names, ms.tolist())), n.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.rd_state_destroy(self.handle)
+            self.handle = None
+            if self in self.mesh.states:
+                self.mesh.states.remove(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,648 @@
+// rd_api.cu -- C ABI of the GB300 residual-distribution solver (see include/rd.h).
+//
+// Device memory comes from the installed allocator hook (default cudaMalloc);
+// all work of a mesh and its states is ordered on the mesh's stream.  A step
+// never synchronises with the host: dt, the simulation time, the step counter
+// and a sticky status word live in a device control block (DevCtl).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "rd_internal.h"
+#include "rd_kernels.cuh"
+
+using namespace rd;
+
+// ---------------------------------------------------------------------------
+// allocator hook
+// ---------------------------------------------------------------------------
+static rd_alloc_fn g_alloc = nullptr;
+static rd_free_fn g_free = nullptr;
+static void* g_alloc_ctx = nullptr;
+
+extern "C" int rd_set_allocator(rd_alloc_fn alloc, rd_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return RD_EINVAL;
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_ctx = ctx;
+  return RD_OK;
+}
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  rd_free_fn fr = nullptr;  // allocator that owns p (nullptr: cudaFree)
+  void* ctx = nullptr;
+};
+
+int dev_alloc(DevBuf& b, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 16;
+  if (g_alloc) {
+    b.p = g_alloc(bytes, (void*)s, g_alloc_ctx);
+    if (!b.p) return RD_ENOMEM;
+    b.fr = g_free;
+    b.ctx = g_alloc_ctx;
+    return RD_OK;
+  }
+  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return RD_ENOMEM;
+  }
+  b.fr = nullptr;
+  return RD_OK;
+}
+
+void dev_free(DevBuf& b) {
+  if (!b.p) return;
+  if (b.fr) b.fr(b.p, b.ctx);
+  else cudaFree(b.p);
+  b.p = nullptr;
+}
+
+#define CU(x)                                  \
+  do {                                         \
+    cudaError_t e_ = (x);                      \
+    if (e_ != cudaSuccess) {                   \
+      cudaGetLastError();                      \
+      return RD_ECUDA;                         \
+    }                                          \
+  } while (0)
+
+#define CK(x)              \
+  do {                     \
+    int s_ = (x);          \
+    if (s_ != RD_OK) return s_; \
+  } while (0)
+
+inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+constexpr int TRI_BLOCK = 128;
+constexpr int VTX_BLOCK = 256;
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// mesh
+// ---------------------------------------------------------------------------
+struct rd_mesh {
+  HostMesh h;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  DevBuf tri, ptr, ent, vperm;
+  // geometry per precision: nx, ny, hl, area, lmax, V
+  DevBuf geo[2][6];
+  bool geo_ready[2] = {false, false};
+};
+
+namespace {
+
+template <class T>
+int upload_vec(DevBuf& b, const std::vector<double>& src, cudaStream_t s) {
+  std::vector<T> tmp(src.size());
+  for (size_t i = 0; i < src.size(); ++i) tmp[i] = (T)src[i];
+  CK(dev_alloc(b, tmp.size() * sizeof(T), s));
+  CU(cudaMemcpyAsync(b.p, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  CU(cudaStreamSynchronize(s));
+  return RD_OK;
+}
+
+template <class T>
+int mesh_geometry(rd_mesh* m) {
+  const int pi = sizeof(T) == 8 ? 0 : 1;
+  if (m->geo_ready[pi]) return RD_OK;
+  const std::vector<double>* src[6] = {&m->h.nx, &m->h.ny, &m->h.hl, &m->h.area, &m->h.lmax, &m->h.V};
+  for (int k = 0; k < 6; ++k) CK(upload_vec<T>(m->geo[pi][k], *src[k], m->stream));
+  m->geo_ready[pi] = true;
+  return RD_OK;
+}
+
+template <class T>
+DevGeo<T> geo_of(const rd_mesh* m) {
+  const int pi = sizeof(T) == 8 ? 0 : 1;
+  DevGeo<T> g;
+  g.nx = (const T*)m->geo[pi][0].p;
+  g.ny = (const T*)m->geo[pi][1].p;
+  g.hl = (const T*)m->geo[pi][2].p;
+  g.area = (const T*)m->geo[pi][3].p;
+  g.lmax = (const T*)m->geo[pi][4].p;
+  return g;
+}
+
+}  // namespace
+
+extern "C" int rd_mesh_create(int32_t n_vertex, const double* xy, int32_t n_tri, const int32_t* tri,
+                              const int8_t* image_shift, double Lx, double Ly, int32_t reorder,
+                              void* cuda_stream, rd_mesh** out) {
+  if (!out) return RD_EINVAL;
+  *out = nullptr;
+  rd_mesh* m = new (std::nothrow) rd_mesh();
+  if (!m) return RD_ENOMEM;
+  int st = build_host_mesh(n_vertex, xy, n_tri, tri, image_shift, Lx, Ly, reorder, m->h);
+  if (st != RD_OK) {
+    delete m;
+    return st;
+  }
+  if (cuda_stream) {
+    m->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete m;
+      return RD_ECUDA;
+    }
+    m->own_stream = true;
+  }
+  auto up_int = [&](DevBuf& b, const std::vector<int32_t>& v) -> int {
+    CK(dev_alloc(b, v.size() * sizeof(int32_t), m->stream));
+    CU(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice, m->stream));
+    return RD_OK;
+  };
+  st = up_int(m->tri, m->h.tri);
+  if (st == RD_OK) st = up_int(m->ptr, m->h.csr_ptr);
+  if (st == RD_OK) st = up_int(m->ent, m->h.csr_ent);
+  if (st == RD_OK) st = up_int(m->vperm, m->h.vperm);
+  if (st == RD_OK && cudaStreamSynchronize(m->stream) != cudaSuccess) {
+    cudaGetLastError();
+    st = RD_ECUDA;
+  }
+  if (st != RD_OK) {
+    rd_mesh_destroy(m);
+    return st;
+  }
+  *out = m;
+  return RD_OK;
+}
+
+extern "C" void rd_mesh_destroy(rd_mesh* m) {
+  if (!m) return;
+  if (m->stream) cudaStreamSynchronize(m->stream);
+  dev_free(m->tri);
+  dev_free(m->ptr);
+  dev_free(m->ent);
+  dev_free(m->vperm);
+  for (int p = 0; p < 2; ++p)
+    for (int k = 0; k < 6; ++k) dev_free(m->geo[p][k]);
+  if (m->own_stream) cudaStreamDestroy(m->stream);
+  delete m;
+}
+
+extern "C" int rd_mesh_permutation(const rd_mesh* m, int32_t* vertex_perm, int32_t* tri_perm) {
+  if (!m) return RD_EINVAL;
+  if (vertex_perm) std::memcpy(vertex_perm, m->h.vperm.data(), sizeof(int32_t) * m->h.nv);
+  if (tri_perm) std::memcpy(tri_perm, m->h.tperm.data(), sizeof(int32_t) * m->h.nt);
+  return RD_OK;
+}
+
+extern "C" int rd_mesh_sizes(const rd_mesh* m, int32_t* n_vertex, int32_t* n_tri) {
+  if (!m) return RD_EINVAL;
+  if (n_vertex) *n_vertex = m->h.nv;
+  if (n_tri) *n_tri = m->h.nt;
+  return RD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// state
+// ---------------------------------------------------------------------------
+struct rd_state {
+  rd_mesh* m = nullptr;
+  rd_params p{};
+  int pi = 0;            // 0: double, 1: float
+  size_t ts = 8;         // sizeof(T)
+  DevBuf W[2], Z[2], spd[2];
+  DevBuf Ws, Zs, R1, share, rec, cfl, partial, ctl, cons_partial, cons_out;
+  DevBuf stage;  // [4][nv] double, caller vertex order (host I/O)
+  long long launched = 0;  // host view of the committed step count (parity of the buffers)
+  cudaGraphExec_t g2 = nullptr;  // two steps (even -> odd -> even)
+  bool graph_failed = false;
+};
+
+namespace {
+
+bool valid_params(const rd_params* p) {
+  if (!p) return false;
+  if (p->scheme != RD_N1 && p->scheme != RD_B2 && p->scheme != RD_LDA2) return false;
+  if (p->precision != RD_FP64 && p->precision != RD_FP32) return false;
+  if (!(p->cfl > 0.0) || !(p->gamma > 1.0) || !(p->eps_fix >= 0.0)) return false;
+  if (!std::isfinite(p->cfl) || !std::isfinite(p->gamma) || !std::isfinite(p->eps_fix)) return false;
+  return true;
+}
+
+__global__ void k_begin(DevCtl* ctl, double t_end) {
+  if (ctl->status == 0) ctl->stop = 0;
+  ctl->t_end = t_end;
+}
+
+// Launches one step reading buffer a and writing buffer 1-a.  ev (nullable):
+// seven events recorded before each kernel and after the last one.
+template <class T>
+int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr) {
+  rd_mesh* m = s->m;
+  const int nt = m->h.nt, nv = m->h.nv, b = 1 - a;
+  cudaStream_t st = m->stream;
+  DevGeo<T> g = geo_of<T>(m);
+  const T* V = (const T*)m->geo[s->pi][5].p;
+  const int* tri = (const int*)m->tri.p;
+  const int* ptr = (const int*)m->ptr.p;
+  const int* ent = (const int*)m->ent.p;
+  DevCtl* ctl = (DevCtl*)s->ctl.p;
+  T gamma = (T)s->p.gamma, eps = (T)s->p.eps_fix, cfl = (T)s->p.cfl;
+  T* share = (T*)s->share.p;
+  T* rec = (T*)s->rec.p;
+  T* cf = (T*)s->cfl.p;
+  unsigned gt = nblk(nt, TRI_BLOCK), gv = nblk(nv, VTX_BLOCK);
+  const T* Za = (const T*)s->Z[a].p;
+  const T* Sa = (const T*)s->spd[a].p;
+  auto mark = [&](int k) {
+    if (ev) cudaEventRecord(ev[k], st);
+  };
+  mark(0);
+  switch (s->p.scheme) {
+    case RD_N1:
+      k_tri_stage1<T, RD_N1><<<gt, TRI_BLOCK, 0, st>>>(nt, nv, tri, g, Za, Sa, gamma, eps, share, nullptr, cf, ctl);
+      break;
+    case RD_B2:
+      k_tri_stage1<T, RD_B2><<<gt, TRI_BLOCK, 0, st>>>(nt, nv, tri, g, Za, Sa, gamma, eps, share, rec, cf, ctl);
+      break;
+    default:
+      k_tri_stage1<T, RD_LDA2><<<gt, TRI_BLOCK, 0, st>>>(nt, nv, tri, g, Za, Sa, gamma, eps, share, rec, cf, ctl);
+      break;
+  }
+  mark(1);
+  k_gather_cfl<T, VTX_BLOCK><<<gv, VTX_BLOCK, 0, st>>>(nv, ptr, ent, share, cf, V, (T*)s->R1.p, (T*)s->partial.p,
+                                                       cfl, ctl);
+  mark(2);
+  if (s->p.scheme == RD_N1) {
+    k_update<T><<<gv, VTX_BLOCK, 0, st>>>(nv, (const T*)s->W[a].p, (const T*)s->R1.p, ptr, ent, nullptr, V, gamma,
+                                          (T*)s->W[b].p, (T*)s->Z[b].p, (T*)s->spd[b].p, ctl);
+    mark(3);
+    mark(4);
+    mark(5);
+  } else {
+    k_update<T><<<gv, VTX_BLOCK, 0, st>>>(nv, (const T*)s->W[a].p, (const T*)s->R1.p, ptr, ent, nullptr, V, gamma,
+                                          (T*)s->Ws.p, (T*)s->Zs.p, nullptr, ctl);
+    mark(3);
+    if (s->p.scheme == RD_B2)
+      k_tri_stage2<T, RD_B2><<<gt, TRI_BLOCK, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
+                                                       (const T*)s->Ws.p, rec, gamma, eps, share, ctl);
+    else
+      k_tri_stage2<T, RD_LDA2><<<gt, TRI_BLOCK, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
+                                                         (const T*)s->Ws.p, rec, gamma, eps, share, ctl);
+    mark(4);
+    k_update<T><<<gv, VTX_BLOCK, 0, st>>>(nv, (const T*)s->Ws.p, nullptr, ptr, ent, share, V, gamma,
+                                          (T*)s->W[b].p, (T*)s->Z[b].p, (T*)s->spd[b].p, ctl);
+    mark(5);
+  }
+  k_commit<<<1, 1, 0, st>>>(ctl);
+  mark(6);
+  CU(cudaGetLastError());
+  return RD_OK;
+}
+
+int launch_step_any(rd_state* s, int a, cudaEvent_t* ev = nullptr) {
+  return s->pi == 0 ? launch_step<double>(s, a, ev) : launch_step<float>(s, a, ev);
+}
+
+int read_ctl(const rd_state* s, DevCtl& c) {
+  CU(cudaMemcpyAsync(&c, s->ctl.p, sizeof(DevCtl), cudaMemcpyDeviceToHost, s->m->stream));
+  CU(cudaStreamSynchronize(s->m->stream));
+  return RD_OK;
+}
+
+int status_to_rd(int st) { return st ? RD_ENONPHYSICAL : RD_OK; }
+
+// Host (caller order, double) -> device staging -> internal order in T, then Z and |v|+c.
+template <class T>
+int upload_state(rd_state* s, const double* W, int buf) {
+  rd_mesh* m = s->m;
+  const int nv = m->h.nv;
+  cudaStream_t st = m->stream;
+  DevCtl* ctl = (DevCtl*)s->ctl.p;
+  CU(cudaMemcpyAsync(s->stage.p, W, 4 * (size_t)nv * sizeof(double), cudaMemcpyHostToDevice, st));
+  k_permute_in<T><<<nblk(nv, VTX_BLOCK), VTX_BLOCK, 0, st>>>(nv, (const int*)m->vperm.p, (const double*)s->stage.p,
+                                                             (T*)s->W[buf].p, ctl);
+  k_prepare<T><<<nblk(nv, VTX_BLOCK), VTX_BLOCK, 0, st>>>(nv, (const T*)s->W[buf].p, (T)s->p.gamma,
+                                                          (T*)s->Z[buf].p, (T*)s->spd[buf].p, ctl);
+  CU(cudaGetLastError());
+  DevCtl c;
+  CK(read_ctl(s, c));
+  return status_to_rd(c.status);
+}
+
+// Device internal order in T -> staging (caller order, double) -> host.
+template <class T>
+int download_state(const rd_state* s, int buf, double* W_out) {
+  rd_mesh* m = s->m;
+  const int nv = m->h.nv;
+  cudaStream_t st = m->stream;
+  k_permute_out<T><<<nblk(nv, VTX_BLOCK), VTX_BLOCK, 0, st>>>(nv, (const int*)m->vperm.p, (const T*)s->W[buf].p,
+                                                              (double*)s->stage.p);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(W_out, s->stage.p, 4 * (size_t)nv * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  return RD_OK;
+}
+
+int alloc_state(rd_state* s) {
+  rd_mesh* m = s->m;
+  const size_t nv = m->h.nv, nt = m->h.nt, ts = s->ts;
+  cudaStream_t st = m->stream;
+  for (int b = 0; b < 2; ++b) {
+    CK(dev_alloc(s->W[b], 4 * nv * ts, st));
+    CK(dev_alloc(s->Z[b], 4 * nv * ts, st));
+    CK(dev_alloc(s->spd[b], nv * ts, st));
+  }
+  CK(dev_alloc(s->R1, 4 * nv * ts, st));
+  CK(dev_alloc(s->share, 12 * nt * ts, st));
+  CK(dev_alloc(s->cfl, nt * ts, st));
+  CK(dev_alloc(s->partial, (size_t)nblk(nv, VTX_BLOCK) * ts, st));
+  CK(dev_alloc(s->ctl, sizeof(DevCtl), st));
+  CK(dev_alloc(s->cons_partial, (size_t)nblk(nv, VTX_BLOCK) * 4 * sizeof(double), st));
+  CK(dev_alloc(s->cons_out, 4 * sizeof(double), st));
+  CK(dev_alloc(s->stage, 4 * nv * sizeof(double), st));
+  if (s->p.scheme != RD_N1) {
+    CK(dev_alloc(s->Ws, 4 * nv * ts, st));
+    CK(dev_alloc(s->Zs, 4 * nv * ts, st));
+    CK(dev_alloc(s->rec, 16 * nt * ts, st));
+  }
+  DevCtl c{};
+  CU(cudaMemcpyAsync(s->ctl.p, &c, sizeof(DevCtl), cudaMemcpyHostToDevice, st));
+  CU(cudaStreamSynchronize(st));
+  return RD_OK;
+}
+
+int build_graph(rd_state* s) {
+  if (s->g2 || s->graph_failed) return RD_OK;
+  cudaStream_t st = s->m->stream;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    s->graph_failed = true;
+    return RD_OK;
+  }
+  int r0 = launch_step_any(s, 0);
+  int r1 = r0 == RD_OK ? launch_step_any(s, 1) : r0;
+  cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (r1 != RD_OK || e != cudaSuccess || !g) {
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    s->graph_failed = true;
+    return RD_OK;
+  }
+  if (cudaGraphInstantiate(&s->g2, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    s->g2 = nullptr;
+    s->graph_failed = true;
+  }
+  cudaGraphDestroy(g);
+  return RD_OK;
+}
+
+}  // namespace
+
+extern "C" int rd_state_init(rd_mesh* m, const double* W, const rd_params* p, rd_state** out) {
+  if (!m || !W || !out || !valid_params(p)) return RD_EINVAL;
+  *out = nullptr;
+  rd_state* s = new (std::nothrow) rd_state();
+  if (!s) return RD_ENOMEM;
+  s->m = m;
+  s->p = *p;
+  s->pi = p->precision == RD_FP64 ? 0 : 1;
+  s->ts = s->pi == 0 ? sizeof(double) : sizeof(float);
+  int st = s->pi == 0 ? mesh_geometry<double>(m) : mesh_geometry<float>(m);
+  if (st == RD_OK) st = alloc_state(s);
+  if (st == RD_OK) st = s->pi == 0 ? upload_state<double>(s, W, 0) : upload_state<float>(s, W, 0);
+  if (st != RD_OK) {
+    rd_state_destroy(s);
+    return st;
+  }
+  *out = s;
+  return RD_OK;
+}
+
+extern "C" int rd_state_set(rd_state* s, const double* W) {
+  if (!s || !W) return RD_EINVAL;
+  DevCtl c;
+  CK(read_ctl(s, c));
+  if (c.status) return RD_ENONPHYSICAL;
+  int buf = (int)(c.steps & 1);
+  s->launched = c.steps;
+  return s->pi == 0 ? upload_state<double>(s, W, buf) : upload_state<float>(s, W, buf);
+}
+
+extern "C" int rd_step(rd_state* s, double* dt_out) {
+  if (!s) return RD_EINVAL;
+  cudaStream_t st = s->m->stream;
+  k_begin<<<1, 1, 0, st>>>((DevCtl*)s->ctl.p, 0.0);
+  CK(launch_step_any(s, (int)(s->launched & 1)));
+  s->launched++;
+  if (dt_out) {
+    DevCtl c;
+    CK(read_ctl(s, c));
+    s->launched = c.steps;
+    *dt_out = c.dt;
+    if (c.status) return RD_ENONPHYSICAL;
+  }
+  return RD_OK;
+}
+
+extern "C" int rd_run(rd_state* s, int32_t n_steps, double t_end, int32_t* steps_done) {
+  if (!s || n_steps < 0) return RD_EINVAL;
+  cudaStream_t st = s->m->stream;
+  DevCtl c0;
+  CK(read_ctl(s, c0));
+  s->launched = c0.steps;
+  if (c0.status) {
+    if (steps_done) *steps_done = 0;
+    return RD_ENONPHYSICAL;
+  }
+  k_begin<<<1, 1, 0, st>>>((DevCtl*)s->ctl.p, t_end > 0.0 ? t_end : 0.0);
+  CU(cudaGetLastError());
+  int32_t left = n_steps;
+  if (left > 0 && (s->launched & 1)) {
+    CK(launch_step_any(s, 1));
+    s->launched++;
+    left--;
+  }
+  if (left >= 2) CK(build_graph(s));
+  while (left >= 2 && s->g2) {
+    CU(cudaGraphLaunch(s->g2, st));
+    s->launched += 2;
+    left -= 2;
+  }
+  while (left > 0) {
+    CK(launch_step_any(s, (int)(s->launched & 1)));
+    s->launched++;
+    left--;
+  }
+  DevCtl c;
+  CK(read_ctl(s, c));
+  s->launched = c.steps;
+  if (steps_done) *steps_done = (int32_t)(c.steps - c0.steps);
+  return status_to_rd(c.status);
+}
+
+extern "C" int rd_state_profile(rd_state* s, int32_t n_steps, double* ms_per_launch, int32_t* launches_per_step) {
+  if (!s || n_steps <= 0 || !ms_per_launch) return RD_EINVAL;
+  cudaStream_t st = s->m->stream;
+  DevCtl c0;
+  CK(read_ctl(s, c0));
+  s->launched = c0.steps;
+  if (c0.status) return RD_ENONPHYSICAL;
+  k_begin<<<1, 1, 0, st>>>((DevCtl*)s->ctl.p, 0.0);
+  std::vector<cudaEvent_t> ev(7 * (size_t)n_steps, nullptr);
+  int rc = RD_OK;
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) rc = RD_ECUDA;
+  for (int32_t k = 0; k < n_steps && rc == RD_OK; ++k) {
+    rc = launch_step_any(s, (int)(s->launched & 1), ev.data() + 7 * (size_t)k);
+    s->launched++;
+  }
+  if (rc == RD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = RD_ECUDA;
+  for (int j = 0; j < 6; ++j) ms_per_launch[j] = 0.0;
+  for (int32_t k = 0; k < n_steps && rc == RD_OK; ++k)
+    for (int j = 0; j < 6; ++j) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[7 * (size_t)k + j], ev[7 * (size_t)k + j + 1]) != cudaSuccess) rc = RD_ECUDA;
+      ms_per_launch[j] += ms / n_steps;
+    }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  cudaGetLastError();
+  if (launches_per_step) *launches_per_step = s->p.scheme == RD_N1 ? 4 : 6;
+  if (rc != RD_OK) return rc;
+  DevCtl c;
+  CK(read_ctl(s, c));
+  s->launched = c.steps;
+  return status_to_rd(c.status);
+}
+
+extern "C" int rd_get_state(const rd_state* s, double* W_out) {
+  if (!s || !W_out) return RD_EINVAL;
+  DevCtl c;
+  CK(read_ctl(s, c));
+  int buf = (int)(c.steps & 1);
+  return s->pi == 0 ? download_state<double>(s, buf, W_out) : download_state<float>(s, buf, W_out);
+}
+
+extern "C" int rd_conserved_totals(const rd_state* s, double out[4]) {
+  if (!s || !out) return RD_EINVAL;
+  DevCtl c;
+  CK(read_ctl(s, c));
+  int buf = (int)(c.steps & 1);
+  const int nv = s->m->h.nv;
+  unsigned nb = nblk(nv, VTX_BLOCK);
+  cudaStream_t st = s->m->stream;
+  if (s->pi == 0)
+    k_conserved_partial<double, VTX_BLOCK><<<nb, VTX_BLOCK, 0, st>>>(
+        nv, (const double*)s->W[buf].p, (const double*)s->m->geo[0][5].p, (double*)s->cons_partial.p);
+  else
+    k_conserved_partial<float, VTX_BLOCK><<<nb, VTX_BLOCK, 0, st>>>(
+        nv, (const float*)s->W[buf].p, (const float*)s->m->geo[1][5].p, (double*)s->cons_partial.p);
+  k_conserved_final<<<1, 32, 0, st>>>((int)nb, (const double*)s->cons_partial.p, (double*)s->cons_out.p);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(out, s->cons_out.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  return RD_OK;
+}
+
+extern "C" int rd_get_time(const rd_state* s, double* t, int64_t* steps) {
+  if (!s) return RD_EINVAL;
+  DevCtl c;
+  CK(read_ctl(s, c));
+  if (t) *t = c.t;
+  if (steps) *steps = c.steps;
+  return RD_OK;
+}
+
+extern "C" int rd_get_dt(const rd_state* s, double* dt) {
+  if (!s || !dt) return RD_EINVAL;
+  DevCtl c;
+  CK(read_ctl(s, c));
+  *dt = c.dt;
+  return RD_OK;
+}
+
+extern "C" int rd_state_triangle_shares(rd_state* s, int32_t which, double* out, double* cfl_term) {
+  if (!s || !out || which < 0 || which > 2) return RD_EINVAL;
+  DevCtl c;
+  CK(read_ctl(s, c));
+  int buf = (int)(c.steps & 1);
+  rd_mesh* m = s->m;
+  const int nt = m->h.nt, nv = m->h.nv;
+  DevBuf tmp;
+  CK(dev_alloc(tmp, 36 * (size_t)nt * s->ts, m->stream));
+  cudaStream_t st = m->stream;
+  int rc = RD_OK;
+  std::vector<double> terms(36 * (size_t)nt), cf(nt);
+  if (s->pi == 0) {
+    k_tri_terms<double><<<nblk(nt, TRI_BLOCK), TRI_BLOCK, 0, st>>>(
+        nt, nv, (const int*)m->tri.p, geo_of<double>(m), (const double*)s->Z[buf].p, (const double*)s->spd[buf].p,
+        s->p.gamma, s->p.eps_fix, (double*)tmp.p, (double*)s->cfl.p, (DevCtl*)s->ctl.p);
+    if (cudaMemcpyAsync(terms.data(), tmp.p, terms.size() * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(cf.data(), s->cfl.p, nt * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      rc = RD_ECUDA;
+  } else {
+    k_tri_terms<float><<<nblk(nt, TRI_BLOCK), TRI_BLOCK, 0, st>>>(
+        nt, nv, (const int*)m->tri.p, geo_of<float>(m), (const float*)s->Z[buf].p, (const float*)s->spd[buf].p,
+        (float)s->p.gamma, (float)s->p.eps_fix, (float*)tmp.p, (float*)s->cfl.p, (DevCtl*)s->ctl.p);
+    std::vector<float> tf(terms.size()), cff(nt);
+    if (cudaMemcpyAsync(tf.data(), tmp.p, tf.size() * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(cff.data(), s->cfl.p, nt * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = RD_ECUDA;
+    for (size_t i = 0; i < tf.size(); ++i) terms[i] = tf[i];
+    for (int i = 0; i < nt; ++i) cf[i] = cff[i];
+  }
+  if (rc == RD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = RD_ECUDA;
+  cudaGetLastError();
+  dev_free(tmp);
+  if (rc != RD_OK) return rc;
+  const size_t off = (size_t)which * 12 * nt;
+  for (int t = 0; t < nt; ++t) {
+    int to = m->h.tperm[t];
+    std::memcpy(out + 12 * (size_t)to, terms.data() + off + 12 * (size_t)t, 12 * sizeof(double));
+    if (cfl_term) cfl_term[to] = cf[t];
+  }
+  CK(read_ctl(s, c));
+  return status_to_rd(c.status);
+}
+
+extern "C" void rd_state_destroy(rd_state* s) {
+  if (!s) return;
+  if (s->m && s->m->stream) cudaStreamSynchronize(s->m->stream);
+  if (s->g2) cudaGraphExecDestroy(s->g2);
+  for (int b = 0; b < 2; ++b) {
+    dev_free(s->W[b]);
+    dev_free(s->Z[b]);
+    dev_free(s->spd[b]);
+  }
+  DevBuf* bufs[] = {&s->Ws, &s->Zs, &s->R1, &s->share, &s->rec, &s->cfl, &s->partial, &s->ctl,
+                    &s->cons_partial, &s->cons_out, &s->stage};
+  for (DevBuf* b : bufs) dev_free(*b);
+  delete s;
+}
+
+// ---------------------------------------------------------------------------
+// misc
+// ---------------------------------------------------------------------------
+extern "C" const char* rd_strerror(int status) {
+  switch (status) {
+    case RD_OK: return "ok";
+    case RD_EINVAL: return "invalid argument";
+    case RD_ENOMEM: return "out of memory";
+    case RD_ECUDA: return "CUDA runtime error";
+    case RD_ENONPHYSICAL: return "non-physical state (rho<=0, p<=0, c^2<=0, singular N^ or NaN)";
+    case RD_ETIMEOUT: return "bounded device wait expired";
+    case RD_ENOTSUP: return "not supported";
+    default: return "unknown status";
+  }
+}
+
+extern "C" int rd_version(void) { return 1; }

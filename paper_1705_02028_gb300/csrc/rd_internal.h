@@ -1,0 +1,51 @@
+// rd_internal.h -- internal types shared by the mesh store (host) and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/rd.h"
+
+namespace rd {
+
+// Host-side mesh store: everything the device buffers are built from.
+// Internal order: vertices and triangles renumbered by the chosen reordering.
+struct HostMesh {
+  int32_t nv = 0, nt = 0;
+  double Lx = 0, Ly = 0;
+  std::vector<int32_t> vperm;    // [nv]  internal vertex -> caller vertex
+  std::vector<int32_t> vinv;     // [nv]  caller vertex -> internal vertex
+  std::vector<int32_t> tperm;    // [nt]  internal triangle -> caller triangle
+  std::vector<int32_t> tri;      // [3][nt] corners (internal vertex ids), component-major
+  std::vector<double> nx, ny;    // [3][nt] unit inward normal of the edge opposite each corner
+  std::vector<double> hl;        // [3][nt] half length of that edge
+  std::vector<double> area;      // [nt]   |T|
+  std::vector<double> lmax;      // [nt]   longest edge l_max^T
+  std::vector<double> V;         // [nv]   V_i = sum_{T containing i} |T| / 3
+  std::vector<int32_t> csr_ptr;  // [nv+1] vertex -> incident (triangle, corner) entries
+  std::vector<int32_t> csr_ent;  // [3 nt] entry = 3 * triangle + corner, ascending per vertex
+};
+
+// Validates and builds the host mesh store.  Returns an RD_* status.
+int build_host_mesh(int32_t nv, const double* xy, int32_t nt, const int32_t* tri,
+                    const int8_t* shift, double Lx, double Ly, int32_t reorder, HostMesh& out);
+
+// Device control block of one state (one per mesh in batched mode).
+struct DevCtl {
+  double dt;              // dt of the current step
+  double t;               // simulation time after the last committed step
+  double t_end;           // > 0: stop when t reaches t_end
+  long long steps;        // committed steps
+  int status;             // sticky error bits (RD_ST_*)
+  int stop;               // nonzero: remaining kernels of this run are no-ops
+  unsigned int ticket;    // last-block-done counter of the dt reduction
+  int pad;
+};
+
+enum : int {
+  ST_NONPHYS_VERTEX = 1,  // rho <= 0, p <= 0 or NaN at a vertex
+  ST_ROE = 2,             // c^2 <= 0 at a Roe state
+  ST_SINGULAR = 4,        // zero pivot in (sum_j K_j^-)
+};
+
+}  // namespace rd

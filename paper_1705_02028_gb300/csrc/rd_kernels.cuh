@@ -1,0 +1,742 @@
+// rd_kernels.cuh -- CUDA kernels of the residual-distribution step (sm_103a).
+//
+// One B2 step (Sec. 3.4, Eqs. eqRK1/eqRK2) is five kernels plus a one-thread
+// commit; N1 (forward Euler, Eq. eqUpdate) is three plus the commit:
+//
+//   k_tri_stage1    per triangle: Roe linearisation at W^n, phi^T, N / LDA / B
+//                   shares (Sec. 3.3), CFL term l_max^T lambda_max^T (Sec. 3.2)
+//   k_gather_cfl    per vertex: R1 = sum of shares through the CSR, sigma_i,
+//                   block min of 2 V_i / sigma_i, last block -> dt
+//   k_update1       per vertex: W* = W^n - dt/V R1 (N1: W^{n+1}); Z(W*), checks
+//   k_tri_stage2    per triangle: linearisation at W*, total residuals
+//                   Phi^N, Phi^LDA (m^LDA = |T|/3 beta_i), blend
+//   k_update2       per vertex: W^{n+1} = W* - dt/V R2, Z and |v|+c for the next step
+//   k_commit        one thread: t += dt, steps++, stop test
+//
+// Arithmetic notes (all algebraically identical to the paper's definitions):
+//   * K_i^{+-} v is applied in factored form R_i Lambda_i^{+-} (L_i v) with the
+//     closed-form left eigenvectors L = R^{-1} of App. A's right eigenvectors.
+//   * N^ = (sum_j K_j^-)^{-1} is never formed: sum_j K_j^- is LU-factorised with
+//     partial pivoting and solved for the two right-hand sides the N and LDA
+//     schemes need (N^ sum_j K_j^- W^_j and N^ phi^T).
+//   * phi^T = sum_i K_i Z_i uses the flux Jacobians dF/dZ, dG/dZ at Zbar
+//     applied to sum_i (n_i/2) Z_i (Sec. 3.2, eqRes..eqLinearA).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rd_internal.h"
+
+#define RD_HD __host__ __device__ __forceinline__
+
+namespace rd {
+
+template <class T>
+struct DevGeo {
+  const T* nx;    // [3][nt] unit inward normals
+  const T* ny;
+  const T* hl;    // [3][nt] half edge lengths
+  const T* area;  // [nt]
+  const T* lmax;  // [nt]
+};
+
+template <class T>
+struct RoeState {
+  T u, v, h, c, q2h, ic2, ic2h, g1;
+};
+
+template <class T>
+struct NodeSys {
+  T nx, ny, w, uperp;  // unit normal, u.n, v nx - u ny
+  T lp[3], lm[3];      // Lambda^+ and Lambda^- for (w+c, w-c, w) times |n|/2
+};
+
+// Regularised |lambda|: (lambda^2 + delta^2) / (2 delta) below delta (C^1), i2d = 1 / (2 delta).
+template <class T>
+RD_HD T abs_reg(T lam, T delta, T i2d) {
+  T a = fabs(lam);
+  return (a < delta) ? (lam * lam + delta * delta) * i2d : a;
+}
+
+// a = L v, L = R^{-1} (left eigenvectors of K(n) for a unit normal, App. A).
+template <class T>
+RD_HD void L_apply(const RoeState<T>& r, const NodeSys<T>& n, const T v[4], T a[4]) {
+  T dp = r.g1 * (r.q2h * v[0] - r.u * v[1] - r.v * v[2] + v[3]);
+  T m = r.c * (n.nx * v[1] + n.ny * v[2] - n.w * v[0]);
+  a[0] = (dp + m) * r.ic2h;
+  a[1] = (dp - m) * r.ic2h;
+  a[2] = n.nx * v[2] - n.ny * v[1] - n.uperp * v[0];
+  a[3] = v[0] - dp * r.ic2;
+}
+
+// o = R a, R = right eigenvectors of App. A as columns.
+template <class T>
+RD_HD void R_apply(const RoeState<T>& r, const NodeSys<T>& n, const T a[4], T o[4]) {
+  T s = a[0] + a[1], d = a[0] - a[1], t0 = s + a[3];
+  o[0] = t0;
+  o[1] = r.u * t0 + r.c * n.nx * d - n.ny * a[2];
+  o[2] = r.v * t0 + r.c * n.ny * d + n.nx * a[2];
+  o[3] = r.h * s + r.c * n.w * d + n.uperp * a[2] + r.q2h * a[3];
+}
+
+template <class T, bool PLUS>
+RD_HD void Kpm_apply(const RoeState<T>& r, const NodeSys<T>& n, const T v[4], T o[4]) {
+  T a[4];
+  L_apply(r, n, v, a);
+  const T* l = PLUS ? n.lp : n.lm;
+  a[0] *= l[0];
+  a[1] *= l[1];
+  a[2] *= l[2];
+  a[3] *= l[2];
+  R_apply(r, n, a, o);
+}
+
+// LU factorisation with partial pivoting of a 4x4 matrix held in registers.
+template <class T>
+struct LU4 {
+  T a[4][4];
+  T rdiag[4];  // reciprocal pivots
+  int piv[3];
+  RD_HD bool factor() {
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      int p = k;
+      T best = fabs(a[k][k]);
+#pragma unroll
+      for (int r = k + 1; r < 4; ++r) {
+        T v = fabs(a[r][k]);
+        if (v > best) { best = v; p = r; }
+      }
+      if (k < 3) piv[k] = p;
+#pragma unroll
+      for (int r = k + 1; r < 4; ++r) {
+        bool sw = (p == r);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          T x = a[k][c], y = a[r][c];
+          a[k][c] = sw ? y : x;
+          a[r][c] = sw ? x : y;
+        }
+      }
+      ok = ok && (best > T(0));
+      T inv = T(1) / a[k][k];
+      rdiag[k] = inv;
+#pragma unroll
+      for (int r = k + 1; r < 4; ++r) {
+        T f = a[r][k] * inv;
+        a[r][k] = f;
+#pragma unroll
+        for (int c = k + 1; c < 4; ++c) a[r][c] -= f * a[k][c];
+      }
+    }
+    return ok;
+  }
+  RD_HD void solve(const T b[4], T x[4]) const {
+    T y[4] = {b[0], b[1], b[2], b[3]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+      for (int r = k + 1; r < 4; ++r) {
+        bool sw = (piv[k] == r);
+        T s = y[k], t = y[r];
+        y[k] = sw ? t : s;
+        y[r] = sw ? s : t;
+      }
+    }
+#pragma unroll
+    for (int r = 1; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < r; ++c) y[r] -= a[r][c] * y[c];
+#pragma unroll
+    for (int r = 3; r >= 0; --r) {
+#pragma unroll
+      for (int c = r + 1; c < 4; ++c) y[r] -= a[r][c] * y[c];
+      y[r] = y[r] * rdiag[r];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] = y[k];
+  }
+};
+
+// Linearisation of one triangle and its N-scheme shares (Sec. 3.2, 3.3.1).
+template <class T>
+struct TriLin {
+  RoeState<T> r;
+  NodeSys<T> nd[3];
+  LU4<T> lu;
+  T phiT[4];
+  T phiN[3][4];
+};
+
+template <class T>
+RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3],
+                                         T gamma, T eps, TriLin<T>& L) {
+  const T third = T(1) / T(3);
+  T Zb[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Zb[k] = (Z[0][k] + Z[1][k] + Z[2][k]) * third;
+  RoeState<T>& r = L.r;
+  r.g1 = gamma - T(1);
+  T iz = T(1) / Zb[0];
+  r.u = Zb[1] * iz;
+  r.v = Zb[2] * iz;
+  r.h = Zb[3] * iz;
+  r.q2h = (r.u * r.u + r.v * r.v) * T(0.5);
+  T c2 = r.g1 * (r.h - r.q2h);
+  if (!(c2 > T(0))) return ST_ROE;
+  r.c = sqrt(c2);
+  r.ic2 = T(1) / c2;
+  r.ic2h = r.ic2 * T(0.5);
+
+  // phi^T = dF/dZ(Zbar) gx + dG/dZ(Zbar) gy, g = sum_i (n_i / 2) Z_i
+  T gx[4] = {T(0), T(0), T(0), T(0)}, gy[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T ax = nx[i] * hl[i], ay = ny[i] * hl[i];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      gx[k] += ax * Z[i][k];
+      gy[k] += ay * Z[i][k];
+    }
+  }
+  {
+    T g = r.g1 / gamma;
+    L.phiT[0] = Zb[1] * gx[0] + Zb[0] * gx[1] + Zb[2] * gy[0] + Zb[0] * gy[2];
+    L.phiT[1] = g * Zb[3] * gx[0] + (T(2) - g) * Zb[1] * gx[1] - g * Zb[2] * gx[2] + g * Zb[0] * gx[3] +
+                Zb[2] * gy[1] + Zb[1] * gy[2];
+    L.phiT[2] = Zb[2] * gx[1] + Zb[1] * gx[2] + g * Zb[3] * gy[0] - g * Zb[1] * gy[1] +
+                (T(2) - g) * Zb[2] * gy[2] + g * Zb[0] * gy[3];
+    L.phiT[3] = Zb[3] * gx[1] + Zb[1] * gx[3] + Zb[3] * gy[2] + Zb[2] * gy[3];
+  }
+
+  // eigen-split per node (App. A), regularised |lambda| below delta
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    NodeSys<T>& n = L.nd[i];
+    n.nx = nx[i];
+    n.ny = ny[i];
+    n.w = r.u * n.nx + r.v * n.ny;
+    n.uperp = r.v * n.nx - r.u * n.ny;
+    T delta = eps * r.c * hl[i];
+    T la[3] = {(n.w + r.c) * hl[i], (n.w - r.c) * hl[i], n.w * hl[i]};
+    T i2d = T(0);
+    if (fabs(la[0]) < delta || fabs(la[1]) < delta || fabs(la[2]) < delta) i2d = T(0.5) / delta;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      T ab = abs_reg(la[k], delta, i2d);
+      n.lp[k] = (la[k] + ab) * T(0.5);
+      n.lm[k] = (la[k] - ab) * T(0.5);
+    }
+  }
+
+  // sum_j K_j^- column by column, then LU
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    T e[4] = {T(q == 0), T(q == 1), T(q == 2), T(q == 3)};
+    T col[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      T o[4];
+      Kpm_apply<T, false>(r, L.nd[j], e, o);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) col[k] += o[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) L.lu.a[k][q] = col[k];
+  }
+  if (!L.lu.factor()) return ST_SINGULAR;
+
+  // conservative linearised states W^_i = dW/dZ(Zbar) Z_i and sum_j K_j^- W^_j
+  T Wh[3][4];
+  T S[4] = {T(0), T(0), T(0), T(0)};
+  {
+    T g = r.g1 / gamma, ig = T(1) / gamma;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Wh[i][0] = T(2) * Zb[0] * Z[i][0];
+      Wh[i][1] = Zb[1] * Z[i][0] + Zb[0] * Z[i][1];
+      Wh[i][2] = Zb[2] * Z[i][0] + Zb[0] * Z[i][2];
+      Wh[i][3] = (Zb[3] * Z[i][0] + Zb[0] * Z[i][3]) * ig + g * (Zb[1] * Z[i][1] + Zb[2] * Z[i][2]);
+      T o[4];
+      Kpm_apply<T, false>(r, L.nd[i], Wh[i], o);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) S[k] += o[k];
+    }
+  }
+  // N scheme: phi_i^N = K_i^+ (W^_i - N^ sum_j K_j^- W^_j)
+  T win[4];
+  L.lu.solve(S, win);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T d[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d[k] = Wh[i][k] - win[k];
+    Kpm_apply<T, true>(r, L.nd[i], d, L.phiN[i]);
+  }
+  return 0;
+}
+
+// beta_i x = -K_i^+ N^ x for the three nodes (Sec. 3.3.2).
+template <class T>
+RD_HD void lda_apply(const TriLin<T>& L, const T x[4], T out[3][4]) {
+  T y[4];
+  L.lu.solve(x, y);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T o[4];
+    Kpm_apply<T, true>(L.r, L.nd[i], y, o);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[i][k] = -o[k];
+  }
+}
+
+// Theta_kk = |tot_k| / max(sum_i |N_ik|, |tot_k|) (0/0 -> 0); out = Theta N + (1-Theta) LDA.
+template <class T>
+RD_HD void blend(const T tot[4], const T N[3][4], const T lda[3][4], T out[3][4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T num = fabs(tot[k]);
+    T den = fabs(N[0][k]) + fabs(N[1][k]) + fabs(N[2][k]);
+    den = den > num ? den : num;
+    T th = den > T(0) ? num / den : T(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) out[i][k] = th * N[i][k] + (T(1) - th) * lda[i][k];
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void load_tri(int t, int nt, const int* __restrict__ tri, const DevGeo<T>& g,
+                                         int v[3], T nx[3], T ny[3], T hl[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    v[c] = __ldg(tri + (size_t)c * nt + t);
+    nx[c] = __ldg(g.nx + (size_t)c * nt + t);
+    ny[c] = __ldg(g.ny + (size_t)c * nt + t);
+    hl[c] = __ldg(g.hl + (size_t)c * nt + t);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void load_vec4(const T* __restrict__ A, size_t nv, int i, T out[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) out[k] = __ldg(A + k * nv + i);
+}
+
+// ---------------------------------------------------------------------------
+// Per-triangle bodies (host+device: the same code is instantiated on a
+// counting scalar type to count the kernels' floating-point operations).
+// ---------------------------------------------------------------------------
+
+// Stage 1 (and forward Euler) shares at W^n.  SCHEME: RD_N1 -> phi^N,
+// RD_LDA2 -> phi^LDA, RD_B2 -> phi^B (Sec. 3.3).  rec (two-stage schemes):
+// phi^N_0..2 and phi^T at W^n, reused by stage 2.  Returns an ST_* status.
+template <class T, int SCHEME>
+RD_HD int stage1_body(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3], T gamma, T eps,
+                      T out[3][4], T rec[16]) {
+  TriLin<T> L;
+  int st = linearise(Z, nx, ny, hl, gamma, eps, L);
+  if (st) return st;
+  if (SCHEME == RD_N1) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) out[i][k] = L.phiN[i][k];
+    return 0;
+  }
+  T lda[3][4];
+  lda_apply(L, L.phiT, lda);
+  if (SCHEME == RD_LDA2) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) out[i][k] = lda[i][k];
+  } else {
+    blend(L.phiT, L.phiN, lda, out);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) rec[4 * i + k] = L.phiN[i][k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) rec[12 + k] = L.phiT[k];
+  return 0;
+}
+
+// Stage 2 (Sec. 3.4): total residuals at (W^n, W*).
+//   Phi^N_i   = |T|/3 (W*_i - W^n_i)/dt + (phi^N_i(W*) + phi^N_i(W^n)) / 2
+//   Phi^T     = sum_j |T|/3 (W*_j - W^n_j)/dt + (phi^T(W^n) + phi^T(W*)) / 2
+//   Phi^LDA_i = beta_i(W*) Phi^T     (m^LDA_ij = |T|/3 beta_i, global lumping)
+//   Phi_i     = Theta Phi^N_i + (I - Theta) Phi^LDA_i, Theta from (Phi^T, Phi^N)
+template <class T, int SCHEME>
+RD_HD int stage2_body(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], const T rec[16], const T nx[3],
+                      const T ny[3], const T hl[3], T area, T dt, T gamma, T eps, T out[3][4]) {
+  TriLin<T> L;
+  int st = linearise(Zs, nx, ny, hl, gamma, eps, L);
+  if (st) return st;
+  T a3 = area * (T(1) / T(3));
+  T idt = T(1) / dt;
+  T PhiN[3][4], PhiT[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) PhiT[k] = T(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      T m = a3 * ((Ws[i][k] - Wn[i][k]) * idt);
+      PhiN[i][k] = m + (L.phiN[i][k] + rec[4 * i + k]) * T(0.5);
+      PhiT[k] += m;
+    }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) PhiT[k] += (rec[12 + k] + L.phiT[k]) * T(0.5);
+  T lda[3][4];
+  lda_apply(L, PhiT, lda);
+  if (SCHEME == RD_LDA2) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) out[i][k] = lda[i][k];
+  } else {
+    blend(PhiT, PhiN, lda, out);
+  }
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Stage-1 triangle kernel: share [nt][3][4]; rec [nt][16] (two-stage only);
+// cfl [nt] = l_max^T max_j (|v_j| + c_j).
+// ---------------------------------------------------------------------------
+template <class T, int SCHEME>
+__global__ void __launch_bounds__(128) k_tri_stage1(int nt, int nv, const int* __restrict__ tri, DevGeo<T> g,
+                                                    const T* __restrict__ Z, const T* __restrict__ spd,
+                                                    T gamma, T eps, T* __restrict__ share,
+                                                    T* __restrict__ rec, T* __restrict__ cfl, DevCtl* ctl) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt || ctl->stop) return;
+  int v[3];
+  T nx[3], ny[3], hl[3], Zc[3][4];
+  load_tri(t, nt, tri, g, v, nx, ny, hl);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) load_vec4(Z, (size_t)nv, v[c], Zc[c]);
+  {
+    T s0 = __ldg(spd + v[0]), s1 = __ldg(spd + v[1]), s2 = __ldg(spd + v[2]);
+    T lam = s0 > s1 ? s0 : s1;
+    lam = lam > s2 ? lam : s2;
+    cfl[t] = __ldg(g.lmax + t) * lam;
+  }
+  T out[3][4], r[16];
+  int st = stage1_body<T, SCHEME>(Zc, nx, ny, hl, gamma, eps, out, r);
+  if (st) {
+    atomicOr(&ctl->status, st);
+    return;
+  }
+  if (SCHEME != RD_N1) {
+    T* rp = rec + (size_t)t * 16;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) rp[k] = r[k];
+  }
+  T* sp = share + (size_t)t * 12;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sp[4 * i + k] = out[i][k];
+}
+
+// Inspection variant: phi^N, phi^LDA, phi^B (each [nt][3][4]) and the CFL term.
+template <class T>
+__global__ void __launch_bounds__(128) k_tri_terms(int nt, int nv, const int* __restrict__ tri, DevGeo<T> g,
+                                                   const T* __restrict__ Z, const T* __restrict__ spd,
+                                                   T gamma, T eps, T* __restrict__ out, T* __restrict__ cfl,
+                                                   DevCtl* ctl) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  int v[3];
+  T nx[3], ny[3], hl[3], Zc[3][4];
+  load_tri(t, nt, tri, g, v, nx, ny, hl);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) load_vec4(Z, (size_t)nv, v[c], Zc[c]);
+  T s0 = spd[v[0]], s1 = spd[v[1]], s2 = spd[v[2]];
+  T lam = s0 > s1 ? s0 : s1;
+  lam = lam > s2 ? lam : s2;
+  cfl[t] = g.lmax[t] * lam;
+  TriLin<T> L;
+  int st = linearise(Zc, nx, ny, hl, gamma, eps, L);
+  if (st) {
+    atomicOr(&ctl->status, st);
+    return;
+  }
+  T lda[3][4], b[3][4];
+  lda_apply(L, L.phiT, lda);
+  blend(L.phiT, L.phiN, lda, b);
+  size_t s3 = (size_t)nt * 12;
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 4; ++k) {
+      out[(size_t)t * 12 + 4 * i + k] = L.phiN[i][k];
+      out[s3 + (size_t)t * 12 + 4 * i + k] = lda[i][k];
+      out[2 * s3 + (size_t)t * 12 + 4 * i + k] = b[i][k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Vertex gather of stage-1 shares and the CFL sums; dt by a two-level min.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T warp_min(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    T w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w < v ? w : v;
+  }
+  return v;
+}
+
+template <class T, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_gather_cfl(int nv, const int* __restrict__ ptr, const int* __restrict__ ent,
+                                                      const T* __restrict__ share, const T* __restrict__ cfl,
+                                                      const T* __restrict__ V, T* __restrict__ R1,
+                                                      T* __restrict__ partial, T cflnum, DevCtl* ctl) {
+  __shared__ T red[BLOCK / 32];
+  __shared__ bool last;
+  if (ctl->stop) return;
+  int i = blockIdx.x * BLOCK + threadIdx.x;
+  T ratio = T(INFINITY);
+  if (i < nv) {
+    T r[4] = {T(0), T(0), T(0), T(0)};
+    T sig = T(0);
+    int e0 = __ldg(ptr + i), e1 = __ldg(ptr + i + 1);
+    for (int e = e0; e < e1; ++e) {
+      int te = __ldg(ent + e);
+      const T* sp = share + (size_t)te * 4;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) r[k] += __ldg(sp + k);
+      sig += __ldg(cfl + te / 3);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) R1[(size_t)k * nv + i] = r[k];
+    ratio = T(2) * __ldg(V + i) / sig;
+  }
+  ratio = warp_min(ratio);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ratio;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    T x = threadIdx.x < BLOCK / 32 ? red[threadIdx.x] : T(INFINITY);
+    x = warp_min(x);
+    if (threadIdx.x == 0) {
+      partial[blockIdx.x] = x;
+      __threadfence();
+      unsigned int tk = atomicAdd(&ctl->ticket, 1u);
+      last = (tk == gridDim.x - 1);
+    }
+  }
+  __syncthreads();
+  if (!last) return;
+  // last block: min over all block minima
+  __threadfence();
+  T m = T(INFINITY);
+  for (int b = threadIdx.x; b < gridDim.x; b += BLOCK) {
+    T x = ((volatile T*)partial)[b];
+    m = x < m ? x : m;
+  }
+  m = warp_min(m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    T x = threadIdx.x < BLOCK / 32 ? red[threadIdx.x] : T(INFINITY);
+    x = warp_min(x);
+    if (threadIdx.x == 0) {
+      double dt = (double)(cflnum * x);
+      if (ctl->t_end > 0.0) {
+        double rem = ctl->t_end - ctl->t;
+        if (dt > rem) dt = rem;
+        if (!(rem > 0.0)) ctl->stop = 1;  // t_end reached: the rest of this step is a no-op
+      }
+      ctl->dt = (double)(T)dt;
+      ctl->ticket = 0u;
+    }
+  }
+}
+
+// Vertex state -> parameter vector Z and |v| + c; returns false if non-physical.
+template <class T>
+__device__ __forceinline__ bool vertex_Z(const T W[4], T gamma, T Z[4], T& spd) {
+  T rho = W[0];
+  if (!(rho > T(0))) return false;
+  T u = W[1] / rho, v = W[2] / rho;
+  T p = (gamma - T(1)) * (W[3] - T(0.5) * rho * (u * u + v * v));
+  if (!(p > T(0))) return false;
+  T h = (W[3] + p) / rho;
+  T sr = sqrt(rho);
+  Z[0] = sr;
+  Z[1] = sr * u;
+  Z[2] = sr * v;
+  Z[3] = sr * h;
+  spd = sqrt(u * u + v * v) + sqrt(gamma * p / rho);
+  return true;
+}
+
+// W_out = W_in - dt/V R; Z_out = Z(W_out); spd_out (nullable) = |v| + c.
+// If R2 != nullptr, W_in is W* and R = R2 gathered here from share (stage 2).
+template <class T>
+__global__ void __launch_bounds__(256) k_update(int nv, const T* __restrict__ Win, const T* __restrict__ R,
+                                                const int* __restrict__ ptr, const int* __restrict__ ent,
+                                                const T* __restrict__ share, const T* __restrict__ V, T gamma,
+                                                T* __restrict__ Wout, T* __restrict__ Zout, T* __restrict__ spdout,
+                                                DevCtl* ctl) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nv || ctl->stop) return;
+  T r[4];
+  if (share) {
+    r[0] = r[1] = r[2] = r[3] = T(0);
+    int e0 = __ldg(ptr + i), e1 = __ldg(ptr + i + 1);
+    for (int e = e0; e < e1; ++e) {
+      const T* sp = share + (size_t)__ldg(ent + e) * 4;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) r[k] += __ldg(sp + k);
+    }
+  } else {
+    load_vec4(R, (size_t)nv, i, r);
+  }
+  T dt = (T)ctl->dt;
+  T f = dt / __ldg(V + i);
+  T W[4], Z[4], spd;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) W[k] = __ldg(Win + (size_t)k * nv + i) - f * r[k];
+  bool ok = vertex_Z(W, gamma, Z, spd);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    Wout[(size_t)k * nv + i] = W[k];
+    Zout[(size_t)k * nv + i] = Z[k];
+  }
+  if (spdout) spdout[i] = spd;
+  if (!ok) {
+    atomicOr(&ctl->status, ST_NONPHYS_VERTEX);
+    ctl->stop = 1;
+  }
+}
+
+// Z and |v|+c of a freshly uploaded state.
+template <class T>
+__global__ void k_prepare(int nv, const T* __restrict__ W, T gamma, T* __restrict__ Z, T* __restrict__ spd,
+                          DevCtl* ctl) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nv) return;
+  T w[4], z[4], s;
+  load_vec4(W, (size_t)nv, i, w);
+  bool ok = vertex_Z(w, gamma, z, s);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Z[(size_t)k * nv + i] = z[k];
+  spd[i] = s;
+  if (!ok) atomicOr(&ctl->status, ST_NONPHYS_VERTEX);
+}
+
+// ---------------------------------------------------------------------------
+// Stage-2 triangle kernel: total residuals at (W^n, W*) -> share [nt][3][4].
+// ---------------------------------------------------------------------------
+template <class T, int SCHEME>
+__global__ void __launch_bounds__(128) k_tri_stage2(int nt, int nv, const int* __restrict__ tri, DevGeo<T> g,
+                                                    const T* __restrict__ Zs, const T* __restrict__ Wn,
+                                                    const T* __restrict__ Ws, const T* __restrict__ rec,
+                                                    T gamma, T eps, T* __restrict__ share, DevCtl* ctl) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt || ctl->stop) return;
+  int v[3];
+  T nx[3], ny[3], hl[3], Zc[3][4], wn[3][4], ws[3][4], r[16];
+  load_tri(t, nt, tri, g, v, nx, ny, hl);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    load_vec4(Zs, (size_t)nv, v[c], Zc[c]);
+    load_vec4(Wn, (size_t)nv, v[c], wn[c]);
+    load_vec4(Ws, (size_t)nv, v[c], ws[c]);
+  }
+  const T* rp = rec + (size_t)t * 16;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) r[k] = __ldg(rp + k);
+  T out[3][4];
+  int st = stage2_body<T, SCHEME>(Zc, wn, ws, r, nx, ny, hl, __ldg(g.area + t), (T)ctl->dt, gamma, eps, out);
+  if (st) {
+    atomicOr(&ctl->status, st);
+    return;
+  }
+  T* sp = share + (size_t)t * 12;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sp[4 * i + k] = out[i][k];
+}
+
+// One thread: commit the step if nothing went wrong.
+static __global__ void k_commit(DevCtl* ctl) {
+  if (ctl->stop) return;
+  if (ctl->status) {
+    ctl->stop = 1;
+    return;
+  }
+  ctl->t += ctl->dt;
+  ctl->steps += 1;
+  if (ctl->t_end > 0.0 && ctl->t >= ctl->t_end) ctl->stop = 1;
+}
+
+// Conserved totals: per-block partial sums of V_i W_i (fixed order), then a
+// one-block pass in block order -> out[4] (double).
+template <class T, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_conserved_partial(int nv, const T* __restrict__ W, const T* __restrict__ V,
+                                                             double* __restrict__ partial) {
+  __shared__ double red[4][BLOCK];
+  int i = blockIdx.x * BLOCK + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = i < nv ? (double)V[i] * (double)W[(size_t)k * nv + i] : 0.0;
+  __syncthreads();
+  for (int s = BLOCK / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) partial[(size_t)blockIdx.x * 4 + k] = red[k][0];
+}
+
+static __global__ void k_conserved_final(int nblocks, const double* __restrict__ partial, double* __restrict__ out) {
+  if (threadIdx.x < 4) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * 4 + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+// Caller-order double state -> internal-order T state (and back).
+template <class T>
+__global__ void k_permute_in(int nv, const int* __restrict__ vperm, const double* __restrict__ src,
+                             T* __restrict__ dst, DevCtl* ctl) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nv) return;
+  int j = __ldg(vperm + i);
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double x = src[(size_t)k * nv + j];
+    ok = ok && isfinite(x);
+    dst[(size_t)k * nv + i] = (T)x;
+  }
+  if (!ok) atomicOr(&ctl->status, ST_NONPHYS_VERTEX);
+}
+
+template <class T>
+__global__ void k_permute_out(int nv, const int* __restrict__ vperm, const T* __restrict__ src,
+                              double* __restrict__ dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nv) return;
+  int j = __ldg(vperm + i);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) dst[(size_t)k * nv + j] = (double)src[(size_t)k * nv + i];
+}
+
+template <class Tsrc, class Tdst>
+__global__ void k_convert(size_t n, const Tsrc* __restrict__ a, Tdst* __restrict__ b) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (Tdst)a[i];
+}
+
+}  // namespace rd

@@ -1,0 +1,94 @@
+"""C ABI checks that need no GPU: the library loads, exports every function
+include/rd.h declares, and rejects invalid input before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1705_02028_gb300 import binding, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "rd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"^\s*(?:const\s+)?[a-z_][a-z_0-9]*\s*\**\s*\b(rd_[a-z_0-9]+)\s*\(", src, flags=re.M))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return binding.load()
+
+
+def test_header_declares_the_api():
+    names = declared_functions()
+    for n in ("rd_mesh_create", "rd_state_init", "rd_step", "rd_run", "rd_get_state", "rd_conserved_totals",
+              "rd_batch_create", "rd_batch_run"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(declared_functions()) <= set(binding._SIGS)
+
+
+def test_strerror_and_version(lib):
+    assert lib.rd_version() >= 1
+    for code in range(7):
+        assert isinstance(lib.rd_strerror(code), bytes) and lib.rd_strerror(code)
+
+
+def _create(lib, mesh, tri=None, shift="keep", xy=None):
+    xy = np.ascontiguousarray(mesh.xy if xy is None else xy)
+    tri = np.ascontiguousarray(mesh.tri if tri is None else tri, dtype=np.int32)
+    sh = mesh.shift if isinstance(shift, str) else shift
+    sh = None if sh is None else np.ascontiguousarray(sh, dtype=np.int8)
+    h = ctypes.c_void_p()
+    rc = lib.rd_mesh_create(xy.shape[0], binding._ptr(xy), tri.shape[0], binding._ptr(tri, ctypes.c_int32),
+                            None if sh is None else binding._ptr(sh, ctypes.c_int8), mesh.Lx, mesh.Ly, 1, None,
+                            ctypes.byref(h))
+    return rc, h
+
+
+def test_mesh_validation_rejects_bad_input_before_any_device_work(lib):
+    mesh = inputs.periodic_grid(5)
+    bad = mesh.tri.copy()
+    bad[3, 1] = mesh.nv                       # index out of range
+    assert _create(lib, mesh, tri=bad)[0] == binding.RD_EINVAL
+    cw = mesh.tri[:, [0, 2, 1]]               # clockwise triangles
+    assert _create(lib, mesh, tri=cw)[0] == binding.RD_EINVAL
+    sh = mesh.shift.copy()
+    sh[0, 0, 0] = 2                           # image shift outside {-1,0,1}
+    assert _create(lib, mesh, shift=sh)[0] == binding.RD_EINVAL
+    assert _create(lib, mesh, shift=None)[0] == binding.RD_EINVAL   # periodic triangles without shifts
+    lonely = np.vstack([mesh.xy, [[0.5, 0.5]]])   # a vertex in no triangle
+    assert _create(lib, mesh, xy=lonely)[0] == binding.RD_EINVAL
+    nan = mesh.xy.copy()
+    nan[2, 0] = np.nan
+    assert _create(lib, mesh, xy=nan)[0] == binding.RD_EINVAL
+
+
+def test_null_and_parameter_checks(lib):
+    h = ctypes.c_void_p()
+    p = binding.Params(1, 0, 0.8, 1.4, 1e-6)
+    assert lib.rd_state_init(None, None, ctypes.byref(p), ctypes.byref(h)) == binding.RD_EINVAL
+    assert lib.rd_step(None, None) == binding.RD_EINVAL
+    assert lib.rd_run(None, 3, 0.0, None) == binding.RD_EINVAL
+    assert lib.rd_batch_run(None, 3) != binding.RD_OK
+    assert lib.rd_set_allocator(binding.ALLOC_FN(lambda a, b, c: None), ctypes.cast(None, binding.FREE_FN),
+                                None) == binding.RD_EINVAL
+
+
+def test_flop_count_of_the_triangle_kernels(lib):
+    """The per-triangle code is instantiated on a counting type (no GPU needed)."""
+    n1 = binding.count_flops("N1", 1)
+    b1 = binding.count_flops("B2", 1)
+    b2 = binding.count_flops("B2", 2)
+    assert n1["sqrt"] == 1 and b1["sqrt"] == 1            # one sqrt per Roe state
+    assert 500 < n1["total"] < b1["total"] < b2["total"] < 3000
+    assert b1["div"] <= 20 and b2["div"] <= 20

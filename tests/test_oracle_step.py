@@ -111,3 +111,23 @@ def test_nonphysical_state_is_rejected():
     W0[3, 5] = -1.0
     with pytest.raises(oracle.OracleError):
         oracle.run(mesh, W0, "B2", nsteps=1)
+
+
+def test_b2_amplifies_round_off_on_sod_like_state():
+    """Evidence for the parity policy: on the Sod-like state the blended two-stage
+    scheme (Theta from the total residuals, Sec. 3.4) amplifies round-off -- the
+    oracle's own double and long-double runs part -- while N1 and LDA2 stay at
+    round-off.  On the smooth KHI state B2 stays at round-off too."""
+    mesh = inputs.periodic_grid(32, relabel_seed=6)
+    W0 = inputs.sod_like_state(mesh)
+
+    def floor(scheme, n, W=W0):
+        a, _ = oracle.run(mesh, W, scheme, nsteps=n, nthreads=4)
+        b, _ = oracle.run(mesh, W, scheme, nsteps=n, nthreads=4, long_double=True)
+        sc = np.maximum(np.abs(b).max(axis=1), np.abs(b[3]).max())
+        return float((np.abs(a - b).max(axis=1) / sc).max())
+
+    assert floor("N1", 60) < 1e-14
+    assert floor("B2", 15) < 1e-13
+    assert floor("B2", 60) > 1e-8
+    assert floor("B2", 60, inputs.khi_state(mesh)) < 1e-13
