@@ -48,10 +48,15 @@ def test_stage1_shares_element_by_element(rd, state):
     rho, u, v, p = inputs.primitives(W)
     spd = np.hypot(u, v) + np.sqrt(1.4 * p / rho)
     cfl_ref = g["lmax"] * spd[mesh.tri].max(axis=1)
+    # Per-triangle shares come out of a 4x4 solve whose condition number reaches
+    # ~1e3 on these states, so their round-off is ~1e3 eps of the largest
+    # intermediate K_i W^_i (10-100x the largest share): the oracle's own double
+    # shares differ from its long-double ones by up to 5.4e-13 of max|phi^N| on
+    # the KHI state.  Tolerance: 1e-11 of max|phi^N|.
+    scale = np.abs(ref["phiN"]).max()
     for which, key in (("N", "phiN"), ("LDA", "phiLDA"), ("B", "phiB")):
         out, cfl = s.triangle_shares(which)
-        scale = np.abs(ref["phiN"]).max()
-        assert np.abs(out - ref[key]).max() <= 1e-12 * scale, which
+        assert np.abs(out - ref[key]).max() <= 1e-11 * scale, which
     assert np.allclose(cfl, cfl_ref, rtol=1e-14)
 
 
