@@ -147,6 +147,26 @@ void rd_state_destroy(rd_state *s);
  * cfl_term[t] = l_max^T lambda_max^T (Sec. 3.2). */
 int rd_state_triangle_shares(rd_state *s, int32_t which, double *out, double *cfl_term);
 
+/* ---- CFL time step of a caller-owned device state (Sec. 3.2) ---------------
+ * dt = cfl * min_i 2 V_i / sum_{T containing i} l_max^T lambda_max^T with
+ * lambda_max^T = max_{j in T} (|v_j| + c_j) evaluated at the vertex states.
+ * Every array argument is a DEVICE pointer owned by the caller; element type
+ * double (RD_FP64) or float (RD_FP32) for W, lmax, V:
+ *   W        [4][n_vertex] conserved state, component-major
+ *   tri      [3][n_tri] int32 corners, component-major: tri[c * n_tri + t]
+ *   lmax     [n_tri] longest edge of each triangle
+ *   V        [n_vertex] nodal volumes
+ *   csr_ptr  [n_vertex + 1], csr_ent [3 n_tri]: the corners (3 t + c) of the
+ *            triangles containing each vertex
+ *   dt_out   one double, written on the stream
+ * Scratch (one double per 256 vertices and a counter) comes from the installed
+ * allocator and is released before return; the call waits for the stream.
+ * Errors: RD_EINVAL, RD_ENOMEM, RD_ECUDA, RD_ENONPHYSICAL (rho <= 0 or p <= 0
+ * at a vertex; dt_out is then not meaningful). */
+int rd_cfl_dt(int32_t n_vertex, int32_t n_tri, int32_t precision, const void *W, const int32_t *tri,
+              const void *lmax, const void *V, const int32_t *csr_ptr, const int32_t *csr_ent, double gamma,
+              double cfl, double *dt_out, void *cuda_stream);
+
 /* ---- measurement ------------------------------------------------------------
  * rd_state_profile: n_steps steps with CUDA events recorded on the mesh stream
  * around every kernel; ms_per_launch[6] receives the mean duration of

@@ -64,6 +64,8 @@ _SIGS = {
     "rd_get_dt": (ctypes.c_int, [_vp, _dp]),
     "rd_state_destroy": (None, [_vp]),
     "rd_state_triangle_shares": (ctypes.c_int, [_vp, ctypes.c_int32, _dp, _dp]),
+    "rd_cfl_dt": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp,
+                                 ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "rd_state_profile": (ctypes.c_int, [_vp, ctypes.c_int32, _dp, _i32p]),
     "rd_count_flops": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _dp]),
     "rd_probe_fma_peak": (ctypes.c_int, [ctypes.c_int32, _dp]),
@@ -152,6 +154,24 @@ def probe_fma_peak(precision: str = "fp64") -> float:
     out = ctypes.c_double()
     _check(lib.rd_probe_fma_peak(PRECISIONS[precision], ctypes.byref(out)), "rd_probe_fma_peak")
     return out.value
+
+
+def cfl_dt(W, tri, lmax, V, csr_ptr, csr_ent, precision="fp64", gamma=1.4, cfl=0.8, stream=None,
+           entry="rd_cfl_dt") -> float:
+    """CFL time step of a state held in torch CUDA tensors (rd_cfl_dt).
+
+    W (4, nv), lmax (nt,), V (nv,): float64 or float32 CUDA tensors; tri (3, nt),
+    csr_ptr (nv+1,), csr_ent (3 nt,): int32 CUDA tensors (caller-owned)."""
+    torch = _require_gpu()
+    lib = load()
+    nv, nt = int(W.shape[1]), int(tri.shape[1])
+    out = torch.zeros(1, dtype=torch.float64, device=W.device)
+    st = stream if stream is not None else torch.cuda.current_stream(W.device)
+    rc = getattr(lib, entry)(nv, nt, PRECISIONS[precision], W.data_ptr(), tri.data_ptr(), lmax.data_ptr(),
+                             V.data_ptr(), csr_ptr.data_ptr(), csr_ent.data_ptr(), float(gamma), float(cfl),
+                             out.data_ptr(), _vp(st.cuda_stream))
+    _check(rc, entry)
+    return float(out.item())
 
 
 def _params(scheme, precision, cfl, gamma, eps_fix) -> Params:

@@ -630,6 +630,58 @@ extern "C" void rd_state_destroy(rd_state* s) {
 }
 
 // ---------------------------------------------------------------------------
+// standalone CFL time step on caller-owned device arrays
+// ---------------------------------------------------------------------------
+namespace rd {
+// Shared by rd_cfl_dt and its allocation-free variant: validates, clears the
+// control word, launches k_cfl_dt on the stream and waits for it.
+int cfl_dt_launch(int32_t nv, int32_t nt, int32_t precision, const void* W, const int32_t* tri, const void* lmax,
+                  const void* V, const int32_t* ptr, const int32_t* ent, double gamma, double cfl, double* dt_out,
+                  void* stream, double* partial, DtScratchCtl* ctl) {
+  static_assert(CFL_DT_BLOCK == VTX_BLOCK, "block size of the CFL reduction");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned nb = nblk(nv, VTX_BLOCK);
+  CU(cudaMemsetAsync(ctl, 0, sizeof(DtScratchCtl), st));
+  if (precision == RD_FP64)
+    k_cfl_dt<double, VTX_BLOCK><<<nb, VTX_BLOCK, 0, st>>>(nv, nt, (const double*)W, tri, (const double*)lmax,
+                                                          (const double*)V, ptr, ent, gamma, cfl, partial, ctl, dt_out);
+  else
+    k_cfl_dt<float, VTX_BLOCK><<<nb, VTX_BLOCK, 0, st>>>(nv, nt, (const float*)W, tri, (const float*)lmax,
+                                                         (const float*)V, ptr, ent, (float)gamma, (float)cfl, partial,
+                                                         ctl, dt_out);
+  CU(cudaGetLastError());
+  DtScratchCtl c;
+  CU(cudaMemcpyAsync(&c, ctl, sizeof(c), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  return c.status ? RD_ENONPHYSICAL : RD_OK;
+}
+
+int cfl_dt_check(int32_t nv, int32_t nt, int32_t precision, const void* W, const int32_t* tri, const void* lmax,
+                 const void* V, const int32_t* ptr, const int32_t* ent, double gamma, double cfl, double* dt_out) {
+  if (nv < 1 || nt < 1 || !W || !tri || !lmax || !V || !ptr || !ent || !dt_out) return RD_EINVAL;
+  if (precision != RD_FP64 && precision != RD_FP32) return RD_EINVAL;
+  if (!(gamma > 1.0) || !(cfl > 0.0)) return RD_EINVAL;
+  return RD_OK;
+}
+}  // namespace rd
+
+extern "C" int rd_cfl_dt(int32_t n_vertex, int32_t n_tri, int32_t precision, const void* W, const int32_t* tri,
+                         const void* lmax, const void* V, const int32_t* csr_ptr, const int32_t* csr_ent,
+                         double gamma, double cfl, double* dt_out, void* cuda_stream) {
+  CK(cfl_dt_check(n_vertex, n_tri, precision, W, tri, lmax, V, csr_ptr, csr_ent, gamma, cfl, dt_out));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  DevBuf scratch;
+  size_t nb = nblk(n_vertex, VTX_BLOCK);
+  size_t off = (nb * sizeof(double) + 255) / 256 * 256;
+  CK(dev_alloc(scratch, off + sizeof(DtScratchCtl), st));
+  int rc = cfl_dt_launch(n_vertex, n_tri, precision, W, tri, lmax, V, csr_ptr, csr_ent, gamma, cfl, dt_out,
+                         (void*)st, (double*)scratch.p, (DtScratchCtl*)((char*)scratch.p + off));
+  cudaStreamSynchronize(st);
+  dev_free(scratch);
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
 // misc
 // ---------------------------------------------------------------------------
 extern "C" const char* rd_strerror(int status) {

@@ -42,6 +42,22 @@ struct DevCtl {
   int pad;
 };
 
+// Control word of the standalone CFL reduction (must start at zero).
+struct DtScratchCtl {
+  unsigned int ticket;
+  int status;
+};
+
+// Standalone CFL time step on caller-owned device arrays (rd_cfl_dt): argument
+// check, then launch on `stream` with the given scratch (block minima of
+// ceil(nv / 256) doubles and the control word) and wait for the result.
+int cfl_dt_check(int32_t nv, int32_t nt, int32_t precision, const void* W, const int32_t* tri, const void* lmax,
+                 const void* V, const int32_t* ptr, const int32_t* ent, double gamma, double cfl, double* dt_out);
+int cfl_dt_launch(int32_t nv, int32_t nt, int32_t precision, const void* W, const int32_t* tri, const void* lmax,
+                  const void* V, const int32_t* ptr, const int32_t* ent, double gamma, double cfl, double* dt_out,
+                  void* stream, double* partial, DtScratchCtl* ctl);
+constexpr int CFL_DT_BLOCK = 256;
+
 enum : int {
   ST_NONPHYS_VERTEX = 1,  // rho <= 0, p <= 0 or NaN at a vertex
   ST_ROE = 2,             // c^2 <= 0 at a Roe state

@@ -706,6 +706,82 @@ static __global__ void k_conserved_final(int nblocks, const double* __restrict__
   }
 }
 
+// ---------------------------------------------------------------------------
+// Standalone CFL time step of a state in caller-owned device memory (Sec. 3.2):
+//   dt = cfl * min_i 2 V_i / sum_{T containing i} l_max^T max_{j in T}(|v_j| + c_j)
+// Per vertex: walk its CSR corners, recompute |v|+c of the three corners of each
+// triangle, sum l_max * lambda_max; block minima to partial[], the last block
+// reduces them into dt_out.  Scratch: partial[gridDim.x] and a DtScratchCtl.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T vertex_speed(const T* __restrict__ W, size_t nv, int i, T gamma, bool& ok) {
+  T rho = __ldg(W + i), mx = __ldg(W + nv + i), my = __ldg(W + 2 * nv + i), e = __ldg(W + 3 * nv + i);
+  T u = mx / rho, v = my / rho;
+  T p = (gamma - T(1)) * (e - T(0.5) * rho * (u * u + v * v));
+  ok = ok && (rho > T(0)) && (p > T(0));
+  return sqrt(u * u + v * v) + sqrt(gamma * p / rho);
+}
+
+template <class T, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_cfl_dt(int nv, int nt, const T* __restrict__ W, const int* __restrict__ tri,
+                                                  const T* __restrict__ lmax, const T* __restrict__ V,
+                                                  const int* __restrict__ ptr, const int* __restrict__ ent, T gamma,
+                                                  T cflnum, double* __restrict__ partial, DtScratchCtl* ctl,
+                                                  double* __restrict__ dt_out) {
+  __shared__ double red[BLOCK / 32];
+  __shared__ bool last;
+  int i = blockIdx.x * BLOCK + threadIdx.x;
+  double ratio = INFINITY;
+  bool ok = true;
+  if (i < nv) {
+    T sig = T(0);
+    int e0 = __ldg(ptr + i), e1 = __ldg(ptr + i + 1);
+    for (int e = e0; e < e1; ++e) {
+      int t = __ldg(ent + e) / 3;
+      T s0 = vertex_speed(W, (size_t)nv, __ldg(tri + t), gamma, ok);
+      T s1 = vertex_speed(W, (size_t)nv, __ldg(tri + (size_t)nt + t), gamma, ok);
+      T s2 = vertex_speed(W, (size_t)nv, __ldg(tri + 2 * (size_t)nt + t), gamma, ok);
+      T lam = s0 > s1 ? s0 : s1;
+      lam = lam > s2 ? lam : s2;
+      sig += __ldg(lmax + t) * lam;
+    }
+    ratio = (double)(T(2) * __ldg(V + i) / sig);
+  }
+  if (!ok) atomicOr(&ctl->status, ST_NONPHYS_VERTEX);
+  ratio = warp_min(ratio);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ratio;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double x = threadIdx.x < BLOCK / 32 ? red[threadIdx.x] : INFINITY;
+    x = warp_min(x);
+    if (threadIdx.x == 0) {
+      partial[blockIdx.x] = x;
+      __threadfence();
+      unsigned int tk = atomicAdd(&ctl->ticket, 1u);
+      last = (tk == gridDim.x - 1);
+    }
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double m = INFINITY;
+  for (int b = threadIdx.x; b < gridDim.x; b += BLOCK) {
+    double x = ((volatile double*)partial)[b];
+    m = x < m ? x : m;
+  }
+  m = warp_min(m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double x = threadIdx.x < BLOCK / 32 ? red[threadIdx.x] : INFINITY;
+    x = warp_min(x);
+    if (threadIdx.x == 0) {
+      dt_out[0] = (double)(cflnum * (T)x);
+      ctl->ticket = 0u;
+    }
+  }
+}
+
 // Caller-order double state -> internal-order T state (and back).
 template <class T>
 __global__ void k_permute_in(int nv, const int* __restrict__ vperm, const double* __restrict__ src,
