@@ -23,7 +23,7 @@
 // long double (round-off floor) and a forward-mode dual number (directional
 // derivatives for the adjoint checks).
 //
-// Readings of points where the paper is silent or garbled (listed in the design doc):
+// Readings of points where the paper is silent or garbled:
 //   (R1) K^{+-} act on the conservative linearised states W^_i = M(Zbar) Z_i,
 //        M = dW/dZ; the K matrix of App. A is the conservative Jacobian.
 //   (R2) n_i is the inward normal of the edge opposite node i, |n_i| = edge
