@@ -167,6 +167,32 @@ int rd_cfl_dt(int32_t n_vertex, int32_t n_tri, int32_t precision, const void *W,
               const void *lmax, const void *V, const int32_t *csr_ptr, const int32_t *csr_ent, double gamma,
               double cfl, double *dt_out, void *cuda_stream);
 
+/* Allocation-free variant of rd_cfl_dt.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory at the
+ * moment they need a time step -- code whose device heap is owned by another
+ * allocator (for example a caching allocator that has reserved the memory),
+ * code that must not trigger cudaMalloc's implicit device synchronisation, or
+ * latency-critical loops that may not allocate at all.  Same arguments, same
+ * kernel and same result as rd_cfl_dt; it calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *   - Scratch is a fixed array built into the library (512 KiB of block minima
+ *     plus an 8-byte control word), held by every device that loads the
+ *     library until the process exits.
+ *   - Limit: n_vertex <= 16,777,216 (65536 blocks of 256 vertices); larger
+ *     meshes are rejected with RD_EINVAL before any device work.
+ *   - The first call on a device, with that device current, looks up the
+ *     device address of the array (cudaGetSymbolAddress) and caches it; make
+ *     that first call before any stream capture.  Call it with the device
+ *     that holds the arrays current.
+ *   - Every call shares the array, which keeps the last call's contents; the
+ *     control word is cleared at the start of each call.  Calls whose device
+ *     work overlaps (other streams, other host threads) race on the array and
+ *     must be serialised by the caller.
+ *   - Waits for the stream before returning, like rd_cfl_dt. */
+int rd_cfl_dt_noalloc(int32_t n_vertex, int32_t n_tri, int32_t precision, const void *W, const int32_t *tri,
+                      const void *lmax, const void *V, const int32_t *csr_ptr, const int32_t *csr_ent,
+                      double gamma, double cfl, double *dt_out, void *cuda_stream);
+
 /* ---- measurement ------------------------------------------------------------
  * rd_state_profile: n_steps steps with CUDA events recorded on the mesh stream
  * around every kernel; ms_per_launch[6] receives the mean duration of

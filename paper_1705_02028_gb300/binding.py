@@ -66,6 +66,8 @@ _SIGS = {
     "rd_state_triangle_shares": (ctypes.c_int, [_vp, ctypes.c_int32, _dp, _dp]),
     "rd_cfl_dt": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp,
                                  ctypes.c_double, ctypes.c_double, _vp, _vp]),
+    "rd_cfl_dt_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp,
+                                         _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "rd_state_profile": (ctypes.c_int, [_vp, ctypes.c_int32, _dp, _i32p]),
     "rd_count_flops": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _dp]),
     "rd_probe_fma_peak": (ctypes.c_int, [ctypes.c_int32, _dp]),
