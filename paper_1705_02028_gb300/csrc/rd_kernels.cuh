@@ -43,13 +43,15 @@ struct DevGeo {
 
 template <class T>
 struct RoeState {
-  T u, v, h, c, q2h, ic2, ic2h, g1;
+  T u, v, h, c, q2h, ic2, ic2h, i2c, g1, alpha, g1u, g1v;
 };
 
+// Per node i: unit normal, w = u.n, and for K_i^+ ([0]) and K_i^- ([1]) the
+// four numbers of the rank-two form below.
 template <class T>
 struct NodeSys {
-  T nx, ny, w, uperp;  // unit normal, u.n, v nx - u ny
-  T lp[3], lm[3];      // Lambda^+ and Lambda^- for (w+c, w-c, w) times |n|/2
+  T nx, ny, w;
+  T l3[2], s1[2], s2[2], hp[2];
 };
 
 // Regularised |lambda|: (lambda^2 + delta^2) / (2 delta) below delta (C^1), i2d = 1 / (2 delta).
@@ -59,37 +61,27 @@ RD_HD T abs_reg(T lam, T delta, T i2d) {
   return (a < delta) ? (lam * lam + delta * delta) * i2d : a;
 }
 
-// a = L v, L = R^{-1} (left eigenvectors of K(n) for a unit normal, App. A).
-template <class T>
-RD_HD void L_apply(const RoeState<T>& r, const NodeSys<T>& n, const T v[4], T a[4]) {
-  T dp = r.g1 * (r.q2h * v[0] - r.u * v[1] - r.v * v[2] + v[3]);
-  T m = r.c * (n.nx * v[1] + n.ny * v[2] - n.w * v[0]);
-  a[0] = (dp + m) * r.ic2h;
-  a[1] = (dp - m) * r.ic2h;
-  a[2] = n.nx * v[2] - n.ny * v[1] - n.uperp * v[0];
-  a[3] = v[0] - dp * r.ic2;
-}
-
-// o = R a, R = right eigenvectors of App. A as columns.
-template <class T>
-RD_HD void R_apply(const RoeState<T>& r, const NodeSys<T>& n, const T a[4], T o[4]) {
-  T s = a[0] + a[1], d = a[0] - a[1], t0 = s + a[3];
-  o[0] = t0;
-  o[1] = r.u * t0 + r.c * n.nx * d - n.ny * a[2];
-  o[2] = r.v * t0 + r.c * n.ny * d + n.nx * a[2];
-  o[3] = r.h * s + r.c * n.w * d + n.uperp * a[2] + r.q2h * a[3];
-}
-
+// K^{+-} in closed form (App. A).  With the right eigenvectors of App. A,
+// e = (1, u, v, h), d = (0, nx, ny, w), the pressure row a = (alpha, -g1 u,
+// -g1 v, g1) and the normal-velocity row b = (-w, nx, ny, 0), the two acoustic
+// projectors are (e +- c d)(a +- c b)^T / (2 c^2) and the entropy and shear
+// projectors sum to I minus them, so for eigenvalues (l1, l2, l3, l3)
+//   K = l3 I + e (s1 a + s2 b)^T + d (s2 a + hp b)^T,
+//   mu1 = l1 - l3, mu2 = l2 - l3, s1 = (mu1 + mu2) / (2 c^2),
+//   s2 = (mu1 - mu2) / (2 c), hp = (mu1 + mu2) / 2.
+// PLUS selects Lambda^+ or Lambda^-; o = K^{+-} v.
 template <class T, bool PLUS>
 RD_HD void Kpm_apply(const RoeState<T>& r, const NodeSys<T>& n, const T v[4], T o[4]) {
-  T a[4];
-  L_apply(r, n, v, a);
-  const T* l = PLUS ? n.lp : n.lm;
-  a[0] *= l[0];
-  a[1] *= l[1];
-  a[2] *= l[2];
-  a[3] *= l[2];
-  R_apply(r, n, a, o);
+  const int j = PLUS ? 0 : 1;
+  T A = r.alpha * v[0] - r.g1u * v[1] - r.g1v * v[2] + r.g1 * v[3];
+  T B = n.nx * v[1] + n.ny * v[2] - n.w * v[0];
+  T P = n.s1[j] * A + n.s2[j] * B;
+  T Q = n.s2[j] * A + n.hp[j] * B;
+  T l3 = n.l3[j];
+  o[0] = l3 * v[0] + P;
+  o[1] = l3 * v[1] + r.u * P + n.nx * Q;
+  o[2] = l3 * v[2] + r.v * P + n.ny * Q;
+  o[3] = l3 * v[3] + r.h * P + n.w * Q;
 }
 
 // LU factorisation with partial pivoting of a 4x4 matrix held in registers.
@@ -189,6 +181,10 @@ RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3]
   r.c = sqrt(c2);
   r.ic2 = T(1) / c2;
   r.ic2h = r.ic2 * T(0.5);
+  r.i2c = r.c * r.ic2h;
+  r.alpha = r.g1 * r.q2h;
+  r.g1u = r.g1 * r.u;
+  r.g1v = r.g1 * r.v;
 
   // phi^T = dF/dZ(Zbar) gx + dG/dZ(Zbar) gy, g = sum_i (n_i / 2) Z_i
   T gx[4] = {T(0), T(0), T(0), T(0)}, gy[4] = {T(0), T(0), T(0), T(0)};
@@ -218,33 +214,61 @@ RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3]
     n.nx = nx[i];
     n.ny = ny[i];
     n.w = r.u * n.nx + r.v * n.ny;
-    n.uperp = r.v * n.nx - r.u * n.ny;
     T delta = eps * r.c * hl[i];
     T la[3] = {(n.w + r.c) * hl[i], (n.w - r.c) * hl[i], n.w * hl[i]};
     T i2d = T(0);
     if (fabs(la[0]) < delta || fabs(la[1]) < delta || fabs(la[2]) < delta) i2d = T(0.5) / delta;
+    T ab[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      T ab = abs_reg(la[k], delta, i2d);
-      n.lp[k] = (la[k] + ab) * T(0.5);
-      n.lm[k] = (la[k] - ab) * T(0.5);
+    for (int k = 0; k < 3; ++k) ab[k] = abs_reg(la[k], delta, i2d);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      // j = 0: Lambda^+ = (la + |la|)/2, j = 1: Lambda^- = (la - |la|)/2
+      T sg = j == 0 ? T(0.5) : T(-0.5);
+      T l1 = la[0] * T(0.5) + sg * ab[0];
+      T l2 = la[1] * T(0.5) + sg * ab[1];
+      T l3 = la[2] * T(0.5) + sg * ab[2];
+      T mu1 = l1 - l3, mu2 = l2 - l3;
+      T sp = mu1 + mu2, sm = mu1 - mu2;
+      n.l3[j] = l3;
+      n.s1[j] = sp * r.ic2h;
+      n.s2[j] = sm * r.i2c;
+      n.hp[j] = sp * T(0.5);
     }
   }
 
-  // sum_j K_j^- column by column, then LU
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    T e[4] = {T(q == 0), T(q == 1), T(q == 2), T(q == 3)};
-    T col[4] = {T(0), T(0), T(0), T(0)};
+  // sum_j K_j^- = (sum l3) I + e P^T + sum_j d_j q_j^T,
+  //   P = (sum s1) a + sum_j s2_j b_j,  q_j = s2_j a + hp_j b_j
+  {
+    T L3 = T(0), S1 = T(0), Pw = T(0), Px = T(0), Py = T(0);
+    T M1[4] = {T(0), T(0), T(0), T(0)}, M2[4] = {T(0), T(0), T(0), T(0)}, M3[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      T o[4];
-      Kpm_apply<T, false>(r, L.nd[j], e, o);
+      const NodeSys<T>& n = L.nd[j];
+      L3 += n.l3[1];
+      S1 += n.s1[1];
+      Pw += n.s2[1] * n.w;
+      Px += n.s2[1] * n.nx;
+      Py += n.s2[1] * n.ny;
+      T q[4] = {n.s2[1] * r.alpha - n.hp[1] * n.w, n.hp[1] * n.nx - n.s2[1] * r.g1u,
+                n.hp[1] * n.ny - n.s2[1] * r.g1v, n.s2[1] * r.g1};
 #pragma unroll
-      for (int k = 0; k < 4; ++k) col[k] += o[k];
+      for (int c = 0; c < 4; ++c) {
+        M1[c] += n.nx * q[c];
+        M2[c] += n.ny * q[c];
+        M3[c] += n.w * q[c];
+      }
+    }
+    T P[4] = {S1 * r.alpha - Pw, Px - S1 * r.g1u, Py - S1 * r.g1v, S1 * r.g1};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      L.lu.a[0][c] = P[c];
+      L.lu.a[1][c] = r.u * P[c] + M1[c];
+      L.lu.a[2][c] = r.v * P[c] + M2[c];
+      L.lu.a[3][c] = r.h * P[c] + M3[c];
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) L.lu.a[k][q] = col[k];
+    for (int k = 0; k < 4; ++k) L.lu.a[k][k] += L3;
   }
   if (!L.lu.factor()) return ST_SINGULAR;
 
@@ -318,10 +342,27 @@ __device__ __forceinline__ void load_tri(int t, int nt, const int* __restrict__ 
   }
 }
 
+// Vertex arrays are records of four components ([nv][4]): one 16-byte load
+// (float) or two (double) per vertex.
+__device__ __forceinline__ void ld4(const float* __restrict__ p, float out[4]) {
+  float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+}
+__device__ __forceinline__ void ld4(const double* __restrict__ p, double out[4]) {
+  double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float v[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double v[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
 template <class T>
-__device__ __forceinline__ void load_vec4(const T* __restrict__ A, size_t nv, int i, T out[4]) {
-#pragma unroll
-  for (int k = 0; k < 4; ++k) out[k] = __ldg(A + k * nv + i);
+__device__ __forceinline__ void load_vec4(const T* __restrict__ A, int i, T out[4]) {
+  ld4(A + 4 * (size_t)i, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -418,7 +459,7 @@ __global__ void __launch_bounds__(128) k_tri_stage1(int nt, int nv, const int* _
   T nx[3], ny[3], hl[3], Zc[3][4];
   load_tri(t, nt, tri, g, v, nx, ny, hl);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) load_vec4(Z, (size_t)nv, v[c], Zc[c]);
+  for (int c = 0; c < 3; ++c) load_vec4(Z, v[c], Zc[c]);
   {
     T s0 = __ldg(spd + v[0]), s1 = __ldg(spd + v[1]), s2 = __ldg(spd + v[2]);
     T lam = s0 > s1 ? s0 : s1;
@@ -434,13 +475,11 @@ __global__ void __launch_bounds__(128) k_tri_stage1(int nt, int nv, const int* _
   if (SCHEME != RD_N1) {
     T* rp = rec + (size_t)t * 16;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) rp[k] = r[k];
+    for (int k = 0; k < 4; ++k) st4(rp + 4 * k, r + 4 * k);
   }
   T* sp = share + (size_t)t * 12;
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) sp[4 * i + k] = out[i][k];
+  for (int i = 0; i < 3; ++i) st4(sp + 4 * i, out[i]);
 }
 
 // Inspection variant: phi^N, phi^LDA, phi^B (each [nt][3][4]) and the CFL term.
@@ -455,7 +494,7 @@ __global__ void __launch_bounds__(128) k_tri_terms(int nt, int nv, const int* __
   T nx[3], ny[3], hl[3], Zc[3][4];
   load_tri(t, nt, tri, g, v, nx, ny, hl);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) load_vec4(Z, (size_t)nv, v[c], Zc[c]);
+  for (int c = 0; c < 3; ++c) load_vec4(Z, v[c], Zc[c]);
   T s0 = spd[v[0]], s1 = spd[v[1]], s2 = spd[v[2]];
   T lam = s0 > s1 ? s0 : s1;
   lam = lam > s2 ? lam : s2;
@@ -507,13 +546,13 @@ __global__ void __launch_bounds__(BLOCK) k_gather_cfl(int nv, const int* __restr
     int e0 = __ldg(ptr + i), e1 = __ldg(ptr + i + 1);
     for (int e = e0; e < e1; ++e) {
       int te = __ldg(ent + e);
-      const T* sp = share + (size_t)te * 4;
+      T q[4];
+      ld4(share + (size_t)te * 4, q);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) r[k] += __ldg(sp + k);
+      for (int k = 0; k < 4; ++k) r[k] += q[k];
       sig += __ldg(cfl + te / 3);
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) R1[(size_t)k * nv + i] = r[k];
+    st4(R1 + 4 * (size_t)i, r);
     ratio = T(2) * __ldg(V + i) / sig;
   }
   ratio = warp_min(ratio);
@@ -590,24 +629,23 @@ __global__ void __launch_bounds__(256) k_update(int nv, const T* __restrict__ Wi
     r[0] = r[1] = r[2] = r[3] = T(0);
     int e0 = __ldg(ptr + i), e1 = __ldg(ptr + i + 1);
     for (int e = e0; e < e1; ++e) {
-      const T* sp = share + (size_t)__ldg(ent + e) * 4;
+      T q[4];
+      ld4(share + (size_t)__ldg(ent + e) * 4, q);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) r[k] += __ldg(sp + k);
+      for (int k = 0; k < 4; ++k) r[k] += q[k];
     }
   } else {
-    load_vec4(R, (size_t)nv, i, r);
+    load_vec4(R, i, r);
   }
   T dt = (T)ctl->dt;
   T f = dt / __ldg(V + i);
   T W[4], Z[4], spd;
+  load_vec4(Win, i, W);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) W[k] = __ldg(Win + (size_t)k * nv + i) - f * r[k];
+  for (int k = 0; k < 4; ++k) W[k] = W[k] - f * r[k];
   bool ok = vertex_Z(W, gamma, Z, spd);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    Wout[(size_t)k * nv + i] = W[k];
-    Zout[(size_t)k * nv + i] = Z[k];
-  }
+  st4(Wout + 4 * (size_t)i, W);
+  st4(Zout + 4 * (size_t)i, Z);
   if (spdout) spdout[i] = spd;
   if (!ok) {
     atomicOr(&ctl->status, ST_NONPHYS_VERTEX);
@@ -622,10 +660,9 @@ __global__ void k_prepare(int nv, const T* __restrict__ W, T gamma, T* __restric
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nv) return;
   T w[4], z[4], s;
-  load_vec4(W, (size_t)nv, i, w);
+  load_vec4(W, i, w);
   bool ok = vertex_Z(w, gamma, z, s);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) Z[(size_t)k * nv + i] = z[k];
+  st4(Z + 4 * (size_t)i, z);
   spd[i] = s;
   if (!ok) atomicOr(&ctl->status, ST_NONPHYS_VERTEX);
 }
@@ -645,13 +682,13 @@ __global__ void __launch_bounds__(128) k_tri_stage2(int nt, int nv, const int* _
   load_tri(t, nt, tri, g, v, nx, ny, hl);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    load_vec4(Zs, (size_t)nv, v[c], Zc[c]);
-    load_vec4(Wn, (size_t)nv, v[c], wn[c]);
-    load_vec4(Ws, (size_t)nv, v[c], ws[c]);
+    load_vec4(Zs, v[c], Zc[c]);
+    load_vec4(Wn, v[c], wn[c]);
+    load_vec4(Ws, v[c], ws[c]);
   }
   const T* rp = rec + (size_t)t * 16;
 #pragma unroll
-  for (int k = 0; k < 16; ++k) r[k] = __ldg(rp + k);
+  for (int k = 0; k < 4; ++k) ld4(rp + 4 * k, r + 4 * k);
   T out[3][4];
   int st = stage2_body<T, SCHEME>(Zc, wn, ws, r, nx, ny, hl, __ldg(g.area + t), (T)ctl->dt, gamma, eps, out);
   if (st) {
@@ -660,9 +697,7 @@ __global__ void __launch_bounds__(128) k_tri_stage2(int nt, int nv, const int* _
   }
   T* sp = share + (size_t)t * 12;
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) sp[4 * i + k] = out[i][k];
+  for (int i = 0; i < 3; ++i) st4(sp + 4 * i, out[i]);
 }
 
 // One thread: commit the step if nothing went wrong.
@@ -685,7 +720,7 @@ __global__ void __launch_bounds__(BLOCK) k_conserved_partial(int nv, const T* __
   __shared__ double red[4][BLOCK];
   int i = blockIdx.x * BLOCK + threadIdx.x;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = i < nv ? (double)V[i] * (double)W[(size_t)k * nv + i] : 0.0;
+  for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = i < nv ? (double)V[i] * (double)W[4 * (size_t)i + k] : 0.0;
   __syncthreads();
   for (int s = BLOCK / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s)
@@ -794,7 +829,7 @@ __global__ void k_permute_in(int nv, const int* __restrict__ vperm, const double
   for (int k = 0; k < 4; ++k) {
     double x = src[(size_t)k * nv + j];
     ok = ok && isfinite(x);
-    dst[(size_t)k * nv + i] = (T)x;
+    dst[4 * (size_t)i + k] = (T)x;
   }
   if (!ok) atomicOr(&ctl->status, ST_NONPHYS_VERTEX);
 }
@@ -806,7 +841,7 @@ __global__ void k_permute_out(int nv, const int* __restrict__ vperm, const T* __
   if (i >= nv) return;
   int j = __ldg(vperm + i);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) dst[(size_t)k * nv + j] = (double)src[(size_t)k * nv + i];
+  for (int k = 0; k < 4; ++k) dst[(size_t)k * nv + j] = (double)src[4 * (size_t)i + k];
 }
 
 template <class Tsrc, class Tdst>
