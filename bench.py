@@ -38,6 +38,7 @@ WORKLOADS = {
     "khi2048_B2": (2048, "khi", "B2"),
     "sod1024_B2": (1024, "sod", "B2"),
     "vortex64_N1": (64, "vortex", "N1"),
+    "batch64_B2": (None, "batch", "B2"),
 }
 # algorithmic HBM bytes of one triangle-update (whole step) for the two-stage
 # scheme: W^n, xy, V read and R1, sigma written in the first pass; W^n, R1, V,
@@ -69,6 +70,8 @@ def parse():
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 companion measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-form companion measurement")
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -185,9 +188,10 @@ def ncu_traffic(workload, precision, kernel, nt):
     return float(e["dram_bytes_per_triangle"]) * nt
 
 
-def run_state_timing(binding, mesh_dev, W0, scheme, precision, steps, warmup, ws, clocks=None):
+def run_state_timing(binding, mesh_dev, W0, scheme, precision, steps, warmup, ws, clocks=None, autotune=True):
     import torch
     s = binding.State(mesh_dev, W0, scheme=scheme, precision=precision)
+    s.shapes = s.autotune() if autotune else None
     s.run(warmup)
     st = mesh_dev.stream
     torch.cuda.synchronize()
@@ -207,12 +211,29 @@ def run_state_timing(binding, mesh_dev, W0, scheme, precision, steps, warmup, ws
     return s, ms_total, per_kernel, launches
 
 
+def ours_batched(args, ws, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    bt = batched(args, ws, args.steps)
+    line = {"metric": METRIC, "value": bt["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": bt["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+            "data": "synthetic (64 seeded periodic meshes, vortex / shear states)",
+            "config": {"workload": "batch64_B2", "meshes": bt["meshes"], "triangles": bt["triangles"],
+                       "scheme": "B2", "cfl": 0.8, "precision": args.precision,
+                       "l2": "inputs larger than L2", "steps_per_graph_launch": args.steps},
+            "batched": bt, "gpu_launches": 7 * args.steps + 1}
+    return line
+
+
 def ours(args, ws, rank, local):
     import numpy as np
     import torch
 
     from paper_1705_02028_gb300 import binding
 
+    if args.workload == "batch64_B2":
+        return ours_batched(args, ws, rank, local)
     torch.cuda.set_device(local)
     mesh, W0, scheme = build_inputs(args.workload)
     nt, nv = mesh.nt, mesh.nv
@@ -221,8 +242,10 @@ def ours(args, ws, rank, local):
 
     clocks = ClockSampler(local)
     s, ms_total, per_kernel, launches = run_state_timing(binding, m, W0, scheme, args.precision,
-                                                         args.steps, args.warmup, ws, clocks)
+                                                         args.steps, args.warmup, ws, clocks,
+                                                         autotune=not args.no_autotune)
     clk = clocks.result
+    shapes = s.shapes
     ms_step = max_over_ranks(ms_total / args.steps, ws)
     value = ws * nt / (ms_step * 1e-3)
 
@@ -296,6 +319,8 @@ def ours(args, ws, rank, local):
                        "l2": "inputs larger than L2 (%.0f MB vertex state)" % (4 * nv * s_bytes / 1e6),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "ms_per_step_graph": ms_graph, "per_kernel_ms": per_kernel,
+            "launch_shapes": {"tri_block": shapes[0], "vtx_block": shapes[1], "source": "rd_state_autotune"}
+            if shapes else None,
             "roofline": roof, "step_hbm": step_hbm, "e2e": e2e,
             "gpu_launches": launches * args.steps + 1,
             "clocks": clk}
@@ -303,7 +328,7 @@ def ours(args, ws, rank, local):
     # FP32 companion measurement on the same mesh
     if not args.no_fp32 and args.precision == "fp64":
         s32, ms32, pk32, _ = run_state_timing(binding, m, W0, scheme, "fp32", max(args.steps, 20),
-                                              args.warmup, ws)
+                                              args.warmup, ws, autotune=not args.no_autotune)
         ms32 = max_over_ranks(ms32 / max(args.steps, 20), ws)
         d32 = max(pk32, key=pk32.get)
         hbm = hbm_peak
@@ -318,9 +343,50 @@ def ours(args, ws, rank, local):
         s32.close()
     m.close()
 
+    if not args.no_batched and args.workload != "batch64_B2":
+        bt = batched(args, ws, args.steps)
+        bt["vs_plain_step"] = bt["value"] / value
+        line["batched"] = bt
+
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     return line
+
+
+def batched(args, ws, steps):
+    """64 independent periodic meshes, sides ~ U{128..1024} (seed 2), vortex or shear state
+    (50/50), B2 FP64, each with its own dt, `steps` steps as ONE CUDA-graph launch."""
+    import torch
+
+    from paper_1705_02028_gb300 import binding, inputs
+    work = inputs.batch_workload(n_mesh=64, seed=2)
+    stream = torch.cuda.Stream()
+    meshes = [binding.Mesh(m, stream=stream) for m, _, _ in work]
+    b = binding.Batch(meshes, [W for _, W, _ in work], scheme="B2", precision=args.precision)
+    nv, nt = b.sizes()
+    shapes = b.autotune() if not args.no_autotune else None
+    b.run(args.warmup)
+    torch.cuda.synchronize()
+    barrier(ws)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.run(steps)                      # one graph launch of `steps` steps
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, ws)
+    pk = b.profile(2)
+    t, n = b.time()
+    dts = b.dt()
+    b.close()
+    for mm in meshes:
+        mm.close()
+    return {"value": ws * nt / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "meshes": len(work),
+            "triangles": nt, "vertices": nv, "steps_per_graph_launch": steps,
+            "sides": [int(mm.Nx) for mm, _, _ in work], "dt_min": float(dts.min()), "dt_max": float(dts.max()),
+            "launch_shapes": {"tri_block": shapes[0], "vtx_block": shapes[1], "source": "rd_batch_autotune"}
+            if shapes else None, "per_kernel_ms": pk, "precision": args.precision}
 
 
 def oracle_sample_rate(scheme, steps, nthreads):

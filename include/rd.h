@@ -210,16 +210,36 @@ int rd_count_flops(int32_t scheme, int32_t stage, double out[4]);
  * dependent-chain-free FMA kernel; precision RD_FP64 or RD_FP32. */
 int rd_probe_fma_peak(int32_t precision, double *flops_per_s);
 
+/* Launch-shape autotuner of one state: times one uncommitted step (the
+ * committed state is not changed) for triangle-kernel blocks of 64, 128, 192,
+ * 256 threads and vertex-kernel blocks of 128, 256, 512 and keeps the
+ * fastest; returns the choice (either pointer may be NULL).  Results do not
+ * depend on the launch shape (every sum has a fixed order). */
+int rd_state_autotune(rd_state *s, int32_t *tri_block, int32_t *vtx_block);
+
 /* ---- batched form: many independent meshes, one graph launch -------------
- * rd_batch_create: n_mesh meshes (all on the same stream) with their own
- * initial states W0[m] (host, component-major, caller order of mesh m).
- * Each mesh keeps its own dt.  Only RD_FP64/RD_FP32 with RD_B2/RD_N1/RD_LDA2. */
+ * rd_batch_create: n_mesh (1..65535) meshes created on the same stream, with
+ * their own initial states W0[m] (host, component-major, caller order of mesh
+ * m).  The meshes are concatenated into one vertex and one triangle range;
+ * every kernel of a step runs once over the whole batch, and each mesh keeps
+ * its own CFL dt (Sec. 3.2), time and step count.  The meshes must outlive
+ * the batch.  Errors as rd_state_init. */
 int rd_batch_create(int32_t n_mesh, rd_mesh *const *meshes, const double *const *W0,
                     const rd_params *p, rd_batch **out);
-/* n_steps steps of every mesh as one CUDA-graph launch. */
+/* n_steps steps of every mesh replayed as ONE CUDA-graph launch (the graph is
+ * captured on the first call for a given n_steps and reused). */
 int rd_batch_run(rd_batch *b, int32_t n_steps);
+/* State of mesh `mesh` (host, component-major, caller order of that mesh). */
 int rd_batch_get_state(const rd_batch *b, int32_t mesh, double *W_out);
-int rd_batch_get_dt(const rd_batch *b, double *dt_out /* [n_mesh] */);
+/* dt of each mesh in the most recently computed step ([n_mesh]). */
+int rd_batch_get_dt(const rd_batch *b, double *dt_out);
+/* Simulation time and step count of each mesh ([n_mesh] each, nullable). */
+int rd_batch_get_time(const rd_batch *b, double *t_out, int64_t *steps_out);
+int rd_batch_sizes(const rd_batch *b, int64_t *n_vertex, int64_t *n_tri);
+/* Launch-shape autotuner of a batch (as rd_state_autotune). */
+int rd_batch_autotune(rd_batch *b, int32_t *tri_block, int32_t *vtx_block);
+/* As rd_state_profile, for a batch (the steps advance the batch). */
+int rd_batch_profile(rd_batch *b, int32_t n_steps, double *ms_per_launch);
 void rd_batch_destroy(rd_batch *b);
 
 #ifdef __cplusplus

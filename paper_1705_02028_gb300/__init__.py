@@ -11,6 +11,6 @@ Modules:
   build    in-tree nvcc build of ``_lib/librd.so``
 """
 from . import inputs  # noqa: F401
-from .binding import Mesh, State, RDError, load  # noqa: F401
+from .binding import Batch, Mesh, State, RDError, load  # noqa: F401
 
-__all__ = ["inputs", "Mesh", "State", "RDError", "load"]
+__all__ = ["inputs", "Mesh", "State", "Batch", "RDError", "load"]

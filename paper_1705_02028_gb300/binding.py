@@ -77,6 +77,11 @@ _SIGS = {
     "rd_batch_get_state": (ctypes.c_int, [_vp, ctypes.c_int32, _dp]),
     "rd_batch_get_dt": (ctypes.c_int, [_vp, _dp]),
     "rd_batch_destroy": (None, [_vp]),
+    "rd_state_autotune": (ctypes.c_int, [_vp, _i32p, _i32p]),
+    "rd_batch_get_time": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_int64)]),
+    "rd_batch_sizes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "rd_batch_autotune": (ctypes.c_int, [_vp, _i32p, _i32p]),
+    "rd_batch_profile": (ctypes.c_int, [_vp, ctypes.c_int32, _dp]),
 }
 
 
@@ -294,12 +299,88 @@ class State:
         names = ("tri_stage1", "gather_cfl", "update1", "tri_stage2", "update2", "commit")
         return dict(zip(names, ms.tolist())), n.value
 
+    def autotune(self):
+        """Pick the fastest launch shapes for this state (rd_state_autotune)."""
+        tb, vb = ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.rd_state_autotune(self.handle, ctypes.byref(tb), ctypes.byref(vb)), "rd_state_autotune")
+        return tb.value, vb.value
+
     def close(self):
         if getattr(self, "handle", None):
             _lib.rd_state_destroy(self.handle)
             self.handle = None
             if self in self.mesh.states:
                 self.mesh.states.remove(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent meshes advanced together (rd_batch_create ... rd_batch_destroy)."""
+
+    def __init__(self, meshes, states, scheme="B2", precision="fp64", cfl=0.8, gamma=1.4, eps_fix=1e-6):
+        load()
+        self.meshes = list(meshes)
+        self.params = _params(scheme, precision, cfl, gamma, eps_fix)
+        self._W = [np.ascontiguousarray(W, dtype=np.float64) for W in states]
+        for m, W in zip(self.meshes, self._W):
+            if W.shape != (4, m.nv):
+                raise ValueError("each state must have shape (4, nv) of its mesh")
+        n = len(self.meshes)
+        hs = (_vp * n)(*[m.handle for m in self.meshes])
+        ws = (_dp * n)(*[_ptr(W) for W in self._W])
+        h = _vp()
+        _check(_lib.rd_batch_create(n, hs, ws, ctypes.byref(self.params), ctypes.byref(h)), "rd_batch_create")
+        self.handle = h
+        self._W = None
+
+    @property
+    def n_mesh(self):
+        return len(self.meshes)
+
+    def sizes(self):
+        nv, nt = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.rd_batch_sizes(self.handle, ctypes.byref(nv), ctypes.byref(nt)), "rd_batch_sizes")
+        return nv.value, nt.value
+
+    def run(self, n_steps: int):
+        _check(_lib.rd_batch_run(self.handle, int(n_steps)), "rd_batch_run")
+
+    def get(self, m: int) -> np.ndarray:
+        W = np.empty((4, self.meshes[m].nv))
+        _check(_lib.rd_batch_get_state(self.handle, int(m), _ptr(W)), "rd_batch_get_state")
+        return W
+
+    def dt(self) -> np.ndarray:
+        out = np.empty(self.n_mesh)
+        _check(_lib.rd_batch_get_dt(self.handle, _ptr(out)), "rd_batch_get_dt")
+        return out
+
+    def time(self):
+        t = np.empty(self.n_mesh)
+        n = np.empty(self.n_mesh, dtype=np.int64)
+        _check(_lib.rd_batch_get_time(self.handle, _ptr(t), _ptr(n, ctypes.c_int64)), "rd_batch_get_time")
+        return t, n
+
+    def autotune(self):
+        tb, vb = ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.rd_batch_autotune(self.handle, ctypes.byref(tb), ctypes.byref(vb)), "rd_batch_autotune")
+        return tb.value, vb.value
+
+    def profile(self, n_steps: int):
+        ms = np.zeros(6)
+        _check(_lib.rd_batch_profile(self.handle, int(n_steps), _ptr(ms)), "rd_batch_profile")
+        names = ("tri_stage1", "gather_cfl", "update1", "tri_stage2", "update2", "commit")
+        return dict(zip(names, ms.tolist()))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.rd_batch_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

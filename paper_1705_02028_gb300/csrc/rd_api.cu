@@ -13,6 +13,7 @@
 #include <new>
 #include <vector>
 
+#include "rd_device.h"
 #include "rd_internal.h"
 #include "rd_kernels.cuh"
 
@@ -33,13 +34,7 @@ extern "C" int rd_set_allocator(rd_alloc_fn alloc, rd_free_fn free_fn, void* ctx
   return RD_OK;
 }
 
-namespace {
-
-struct DevBuf {
-  void* p = nullptr;
-  rd_free_fn fr = nullptr;  // allocator that owns p (nullptr: cudaFree)
-  void* ctx = nullptr;
-};
+namespace rd {
 
 int dev_alloc(DevBuf& b, size_t bytes, cudaStream_t s) {
   if (bytes == 0) bytes = 16;
@@ -66,42 +61,12 @@ void dev_free(DevBuf& b) {
   b.p = nullptr;
 }
 
-#define CU(x)                                  \
-  do {                                         \
-    cudaError_t e_ = (x);                      \
-    if (e_ != cudaSuccess) {                   \
-      cudaGetLastError();                      \
-      return RD_ECUDA;                         \
-    }                                          \
-  } while (0)
-
-#define CK(x)              \
-  do {                     \
-    int s_ = (x);          \
-    if (s_ != RD_OK) return s_; \
-  } while (0)
-
-inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
-
-constexpr int TRI_BLOCK = 128;
-constexpr int VTX_BLOCK = 256;
-
-}  // namespace
+}  // namespace rd
 
 // ---------------------------------------------------------------------------
 // mesh
 // ---------------------------------------------------------------------------
-struct rd_mesh {
-  HostMesh h;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  DevBuf tri, ptr, ent, vperm;
-  // geometry per precision: nx, ny, hl, area, lmax, V
-  DevBuf geo[2][6];
-  bool geo_ready[2] = {false, false};
-};
-
-namespace {
+namespace rd {
 
 template <class T>
 int upload_vec(DevBuf& b, const std::vector<double>& src, cudaStream_t s) {
@@ -135,7 +100,7 @@ DevGeo<T> geo_of(const rd_mesh* m) {
   return g;
 }
 
-}  // namespace
+}  // namespace rd
 
 extern "C" int rd_mesh_create(int32_t n_vertex, const double* xy, int32_t n_tri, const int32_t* tri,
                               const int8_t* image_shift, double Lx, double Ly, int32_t reorder,
@@ -219,6 +184,7 @@ struct rd_state {
   DevBuf Ws, Zs, R1, share, rec, cfl, partial, ctl, cons_partial, cons_out;
   DevBuf stage;  // [4][nv] double, caller vertex order (host I/O)
   long long launched = 0;  // host view of the committed step count (parity of the buffers)
+  int tri_block = TRI_BLOCK, vtx_block = VTX_BLOCK;  // launch shapes (autotuned)
   cudaGraphExec_t g2 = nullptr;  // two steps (even -> odd -> even)
   bool graph_failed = false;
 };
@@ -239,10 +205,34 @@ __global__ void k_begin(DevCtl* ctl, double t_end) {
   ctl->t_end = t_end;
 }
 
+}  // namespace
+
+template <class T>
+void rd::launch_gather_cfl(int vblock, cudaStream_t st, int nv, const int* ptr, const int* ent, const T* share,
+                           const T* cfl, const T* V, T* R1, T* partial, T cflnum, DevCtl* ctl) {
+  switch (vblock) {
+    case 128:
+      k_gather_cfl<T, 128><<<nblk(nv, 128), 128, 0, st>>>(nv, ptr, ent, share, cfl, V, R1, partial, cflnum, ctl);
+      break;
+    case 512:
+      k_gather_cfl<T, 512><<<nblk(nv, 512), 512, 0, st>>>(nv, ptr, ent, share, cfl, V, R1, partial, cflnum, ctl);
+      break;
+    default:
+      k_gather_cfl<T, 256><<<nblk(nv, 256), 256, 0, st>>>(nv, ptr, ent, share, cfl, V, R1, partial, cflnum, ctl);
+      break;
+  }
+}
+template void rd::launch_gather_cfl<double>(int, cudaStream_t, int, const int*, const int*, const double*,
+                                            const double*, const double*, double*, double*, double, DevCtl*);
+template void rd::launch_gather_cfl<float>(int, cudaStream_t, int, const int*, const int*, const float*,
+                                           const float*, const float*, float*, float*, float, DevCtl*);
+
+namespace {
+
 // Launches one step reading buffer a and writing buffer 1-a.  ev (nullable):
 // seven events recorded before each kernel and after the last one.
 template <class T>
-int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr) {
+int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = true) {
   rd_mesh* m = s->m;
   const int nt = m->h.nt, nv = m->h.nv, b = 1 - a;
   cudaStream_t st = m->stream;
@@ -256,7 +246,8 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr) {
   T* share = (T*)s->share.p;
   T* rec = (T*)s->rec.p;
   T* cf = (T*)s->cfl.p;
-  unsigned gt = nblk(nt, TRI_BLOCK), gv = nblk(nv, VTX_BLOCK);
+  const int TB = s->tri_block, VB = s->vtx_block;
+  unsigned gt = nblk(nt, TB), gv = nblk(nv, VB);
   const T* Za = (const T*)s->Z[a].p;
   const T* Sa = (const T*)s->spd[a].p;
   auto mark = [&](int k) {
@@ -265,48 +256,47 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr) {
   mark(0);
   switch (s->p.scheme) {
     case RD_N1:
-      k_tri_stage1<T, RD_N1><<<gt, TRI_BLOCK, 0, st>>>(nt, nv, tri, g, Za, Sa, gamma, eps, share, nullptr, cf, ctl);
+      k_tri_stage1<T, RD_N1><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, gamma, eps, share, nullptr, cf, ctl);
       break;
     case RD_B2:
-      k_tri_stage1<T, RD_B2><<<gt, TRI_BLOCK, 0, st>>>(nt, nv, tri, g, Za, Sa, gamma, eps, share, rec, cf, ctl);
+      k_tri_stage1<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, gamma, eps, share, rec, cf, ctl);
       break;
     default:
-      k_tri_stage1<T, RD_LDA2><<<gt, TRI_BLOCK, 0, st>>>(nt, nv, tri, g, Za, Sa, gamma, eps, share, rec, cf, ctl);
+      k_tri_stage1<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, gamma, eps, share, rec, cf, ctl);
       break;
   }
   mark(1);
-  k_gather_cfl<T, VTX_BLOCK><<<gv, VTX_BLOCK, 0, st>>>(nv, ptr, ent, share, cf, V, (T*)s->R1.p, (T*)s->partial.p,
-                                                       cfl, ctl);
+  launch_gather_cfl<T>(VB, st, nv, ptr, ent, share, cf, V, (T*)s->R1.p, (T*)s->partial.p, cfl, ctl);
   mark(2);
   if (s->p.scheme == RD_N1) {
-    k_update<T><<<gv, VTX_BLOCK, 0, st>>>(nv, (const T*)s->W[a].p, (const T*)s->R1.p, ptr, ent, nullptr, V, gamma,
+    k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)s->W[a].p, (const T*)s->R1.p, ptr, ent, nullptr, V, gamma,
                                           (T*)s->W[b].p, (T*)s->Z[b].p, (T*)s->spd[b].p, ctl);
     mark(3);
     mark(4);
     mark(5);
   } else {
-    k_update<T><<<gv, VTX_BLOCK, 0, st>>>(nv, (const T*)s->W[a].p, (const T*)s->R1.p, ptr, ent, nullptr, V, gamma,
+    k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)s->W[a].p, (const T*)s->R1.p, ptr, ent, nullptr, V, gamma,
                                           (T*)s->Ws.p, (T*)s->Zs.p, nullptr, ctl);
     mark(3);
     if (s->p.scheme == RD_B2)
-      k_tri_stage2<T, RD_B2><<<gt, TRI_BLOCK, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
+      k_tri_stage2<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
                                                        (const T*)s->Ws.p, rec, gamma, eps, share, ctl);
     else
-      k_tri_stage2<T, RD_LDA2><<<gt, TRI_BLOCK, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
+      k_tri_stage2<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
                                                          (const T*)s->Ws.p, rec, gamma, eps, share, ctl);
     mark(4);
-    k_update<T><<<gv, VTX_BLOCK, 0, st>>>(nv, (const T*)s->Ws.p, nullptr, ptr, ent, share, V, gamma,
+    k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)s->Ws.p, nullptr, ptr, ent, share, V, gamma,
                                           (T*)s->W[b].p, (T*)s->Z[b].p, (T*)s->spd[b].p, ctl);
     mark(5);
   }
-  k_commit<<<1, 1, 0, st>>>(ctl);
+  if (commit) k_commit<<<1, 1, 0, st>>>(ctl);
   mark(6);
   CU(cudaGetLastError());
   return RD_OK;
 }
 
-int launch_step_any(rd_state* s, int a, cudaEvent_t* ev = nullptr) {
-  return s->pi == 0 ? launch_step<double>(s, a, ev) : launch_step<float>(s, a, ev);
+int launch_step_any(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = true) {
+  return s->pi == 0 ? launch_step<double>(s, a, ev, commit) : launch_step<float>(s, a, ev, commit);
 }
 
 int read_ctl(const rd_state* s, DevCtl& c) {
@@ -361,7 +351,7 @@ int alloc_state(rd_state* s) {
   CK(dev_alloc(s->R1, 4 * nv * ts, st));
   CK(dev_alloc(s->share, 12 * nt * ts, st));
   CK(dev_alloc(s->cfl, nt * ts, st));
-  CK(dev_alloc(s->partial, (size_t)nblk(nv, VTX_BLOCK) * ts, st));
+  CK(dev_alloc(s->partial, (size_t)nblk(nv, VTX_BLOCK_MIN) * ts, st));
   CK(dev_alloc(s->ctl, sizeof(DevCtl), st));
   CK(dev_alloc(s->cons_partial, (size_t)nblk(nv, VTX_BLOCK) * 4 * sizeof(double), st));
   CK(dev_alloc(s->cons_out, 4 * sizeof(double), st));
@@ -521,6 +511,50 @@ extern "C" int rd_state_profile(rd_state* s, int32_t n_steps, double* ms_per_lau
   CK(read_ctl(s, c));
   s->launched = c.steps;
   return status_to_rd(c.status);
+}
+
+extern "C" int rd_state_autotune(rd_state* s, int32_t* tri_block, int32_t* vtx_block) {
+  if (!s) return RD_EINVAL;
+  DevCtl c0;
+  CK(read_ctl(s, c0));
+  if (c0.status) return RD_ENONPHYSICAL;
+  const int a = (int)(c0.steps & 1);
+  cudaStream_t st = s->m->stream;
+  const int tri_c[] = {64, 128, 192, 256};
+  const int vtx_c[] = {128, 256, 512};
+  cudaEvent_t ev[7];
+  for (auto& e : ev) cudaEventCreate(&e);
+  auto time_step = [&](int tb, int vb, float& ms) -> int {
+    s->tri_block = tb;
+    s->vtx_block = vb;
+    k_begin<<<1, 1, 0, st>>>((DevCtl*)s->ctl.p, 0.0);
+    CK(launch_step_any(s, a, nullptr, false));  // warm
+    CK(launch_step_any(s, a, ev, false));
+    CU(cudaStreamSynchronize(st));
+    CU(cudaEventElapsedTime(&ms, ev[0], ev[6]));
+    return RD_OK;
+  };
+  int best_t = TRI_BLOCK, best_v = VTX_BLOCK, rc = RD_OK;
+  float best = 1e30f, ms = 0.f;
+  for (int tb : tri_c) {
+    if ((rc = time_step(tb, VTX_BLOCK, ms)) != RD_OK) break;
+    if (ms < best) { best = ms; best_t = tb; }
+  }
+  best = 1e30f;
+  for (int vb : vtx_c) {
+    if (rc != RD_OK || (rc = time_step(best_t, vb, ms)) != RD_OK) break;
+    if (ms < best) { best = ms; best_v = vb; }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  s->tri_block = best_t;
+  s->vtx_block = best_v;
+  if (s->g2) {  // the captured graph holds the old launch shapes
+    cudaGraphExecDestroy(s->g2);
+    s->g2 = nullptr;
+  }
+  if (tri_block) *tri_block = best_t;
+  if (vtx_block) *vtx_block = best_v;
+  return rc;
 }
 
 extern "C" int rd_get_state(const rd_state* s, double* W_out) {

@@ -449,7 +449,7 @@ RD_HD int stage2_body(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], cons
 // cfl [nt] = l_max^T max_j (|v_j| + c_j).
 // ---------------------------------------------------------------------------
 template <class T, int SCHEME>
-__global__ void __launch_bounds__(128) k_tri_stage1(int nt, int nv, const int* __restrict__ tri, DevGeo<T> g,
+__global__ void __launch_bounds__(256) k_tri_stage1(int nt, int nv, const int* __restrict__ tri, DevGeo<T> g,
                                                     const T* __restrict__ Z, const T* __restrict__ spd,
                                                     T gamma, T eps, T* __restrict__ share,
                                                     T* __restrict__ rec, T* __restrict__ cfl, DevCtl* ctl) {
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(128) k_tri_stage1(int nt, int nv, const int* _
 
 // Inspection variant: phi^N, phi^LDA, phi^B (each [nt][3][4]) and the CFL term.
 template <class T>
-__global__ void __launch_bounds__(128) k_tri_terms(int nt, int nv, const int* __restrict__ tri, DevGeo<T> g,
+__global__ void __launch_bounds__(256) k_tri_terms(int nt, int nv, const int* __restrict__ tri, DevGeo<T> g,
                                                    const T* __restrict__ Z, const T* __restrict__ spd,
                                                    T gamma, T eps, T* __restrict__ out, T* __restrict__ cfl,
                                                    DevCtl* ctl) {
@@ -617,11 +617,12 @@ __device__ __forceinline__ bool vertex_Z(const T W[4], T gamma, T Z[4], T& spd) 
 // W_out = W_in - dt/V R; Z_out = Z(W_out); spd_out (nullable) = |v| + c.
 // If R2 != nullptr, W_in is W* and R = R2 gathered here from share (stage 2).
 template <class T>
-__global__ void __launch_bounds__(256) k_update(int nv, const T* __restrict__ Win, const T* __restrict__ R,
+__global__ void __launch_bounds__(512) k_update(int nv, const T* __restrict__ Win, const T* __restrict__ R,
                                                 const int* __restrict__ ptr, const int* __restrict__ ent,
                                                 const T* __restrict__ share, const T* __restrict__ V, T gamma,
                                                 T* __restrict__ Wout, T* __restrict__ Zout, T* __restrict__ spdout,
-                                                DevCtl* ctl) {
+                                                DevCtl* ctl, const double* __restrict__ dtm = nullptr,
+                                                const uint16_t* __restrict__ vmesh = nullptr) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nv || ctl->stop) return;
   T r[4];
@@ -637,7 +638,7 @@ __global__ void __launch_bounds__(256) k_update(int nv, const T* __restrict__ Wi
   } else {
     load_vec4(R, i, r);
   }
-  T dt = (T)ctl->dt;
+  T dt = dtm ? (T)__ldg(dtm + __ldg(vmesh + i)) : (T)ctl->dt;
   T f = dt / __ldg(V + i);
   T W[4], Z[4], spd;
   load_vec4(Win, i, W);
@@ -671,10 +672,12 @@ __global__ void k_prepare(int nv, const T* __restrict__ W, T gamma, T* __restric
 // Stage-2 triangle kernel: total residuals at (W^n, W*) -> share [nt][3][4].
 // ---------------------------------------------------------------------------
 template <class T, int SCHEME>
-__global__ void __launch_bounds__(128) k_tri_stage2(int nt, int nv, const int* __restrict__ tri, DevGeo<T> g,
+__global__ void __launch_bounds__(256) k_tri_stage2(int nt, int nv, const int* __restrict__ tri, DevGeo<T> g,
                                                     const T* __restrict__ Zs, const T* __restrict__ Wn,
                                                     const T* __restrict__ Ws, const T* __restrict__ rec,
-                                                    T gamma, T eps, T* __restrict__ share, DevCtl* ctl) {
+                                                    T gamma, T eps, T* __restrict__ share, DevCtl* ctl,
+                                                    const double* __restrict__ dtm = nullptr,
+                                                    const uint16_t* __restrict__ tmesh = nullptr) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt || ctl->stop) return;
   int v[3];
@@ -690,7 +693,8 @@ __global__ void __launch_bounds__(128) k_tri_stage2(int nt, int nv, const int* _
 #pragma unroll
   for (int k = 0; k < 4; ++k) ld4(rp + 4 * k, r + 4 * k);
   T out[3][4];
-  int st = stage2_body<T, SCHEME>(Zc, wn, ws, r, nx, ny, hl, __ldg(g.area + t), (T)ctl->dt, gamma, eps, out);
+  T dt = dtm ? (T)__ldg(dtm + __ldg(tmesh + t)) : (T)ctl->dt;
+  int st = stage2_body<T, SCHEME>(Zc, wn, ws, r, nx, ny, hl, __ldg(g.area + t), dt, gamma, eps, out);
   if (st) {
     atomicOr(&ctl->status, st);
     return;
@@ -815,6 +819,77 @@ __global__ void __launch_bounds__(BLOCK) k_cfl_dt(int nv, int nt, const T* __res
       ctl->ticket = 0u;
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: many independent meshes concatenated into one vertex / triangle
+// range, each with its own dt.  vmesh[i] is the mesh of vertex i.
+// ---------------------------------------------------------------------------
+
+// Gather of stage-1 shares (as k_gather_cfl) with a per-mesh min of 2 V_i / sigma_i:
+// positive doubles order like their bit patterns, so the min is an atomicMin on
+// the bits (exact and order-independent, hence deterministic).
+template <class T>
+__global__ void __launch_bounds__(512) k_gather_cfl_batch(int nv, const int* __restrict__ ptr,
+                                                          const int* __restrict__ ent, const T* __restrict__ share,
+                                                          const T* __restrict__ cfl, const T* __restrict__ V,
+                                                          const uint16_t* __restrict__ vmesh, T* __restrict__ R1,
+                                                          unsigned long long* __restrict__ mesh_min, DevCtl* ctl) {
+  if (ctl->stop) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool act = i < nv;
+  double ratio = INFINITY;
+  int m = act ? (int)__ldg(vmesh + i) : -1;
+  if (act) {
+    T r[4] = {T(0), T(0), T(0), T(0)};
+    T sig = T(0);
+    int e0 = __ldg(ptr + i), e1 = __ldg(ptr + i + 1);
+    for (int e = e0; e < e1; ++e) {
+      int te = __ldg(ent + e);
+      T q[4];
+      ld4(share + (size_t)te * 4, q);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) r[k] += q[k];
+      sig += __ldg(cfl + te / 3);
+    }
+    st4(R1 + 4 * (size_t)i, r);
+    ratio = (double)(T(2) * __ldg(V + i) / sig);
+  }
+  // one atomic per warp when the warp lies inside one mesh (the common case)
+  int m0 = __shfl_sync(0xffffffffu, m, 0);
+  bool uniform = __all_sync(0xffffffffu, m == m0 || m < 0);
+  if (uniform) {
+    double x = warp_min(ratio);
+    if ((threadIdx.x & 31) == 0 && m0 >= 0) atomicMin(mesh_min + m0, (unsigned long long)__double_as_longlong(x));
+  } else if (act) {
+    atomicMin(mesh_min + m, (unsigned long long)__double_as_longlong(ratio));
+  }
+}
+
+// dt of every mesh from its min, then reset the mins for the next step.
+static __global__ void k_batch_dt(int n_mesh, double cflnum, unsigned long long* __restrict__ mesh_min,
+                                  double* __restrict__ dtm, DevCtl* ctl) {
+  if (ctl->stop) return;
+  for (int m = threadIdx.x; m < n_mesh; m += blockDim.x) {
+    double x = __longlong_as_double((long long)mesh_min[m]);
+    dtm[m] = cflnum * x;
+    mesh_min[m] = (unsigned long long)__double_as_longlong((double)INFINITY);
+  }
+}
+
+// Per mesh: t += dt, steps++ (only if the step raised no error).
+static __global__ void k_commit_batch(int n_mesh, const double* __restrict__ dtm, double* __restrict__ tm,
+                                      long long* __restrict__ stepsm, DevCtl* ctl) {
+  if (ctl->stop) return;
+  if (ctl->status) {
+    if (threadIdx.x == 0) ctl->stop = 1;
+    return;
+  }
+  for (int m = threadIdx.x; m < n_mesh; m += blockDim.x) {
+    tm[m] += dtm[m];
+    stepsm[m] += 1;
+  }
+  if (threadIdx.x == 0) ctl->steps += 1;
 }
 
 // Caller-order double state -> internal-order T state (and back).
