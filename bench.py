@@ -72,6 +72,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form companion measurement")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-rollout companion measurement")
     return ap.parse_args()
 
 
@@ -347,6 +348,8 @@ def ours(args, ws, rank, local):
         bt = batched(args, ws, args.steps)
         bt["vs_plain_step"] = bt["value"] / value
         line["batched"] = bt
+    if not args.no_adjoint and args.precision == "fp64":
+        line["adjoint"] = adjoint_measure(args, ws)
 
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
@@ -387,6 +390,51 @@ def batched(args, ws, steps):
             "sides": [int(mm.Nx) for mm, _, _ in work], "dt_min": float(dts.min()), "dt_max": float(dts.max()),
             "launch_shapes": {"tri_block": shapes[0], "vtx_block": shapes[1], "source": "rd_batch_autotune"}
             if shapes else None, "per_kernel_ms": pk, "precision": args.precision}
+
+
+def adjoint_measure(args, ws, n_steps=200, ckpt_every=20):
+    """Gradient of L = 1/2 sum V (rho - rho_tgt)^2 after a 200-step B2 FP64 rollout on the
+    512x512 periodic mesh from a smooth density perturbation (amplitude 0.05), checkpoints
+    every 20 steps, against 200 plain steps of the same state."""
+    import numpy as np
+    import torch
+
+    from paper_1705_02028_gb300 import binding, inputs
+    mesh = inputs.periodic_grid(512)
+    W0 = inputs.smooth_density_state(mesh, seed=3)
+    tgt = inputs.smooth_density_state(mesh, seed=4)
+    m = binding.Mesh(mesh)
+    plain = binding.State(m, W0, scheme="B2")
+    plain.run(3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain.run(n_steps)
+    t_plain = time.perf_counter() - t0
+    plain.close()
+    s = binding.State(m, W0, scheme="B2")
+    s.adjoint_forward(2, 1)             # warm the adjoint kernels once
+    s.adjoint_backward(np.zeros_like(W0))
+    s.set(W0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.adjoint_forward(n_steps, ckpt_every)
+    t_fwd = time.perf_counter() - t0
+    Wf = s.get()
+    # L = 1/2 sum V (rho - rho_tgt)^2 with V = |T|/3 summed over the triangles (regular grid: h^2)
+    V = np.full(mesh.nv, (1.0 / 512) ** 2)
+    seed = np.zeros_like(Wf)
+    seed[0] = V * (Wf[0] - tgt[0])
+    t0 = time.perf_counter()
+    g = s.adjoint_backward(seed)
+    t_bwd = time.perf_counter() - t0
+    s.close()
+    m.close()
+    nt = mesh.nt
+    return {"mesh": "512x512", "triangles": nt, "steps": n_steps, "ckpt_every": ckpt_every, "scheme": "B2",
+            "precision": "fp64", "plain_s": t_plain, "forward_s": t_fwd, "backward_s": t_bwd,
+            "value": nt * n_steps / (t_fwd + t_bwd), "unit": "triangle-updates/s (forward + backward)",
+            "plain_value": nt * n_steps / t_plain,
+            "cost_vs_plain_step": (t_fwd + t_bwd) / t_plain, "grad_norm": float(np.linalg.norm(g))}
 
 
 def oracle_sample_rate(scheme, steps, nthreads):

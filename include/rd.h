@@ -193,6 +193,37 @@ int rd_cfl_dt_noalloc(int32_t n_vertex, int32_t n_tri, int32_t precision, const 
                       const void *lmax, const void *V, const int32_t *csr_ptr, const int32_t *csr_ent,
                       double gamma, double cfl, double *dt_out, void *cuda_stream);
 
+/* ---- discrete adjoint of a rollout ------------------------------------------
+ * rd_adjoint_forward: advance s by n_steps ordinary steps (CFL dt), recording
+ * every step's dt (dts_out, nullable, [n_steps] host) and keeping the state
+ * on the device every ckpt_every steps (ceil(n_steps / ckpt_every) copies).
+ * rd_adjoint_backward: given dL/dW at the end of that rollout (host,
+ * component-major, caller order), return dL/dW at its start for the same
+ * discrete map with the recorded dt sequence held fixed (dt's own dependence
+ * on W is not differentiated).  Each checkpoint segment is re-run keeping W^n
+ * of every step and, per triangle and stage, a mask of the branches the N / B
+ * schemes took (regularised |lambda| of each node and eigenvalue, signs and
+ * guards inside Theta); the segment is then reversed step by step with the
+ * hand-written adjoint kernels (stage-2 triangle reverse, gather, stage-1
+ * triangle reverse, gather -- the transposes of Sec. 3.4's updates), which
+ * branch on those masks.  Device memory: ckpt_every + 1 state copies, two
+ * masks per triangle and step of a segment, and per-corner adjoint records.
+ * The state itself is left where rd_adjoint_forward put it.
+ * rd_run_fixed_dt: n_steps steps with the prescribed dt sequence (host,
+ * [n_steps]) instead of the CFL dt, e.g. the recorded one, for finite
+ * differences of the same map. */
+int rd_adjoint_forward(rd_state *s, int32_t n_steps, int32_t ckpt_every, double *dts_out);
+int rd_adjoint_backward(rd_state *s, const double *dL_dW_final, double *dL_dW0);
+int rd_run_fixed_dt(rd_state *s, int32_t n_steps, const double *dts);
+/* Branch masks of the next step of s (stage 1 at the current state, stage 2
+ * at that step's W* with the CFL dt), one 64-bit word per caller triangle
+ * (nullable outputs; mask2 is zero for RD_N1).  Bits: 0-8 regularised
+ * |lambda| branch of node i, eigenvalue k at bit 3i+k; 9-17 lambda < 0;
+ * 18-21 total residual < 0; 22-25 total residual == 0; 26-29 Theta's
+ * denominator is sum_i |N_ik|; 30-33 denominator > 0; 34-45 N_ik < 0 at bit
+ * 34+4i+k; 46-57 N_ik == 0.  The state does not advance. */
+int rd_state_branch_masks(rd_state *s, uint64_t *mask1, uint64_t *mask2);
+
 /* ---- measurement ------------------------------------------------------------
  * rd_state_profile: n_steps steps with CUDA events recorded on the mesh stream
  * around every kernel; ms_per_launch[6] receives the mean duration of

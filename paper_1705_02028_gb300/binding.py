@@ -78,6 +78,10 @@ _SIGS = {
     "rd_batch_get_dt": (ctypes.c_int, [_vp, _dp]),
     "rd_batch_destroy": (None, [_vp]),
     "rd_state_autotune": (ctypes.c_int, [_vp, _i32p, _i32p]),
+    "rd_adjoint_forward": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _dp]),
+    "rd_adjoint_backward": (ctypes.c_int, [_vp, _dp, _dp]),
+    "rd_run_fixed_dt": (ctypes.c_int, [_vp, ctypes.c_int32, _dp]),
+    "rd_state_branch_masks": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "rd_batch_get_time": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_int64)]),
     "rd_batch_sizes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "rd_batch_autotune": (ctypes.c_int, [_vp, _i32p, _i32p]),
@@ -299,6 +303,33 @@ class State:
         names = ("tri_stage1", "gather_cfl", "update1", "tri_stage2", "update2", "commit")
         return dict(zip(names, ms.tolist())), n.value
 
+    def run_fixed_dt(self, dts):
+        """Steps with a prescribed dt sequence (rd_run_fixed_dt)."""
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        _check(_lib.rd_run_fixed_dt(self.handle, len(d), _ptr(d)), "rd_run_fixed_dt")
+
+    def adjoint_forward(self, n_steps: int, ckpt_every: int = 20) -> np.ndarray:
+        """Rollout of n_steps recording dt and checkpoints; returns the dt sequence."""
+        dts = np.empty(int(n_steps))
+        _check(_lib.rd_adjoint_forward(self.handle, int(n_steps), int(ckpt_every), _ptr(dts)),
+               "rd_adjoint_forward")
+        return dts
+
+    def adjoint_backward(self, dL_dW_final) -> np.ndarray:
+        """dL/dW0 of the last adjoint_forward rollout (dt sequence held fixed)."""
+        g = np.ascontiguousarray(dL_dW_final, dtype=np.float64)
+        out = np.empty((4, self.mesh.nv))
+        _check(_lib.rd_adjoint_backward(self.handle, _ptr(g), _ptr(out)), "rd_adjoint_backward")
+        return out
+
+    def branch_masks(self):
+        """Per-triangle branch masks of the next step (stage 1, stage 2)."""
+        m1 = np.zeros(self.mesh.nt, dtype=np.uint64)
+        m2 = np.zeros(self.mesh.nt, dtype=np.uint64)
+        _check(_lib.rd_state_branch_masks(self.handle, _ptr(m1, ctypes.c_uint64), _ptr(m2, ctypes.c_uint64)),
+               "rd_state_branch_masks")
+        return m1, m2
+
     def autotune(self):
         """Pick the fastest launch shapes for this state (rd_state_autotune)."""
         tb, vb = ctypes.c_int32(), ctypes.c_int32()
@@ -387,3 +418,27 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def rollout(state: "State", W0, n_steps: int, ckpt_every: int = 20):
+    """Differentiable rollout: W_final = F^{n_steps}(W0) as a torch.autograd.Function.
+
+    W0 is a float64 CPU tensor of shape (4, nv) in the caller's vertex order; the
+    forward pass records the dt sequence (held fixed by the backward pass, which
+    runs the library's hand-written adjoint kernels with checkpoints every
+    `ckpt_every` steps)."""
+    import torch
+
+    class _Rollout(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, w0):
+            state.set(w0.detach().cpu().numpy())
+            ctx.dts = state.adjoint_forward(n_steps, ckpt_every)
+            return torch.from_numpy(state.get())
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            g0 = state.adjoint_backward(grad_out.detach().cpu().numpy())
+            return torch.from_numpy(g0)
+
+    return _Rollout.apply(W0)

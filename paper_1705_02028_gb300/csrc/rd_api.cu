@@ -173,21 +173,8 @@ extern "C" int rd_mesh_sizes(const rd_mesh* m, int32_t* n_vertex, int32_t* n_tri
 }
 
 // ---------------------------------------------------------------------------
-// state
+// state (struct rd_state is defined in rd_device.h)
 // ---------------------------------------------------------------------------
-struct rd_state {
-  rd_mesh* m = nullptr;
-  rd_params p{};
-  int pi = 0;            // 0: double, 1: float
-  size_t ts = 8;         // sizeof(T)
-  DevBuf W[2], Z[2], spd[2];
-  DevBuf Ws, Zs, R1, share, rec, cfl, partial, ctl, cons_partial, cons_out;
-  DevBuf stage;  // [4][nv] double, caller vertex order (host I/O)
-  long long launched = 0;  // host view of the committed step count (parity of the buffers)
-  int tri_block = TRI_BLOCK, vtx_block = VTX_BLOCK;  // launch shapes (autotuned)
-  cudaGraphExec_t g2 = nullptr;  // two steps (even -> odd -> even)
-  bool graph_failed = false;
-};
 
 namespace {
 
@@ -231,8 +218,12 @@ namespace {
 
 // Launches one step reading buffer a and writing buffer 1-a.  ev (nullable):
 // seven events recorded before each kernel and after the last one.
+__global__ void k_fix_dt(DevCtl* ctl, double dt) {
+  if (!ctl->stop) ctl->dt = dt;
+}
+
 template <class T>
-int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = true) {
+int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = true, double fixed_dt = 0.0) {
   rd_mesh* m = s->m;
   const int nt = m->h.nt, nv = m->h.nv, b = 1 - a;
   cudaStream_t st = m->stream;
@@ -267,6 +258,7 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
   }
   mark(1);
   launch_gather_cfl<T>(VB, st, nv, ptr, ent, share, cf, V, (T*)s->R1.p, (T*)s->partial.p, cfl, ctl);
+  if (fixed_dt > 0.0) k_fix_dt<<<1, 1, 0, st>>>(ctl, fixed_dt);
   mark(2);
   if (s->p.scheme == RD_N1) {
     k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)s->W[a].p, (const T*)s->R1.p, ptr, ent, nullptr, V, gamma,
@@ -295,8 +287,8 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
   return RD_OK;
 }
 
-int launch_step_any(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = true) {
-  return s->pi == 0 ? launch_step<double>(s, a, ev, commit) : launch_step<float>(s, a, ev, commit);
+int launch_step_any(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = true, double fixed_dt = 0.0) {
+  return s->pi == 0 ? launch_step<double>(s, a, ev, commit, fixed_dt) : launch_step<float>(s, a, ev, commit, fixed_dt);
 }
 
 int read_ctl(const rd_state* s, DevCtl& c) {
@@ -395,6 +387,32 @@ int build_graph(rd_state* s) {
 }
 
 }  // namespace
+
+// Helpers shared with the adjoint translation unit.
+int rd::state_step(rd_state* s, int a, double fixed_dt) {
+  k_begin<<<1, 1, 0, s->m->stream>>>((DevCtl*)s->ctl.p, 0.0);
+  return launch_step_any(s, a, nullptr, true, fixed_dt);
+}
+int rd::state_read_ctl(const rd_state* s, DevCtl& c) { return read_ctl(s, c); }
+
+extern "C" int rd_run_fixed_dt(rd_state* s, int32_t n_steps, const double* dts) {
+  if (!s || n_steps < 0 || (n_steps > 0 && !dts)) return RD_EINVAL;
+  for (int32_t k = 0; k < n_steps; ++k)
+    if (!(dts[k] > 0.0) || !std::isfinite(dts[k])) return RD_EINVAL;
+  DevCtl c0;
+  CK(read_ctl(s, c0));
+  s->launched = c0.steps;
+  if (c0.status) return RD_ENONPHYSICAL;
+  k_begin<<<1, 1, 0, s->m->stream>>>((DevCtl*)s->ctl.p, 0.0);
+  for (int32_t k = 0; k < n_steps; ++k) {
+    CK(launch_step_any(s, (int)(s->launched & 1), nullptr, true, dts[k]));
+    s->launched++;
+  }
+  DevCtl c;
+  CK(read_ctl(s, c));
+  s->launched = c.steps;
+  return status_to_rd(c.status);
+}
 
 extern "C" int rd_state_init(rd_mesh* m, const double* W, const rd_params* p, rd_state** out) {
   if (!m || !W || !out || !valid_params(p)) return RD_EINVAL;
@@ -660,6 +678,7 @@ extern "C" void rd_state_destroy(rd_state* s) {
   DevBuf* bufs[] = {&s->Ws, &s->Zs, &s->R1, &s->share, &s->rec, &s->cfl, &s->partial, &s->ctl,
                     &s->cons_partial, &s->cons_out, &s->stage};
   for (DevBuf* b : bufs) dev_free(*b);
+  adjoint_free(s->adj);
   delete s;
 }
 

@@ -49,6 +49,15 @@ void launch_gather_cfl(int vblock, cudaStream_t st, int nv, const int* ptr, cons
 
 }  // namespace rd
 
+struct rd_adjoint_store;
+struct rd_state;
+namespace rd {
+void adjoint_free(rd_adjoint_store* a);
+// One committed step of a state reading buffer a (fixed_dt > 0 replaces the CFL dt).
+int state_step(rd_state* s, int a, double fixed_dt);
+int state_read_ctl(const rd_state* s, DevCtl& c);
+}
+
 // The mesh handle: host mesh store plus its device arrays.
 struct rd_mesh {
   rd::HostMesh h;
@@ -58,4 +67,21 @@ struct rd_mesh {
   // geometry per precision (0: double, 1: float): nx, ny, hl, area, lmax, V
   rd::DevBuf geo[2][6];
   bool geo_ready[2] = {false, false};
+};
+
+// The state handle: double-buffered vertex state, step scratch and the device
+// control block (dt, time, step count, status).
+struct rd_state {
+  rd_mesh* m = nullptr;
+  rd_params p{};
+  int pi = 0;     // 0: double, 1: float
+  size_t ts = 8;  // sizeof(T)
+  rd::DevBuf W[2], Z[2], spd[2];
+  rd::DevBuf Ws, Zs, R1, share, rec, cfl, partial, ctl, cons_partial, cons_out;
+  rd::DevBuf stage;        // [4][nv] double, caller vertex order (host I/O)
+  long long launched = 0;  // host view of the committed step count (parity of the buffers)
+  int tri_block = rd::TRI_BLOCK, vtx_block = rd::VTX_BLOCK;  // launch shapes (autotuned)
+  cudaGraphExec_t g2 = nullptr;  // two steps (even -> odd -> even)
+  bool graph_failed = false;
+  rd_adjoint_store* adj = nullptr;  // checkpoints and buffers of the adjoint rollout
 };

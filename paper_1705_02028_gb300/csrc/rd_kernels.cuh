@@ -150,6 +150,34 @@ struct LU4 {
 #pragma unroll
     for (int k = 0; k < 4; ++k) x[k] = y[k];
   }
+  // z = A^{-T} b (A = P^T L U): U^T y = b, L^T w = y, z = P^T w.
+  RD_HD void solve_t(const T b[4], T z[4]) const {
+    T y[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      T s = b[r];
+#pragma unroll
+      for (int c = 0; c < r; ++c) s -= a[c][r] * y[c];
+      y[r] = s * rdiag[r];
+    }
+#pragma unroll
+    for (int r = 3; r >= 0; --r) {
+      T s = y[r];
+#pragma unroll
+      for (int c = r + 1; c < 4; ++c) s -= a[c][r] * z[c];
+      z[r] = s;
+    }
+#pragma unroll
+    for (int k = 2; k >= 0; --k) {
+#pragma unroll
+      for (int r = k + 1; r < 4; ++r) {
+        bool sw = (piv[k] == r);
+        T p = z[k], q = z[r];
+        z[k] = sw ? q : p;
+        z[r] = sw ? p : q;
+      }
+    }
+  }
 };
 
 // Linearisation of one triangle and its N-scheme shares (Sec. 3.2, 3.3.1).
@@ -160,13 +188,15 @@ struct TriLin {
   LU4<T> lu;
   T phiT[4];
   T phiN[3][4];
+  // intermediates kept for the reverse sweep (dead in the forward kernels)
+  T Zb[4], gx[4], gy[4], Wh[3][4], win[4];
 };
 
 template <class T>
 RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3],
                                          T gamma, T eps, TriLin<T>& L) {
   const T third = T(1) / T(3);
-  T Zb[4];
+  T* Zb = L.Zb;
 #pragma unroll
   for (int k = 0; k < 4; ++k) Zb[k] = (Z[0][k] + Z[1][k] + Z[2][k]) * third;
   RoeState<T>& r = L.r;
@@ -187,7 +217,10 @@ RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3]
   r.g1v = r.g1 * r.v;
 
   // phi^T = dF/dZ(Zbar) gx + dG/dZ(Zbar) gy, g = sum_i (n_i / 2) Z_i
-  T gx[4] = {T(0), T(0), T(0), T(0)}, gy[4] = {T(0), T(0), T(0), T(0)};
+  T* gx = L.gx;
+  T* gy = L.gy;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) gx[k] = gy[k] = T(0);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     T ax = nx[i] * hl[i], ay = ny[i] * hl[i];
@@ -273,7 +306,7 @@ RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3]
   if (!L.lu.factor()) return ST_SINGULAR;
 
   // conservative linearised states W^_i = dW/dZ(Zbar) Z_i and sum_j K_j^- W^_j
-  T Wh[3][4];
+  T (*Wh)[4] = L.Wh;
   T S[4] = {T(0), T(0), T(0), T(0)};
   {
     T g = r.g1 / gamma, ig = T(1) / gamma;
@@ -290,7 +323,7 @@ RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3]
     }
   }
   // N scheme: phi_i^N = K_i^+ (W^_i - N^ sum_j K_j^- W^_j)
-  T win[4];
+  T* win = L.win;
   L.lu.solve(S, win);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -598,7 +631,7 @@ __global__ void __launch_bounds__(BLOCK) k_gather_cfl(int nv, const int* __restr
 
 // Vertex state -> parameter vector Z and |v| + c; returns false if non-physical.
 template <class T>
-__device__ __forceinline__ bool vertex_Z(const T W[4], T gamma, T Z[4], T& spd) {
+RD_HD bool vertex_Z(const T W[4], T gamma, T Z[4], T& spd) {
   T rho = W[0];
   if (!(rho > T(0))) return false;
   T u = W[1] / rho, v = W[2] / rho;
