@@ -32,6 +32,18 @@
 
 namespace rd {
 
+// Minimum resident 256-thread blocks per SM asked of the triangle kernels: the
+// FP32 kernels are latency bound and gain from 24 warps per SM (85 registers);
+// the FP64 kernels are bound by the FP64 pipe and keep their registers.
+template <class T>
+struct TriOcc {
+  static constexpr int value = 1;
+};
+template <>
+struct TriOcc<float> {
+  static constexpr int value = 3;
+};
+
 template <class T>
 struct DevGeo {
   const T* nx;    // [3][nt] unit inward normals
@@ -482,7 +494,7 @@ RD_HD int stage2_body(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], cons
 // cfl [nt] = l_max^T max_j (|v_j| + c_j).
 // ---------------------------------------------------------------------------
 template <class T, int SCHEME>
-__global__ void __launch_bounds__(256) k_tri_stage1(int nt, int nv, const int* __restrict__ tri, DevGeo<T> g,
+__global__ void __launch_bounds__(256, TriOcc<T>::value) k_tri_stage1(int nt, int nv, const int* __restrict__ tri, DevGeo<T> g,
                                                     const T* __restrict__ Z, const T* __restrict__ spd,
                                                     T gamma, T eps, T* __restrict__ share,
                                                     T* __restrict__ rec, T* __restrict__ cfl, DevCtl* ctl) {
@@ -563,6 +575,37 @@ __device__ __forceinline__ T warp_min(T v) {
   return v;
 }
 
+// Sum of the corner records of one vertex in CSR order (and, if CFL, of the
+// triangles' CFL terms): indices and records of several corners are loaded
+// before any is added, so the loads are in flight together; the sums keep
+// the sequential CSR order.
+template <class T, bool CFL>
+__device__ __forceinline__ void gather_corners(int e0, int e1, const int* __restrict__ ent,
+                                               const T* __restrict__ share, const T* __restrict__ cfl, T r[4],
+                                               T& sig) {
+  // 8 corners in flight for 16-byte float records, 2 for 32-byte double records
+  constexpr int C = sizeof(T) == 4 ? 8 : 2;
+  for (int eb = e0; eb < e1; eb += C) {
+    int te[C];
+    T q[C][4], c[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) te[j] = (eb + j < e1) ? __ldg(ent + eb + j) : -1;
+#pragma unroll
+    for (int j = 0; j < C; ++j)
+      if (te[j] >= 0) {
+        ld4(share + (size_t)te[j] * 4, q[j]);
+        if (CFL) c[j] = __ldg(cfl + te[j] / 3);
+      }
+#pragma unroll
+    for (int j = 0; j < C; ++j)
+      if (te[j] >= 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) r[k] += q[j][k];
+        if (CFL) sig += c[j];
+      }
+  }
+}
+
 template <class T, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_gather_cfl(int nv, const int* __restrict__ ptr, const int* __restrict__ ent,
                                                       const T* __restrict__ share, const T* __restrict__ cfl,
@@ -576,15 +619,7 @@ __global__ void __launch_bounds__(BLOCK) k_gather_cfl(int nv, const int* __restr
   if (i < nv) {
     T r[4] = {T(0), T(0), T(0), T(0)};
     T sig = T(0);
-    int e0 = __ldg(ptr + i), e1 = __ldg(ptr + i + 1);
-    for (int e = e0; e < e1; ++e) {
-      int te = __ldg(ent + e);
-      T q[4];
-      ld4(share + (size_t)te * 4, q);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) r[k] += q[k];
-      sig += __ldg(cfl + te / 3);
-    }
+    gather_corners<T, true>(__ldg(ptr + i), __ldg(ptr + i + 1), ent, share, cfl, r, sig);
     st4(R1 + 4 * (size_t)i, r);
     ratio = T(2) * __ldg(V + i) / sig;
   }
@@ -661,13 +696,8 @@ __global__ void __launch_bounds__(512) k_update(int nv, const T* __restrict__ Wi
   T r[4];
   if (share) {
     r[0] = r[1] = r[2] = r[3] = T(0);
-    int e0 = __ldg(ptr + i), e1 = __ldg(ptr + i + 1);
-    for (int e = e0; e < e1; ++e) {
-      T q[4];
-      ld4(share + (size_t)__ldg(ent + e) * 4, q);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) r[k] += q[k];
-    }
+    T unused = T(0);
+    gather_corners<T, false>(__ldg(ptr + i), __ldg(ptr + i + 1), ent, share, nullptr, r, unused);
   } else {
     load_vec4(R, i, r);
   }
@@ -705,7 +735,7 @@ __global__ void k_prepare(int nv, const T* __restrict__ W, T gamma, T* __restric
 // Stage-2 triangle kernel: total residuals at (W^n, W*) -> share [nt][3][4].
 // ---------------------------------------------------------------------------
 template <class T, int SCHEME>
-__global__ void __launch_bounds__(256) k_tri_stage2(int nt, int nv, const int* __restrict__ tri, DevGeo<T> g,
+__global__ void __launch_bounds__(256, TriOcc<T>::value) k_tri_stage2(int nt, int nv, const int* __restrict__ tri, DevGeo<T> g,
                                                     const T* __restrict__ Zs, const T* __restrict__ Wn,
                                                     const T* __restrict__ Ws, const T* __restrict__ rec,
                                                     T gamma, T eps, T* __restrict__ share, DevCtl* ctl,
