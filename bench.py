@@ -33,12 +33,15 @@ if ROOT not in sys.path:
 METRIC = "triangle-updates/s FP64/FP32 & % HBM roofline; batched & adjoint vs plain step"
 UNIT = "triangle-updates/s"
 WORKLOADS = {
-    # name: (side, state, scheme)
-    "khi4096_B2": (4096, "khi", "B2"),
-    "khi2048_B2": (2048, "khi", "B2"),
-    "sod1024_B2": (1024, "sod", "B2"),
-    "vortex64_N1": (64, "vortex", "N1"),
-    "batch64_B2": (None, "batch", "B2"),
+    # name: (side, state, scheme, mesh kind)
+    "khi4096_B2": (4096, "khi", "B2", "grid"),
+    "khi2048_B2": (2048, "khi", "B2", "grid"),
+    "sod1024_B2": (1024, "sod", "B2", "grid"),
+    "vortex64_N1": (64, "vortex", "N1", "grid"),
+    "batch64_B2": (None, "batch", "B2", "grid"),
+    # unstructured: jittered vertices, Delaunay diagonals, labels scrambled (seed 6)
+    "khi4096j_B2": (4096, "khi", "B2", "jittered"),
+    "khi2048j_B2": (2048, "khi", "B2", "jittered"),
 }
 # algorithmic HBM bytes of one triangle-update (whole step) for the two-stage
 # scheme: W^n, xy, V read and R1, sigma written in the first pass; W^n, R1, V,
@@ -68,6 +71,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="khi4096_B2")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--reorder", choices=["none", "morton", "rcm"], default="morton",
+                    help="vertex/triangle reordering of the mesh store")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 companion measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form companion measurement")
@@ -109,8 +114,11 @@ def max_over_ranks(x, ws):
 
 def build_inputs(workload):
     from paper_1705_02028_gb300 import inputs
-    side, state, scheme = WORKLOADS[workload]
-    mesh = inputs.periodic_grid(side)
+    side, state, scheme, kind = WORKLOADS[workload]
+    if kind == "jittered":
+        mesh = inputs.jittered_grid(side, relabel_seed=6)
+    else:
+        mesh = inputs.periodic_grid(side)
     W0 = {"khi": inputs.khi_state, "sod": inputs.sod_like_state, "vortex": inputs.vortex_state}[state](mesh)
     return mesh, W0, scheme
 
@@ -238,7 +246,7 @@ def ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     mesh, W0, scheme = build_inputs(args.workload)
     nt, nv = mesh.nt, mesh.nv
-    m = binding.Mesh(mesh, reorder="morton")
+    m = binding.Mesh(mesh, reorder=args.reorder)
     s_bytes = 8 if args.precision == "fp64" else 4
 
     clocks = ClockSampler(local)
@@ -316,7 +324,8 @@ def ours(args, ws, rank, local):
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
             "data": "synthetic (seeded KHI shear layer / generated periodic triangulation)",
             "config": {"workload": args.workload, "triangles": nt, "vertices": nv, "scheme": scheme,
-                       "cfl": 0.8, "precision": args.precision, "reorder": "morton",
+                       "cfl": 0.8, "precision": args.precision, "reorder": args.reorder,
+                       "mesh": WORKLOADS[args.workload][3],
                        "l2": "inputs larger than L2 (%.0f MB vertex state)" % (4 * nv * s_bytes / 1e6),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "ms_per_step_graph": ms_graph, "per_kernel_ms": per_kernel,
@@ -437,12 +446,20 @@ def adjoint_measure(args, ws, n_steps=200, ckpt_every=20):
             "cost_vs_plain_step": (t_fwd + t_bwd) / t_plain, "grad_norm": float(np.linalg.norm(g))}
 
 
-def oracle_sample_rate(scheme, steps, nthreads):
+def sample_mesh(workload):
+    """1024^2 periodic mesh of the workload's kind (1/16 of a 4096^2 workload's triangles)."""
+    from paper_1705_02028_gb300 import inputs
+    if WORKLOADS[workload][3] == "jittered":
+        return inputs.jittered_grid(1024, relabel_seed=6)
+    return inputs.periodic_grid(1024)
+
+
+def oracle_sample_rate(workload, scheme, steps, nthreads):
     """Oracle triangle-updates/s on the sample: the KHI state on a 1024^2 periodic mesh
-    (1/16 of the 4096^2 workload's triangles), `steps` full steps."""
+    of the workload's kind, `steps` full steps."""
     import oracle
     from paper_1705_02028_gb300 import inputs
-    mesh = inputs.periodic_grid(1024)
+    mesh = sample_mesh(workload)
     W0 = inputs.khi_state(mesh)
     t0 = time.perf_counter()
     oracle.run(mesh, W0, scheme, nsteps=steps, nthreads=nthreads)
@@ -455,13 +472,13 @@ def cpu_baseline(args):
     scheme = WORKLOADS[args.workload][2]
     nth = os.cpu_count() or 1
     oracle.build()
-    rate, secs, nts = oracle_sample_rate(scheme, 2, nth)
+    rate, secs, nts = oracle_sample_rate(args.workload, scheme, 2, nth)
     if secs < 8.0:  # aim for ~10-30 s of CPU work
         extra = max(1, int(10.0 / max(secs / 2, 1e-3)))
-        rate, secs, nts = oracle_sample_rate(scheme, min(extra, 40), nth)
+        rate, secs, nts = oracle_sample_rate(args.workload, scheme, min(extra, 40), nth)
     return {"value": rate, "unit": UNIT, "cores": nth, "kind": "oracle", "seconds": secs,
             "sample": f"{scheme} steps of the KHI state on a 1024x1024 periodic mesh ({nts} triangles, "
-                      f"1/16 of the workload), FP64 C++ oracle, OpenMP over {nth} host threads"}
+                      f"1/16 of the workload, {WORKLOADS[args.workload][3]} mesh), FP64 C++ oracle, OpenMP over {nth} host threads"}
 
 
 def reference(args, ws, rank):
@@ -472,7 +489,7 @@ def reference(args, ws, rank):
     nth = os.cpu_count() or 1
     oracle.build()
     from paper_1705_02028_gb300 import inputs
-    mesh = inputs.periodic_grid(1024)
+    mesh = sample_mesh(args.workload)
     W = inputs.khi_state(mesh)
     for _ in range(args.warmup):
         W, _ = oracle.run(mesh, W, scheme, nsteps=1, nthreads=nth)
@@ -482,7 +499,7 @@ def reference(args, ws, rank):
     secs = time.perf_counter() - t0
     ms_step = secs / args.steps * 1e3
     value = mesh.nt / (ms_step * 1e-3)
-    sample = (f"each step: one {scheme} step of the KHI state on a 1024x1024 periodic mesh "
+    sample = (f"each step: one {scheme} step of the KHI state on a 1024x1024 {WORKLOADS[args.workload][3]} periodic mesh "
               f"({mesh.nt} triangles, 1/16 of the 4096^2 workload), FP64 C++ oracle on {nth} host threads")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,

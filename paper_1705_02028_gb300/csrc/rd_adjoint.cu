@@ -297,7 +297,7 @@ int backward(rd_state* s, rd_adjoint_store* A, const double* dLdWf, double* dLdW
   // stage-1 pass at W^n (shares, record, CFL terms), then W*, Z* with the recorded dt
   auto stage1_and_wstar = [&](const T* Wn, double dt, T* Wout, T* Zout) {
     k_prepare<T><<<gv, ADJ_VTX_BLOCK, 0, st>>>(nv, Wn, gamma, Zn, spd, ctl);
-    k_tri_stage1<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, nv, tri, g, Zn, spd, gamma, eps, share, two ? rec : nullptr,
+    k_tri_stage1<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, nv, tri, g, Zn, spd, Gas<T>::of(gamma), eps, share, two ? rec : nullptr,
                                                       cf, ctl);
     launch_gather_cfl<T>(VTX_BLOCK, st, nv, ptr, ent, share, cf, V, (T*)A->R1.p, (T*)A->partial.p, cflnum, ctl);
     k_set_dt<<<1, 1, 0, st>>>(ctl, dt);
@@ -316,7 +316,7 @@ int backward(rd_state* s, rd_adjoint_store* A, const double* dLdWf, double* dLdW
       if (two) {
         stage1_and_wstar(Wn, dt, Ws, Zs);
         k_mask1<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, Zn, gamma, eps, mask1 + (size_t)j * nt);
-        k_tri_stage2<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, nv, tri, g, Zs, Wn, Ws, rec, gamma, eps, share, ctl);
+        k_tri_stage2<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, nv, tri, g, Zs, Wn, Ws, rec, Gas<T>::of(gamma), eps, share, ctl);
         k_mask2<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, Zs, Wn, Ws, rec, (T)dt, gamma, eps,
                                                     mask2 + (size_t)j * nt);
         k_update<T><<<gv, ADJ_VTX_BLOCK, 0, st>>>(nv, Ws, nullptr, ptr, ent, share, V, gamma, Wn1, Zs, nullptr, ctl);
@@ -440,7 +440,7 @@ int branch_masks(rd_state* s, uint64_t* mask1, uint64_t* mask2) {
   const T* Wn = (const T*)s->W[(int)(c.steps & 1)].p;
   CU(cudaMemsetAsync(ctl, 0, sizeof(DevCtl), st));
   k_prepare<T><<<gv, ADJ_VTX_BLOCK, 0, st>>>(nv, Wn, gamma, (T*)A->Zn.p, (T*)A->spd.p, ctl);
-  k_tri_stage1<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, nv, tri, g, (const T*)A->Zn.p, (const T*)A->spd.p, gamma, eps,
+  k_tri_stage1<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, nv, tri, g, (const T*)A->Zn.p, (const T*)A->spd.p, Gas<T>::of(gamma), eps,
                                                     (T*)A->share.p, (T*)A->rec.p, (T*)A->cfl.p, ctl);
   launch_gather_cfl<T>(VTX_BLOCK, st, nv, ptr, ent, (const T*)A->share.p, (const T*)A->cfl.p, V, (T*)A->R1.p,
                        (T*)A->partial.p, cflnum, ctl);

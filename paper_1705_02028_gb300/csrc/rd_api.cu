@@ -247,13 +247,13 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
   mark(0);
   switch (s->p.scheme) {
     case RD_N1:
-      k_tri_stage1<T, RD_N1><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, gamma, eps, share, nullptr, cf, ctl);
+      k_tri_stage1<T, RD_N1><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, nullptr, cf, ctl);
       break;
     case RD_B2:
-      k_tri_stage1<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, gamma, eps, share, rec, cf, ctl);
+      k_tri_stage1<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, rec, cf, ctl);
       break;
     default:
-      k_tri_stage1<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, gamma, eps, share, rec, cf, ctl);
+      k_tri_stage1<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, rec, cf, ctl);
       break;
   }
   mark(1);
@@ -272,10 +272,10 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
     mark(3);
     if (s->p.scheme == RD_B2)
       k_tri_stage2<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
-                                                       (const T*)s->Ws.p, rec, gamma, eps, share, ctl);
+                                                       (const T*)s->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl);
     else
       k_tri_stage2<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
-                                                         (const T*)s->Ws.p, rec, gamma, eps, share, ctl);
+                                                         (const T*)s->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl);
     mark(4);
     k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)s->Ws.p, nullptr, ptr, ent, share, V, gamma,
                                           (T*)s->W[b].p, (T*)s->Z[b].p, (T*)s->spd[b].p, ctl);

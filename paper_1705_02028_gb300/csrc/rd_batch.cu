@@ -74,13 +74,13 @@ int batch_step(rd_batch* b, int a, cudaEvent_t* ev, bool commit) {
   const T* Sa = (const T*)b->spd[a].p;
   switch (b->p.scheme) {
     case RD_N1:
-      k_tri_stage1<T, RD_N1><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, gamma, eps, share, nullptr, cf, ctl);
+      k_tri_stage1<T, RD_N1><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, nullptr, cf, ctl);
       break;
     case RD_B2:
-      k_tri_stage1<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, gamma, eps, share, rec, cf, ctl);
+      k_tri_stage1<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, rec, cf, ctl);
       break;
     default:
-      k_tri_stage1<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, gamma, eps, share, rec, cf, ctl);
+      k_tri_stage1<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, rec, cf, ctl);
       break;
   }
   mark(1);
@@ -100,10 +100,10 @@ int batch_step(rd_batch* b, int a, cudaEvent_t* ev, bool commit) {
     mark(3);
     if (b->p.scheme == RD_B2)
       k_tri_stage2<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)b->Zs.p, (const T*)b->W[a].p,
-                                                (const T*)b->Ws.p, rec, gamma, eps, share, ctl, dtm, tm);
+                                                (const T*)b->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl, dtm, tm);
     else
       k_tri_stage2<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)b->Zs.p, (const T*)b->W[a].p,
-                                                  (const T*)b->Ws.p, rec, gamma, eps, share, ctl, dtm, tm);
+                                                  (const T*)b->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl, dtm, tm);
     mark(4);
     k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)b->Ws.p, nullptr, ptr, ent, share, V, gamma, (T*)b->W[c].p,
                                    (T*)b->Z[c].p, (T*)b->spd[c].p, ctl, dtm, vm);

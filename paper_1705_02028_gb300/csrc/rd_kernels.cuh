@@ -32,17 +32,81 @@
 
 namespace rd {
 
-// Minimum resident 256-thread blocks per SM asked of the triangle kernels: the
-// FP32 kernels are latency bound and gain from 24 warps per SM (85 registers);
-// the FP64 kernels are bound by the FP64 pipe and keep their registers.
-template <class T>
+// Minimum resident 256-thread blocks per SM asked of the triangle kernels.  The
+// FP32 kernels are latency bound: stage 1 runs fastest at 24 warps per SM (85
+// registers), stage 2, which holds three vertex states per corner, at 16 warps
+// (128 registers; 24 warps spill).  The FP64 kernels are bound by the FP64
+// pipe and keep their registers.
+template <class T, int STAGE>
 struct TriOcc {
   static constexpr int value = 1;
 };
 template <>
-struct TriOcc<float> {
+struct TriOcc<float, 1> {
   static constexpr int value = 3;
 };
+template <>
+struct TriOcc<float, 2> {
+  static constexpr int value = 2;
+};
+
+// Constants of the ideal-gas closure, formed once per launch on the host so that
+// no thread divides by gamma: gamma, g1 = gamma - 1, g = (gamma - 1) / gamma,
+// ig = 1 / gamma.  Host and device divisions are both correctly rounded, so
+// the values equal those a thread would compute.
+template <class T>
+struct Gas {
+  T gamma, g1, g, ig;
+  static RD_HD Gas of(T gamma) {
+    Gas q;
+    q.gamma = gamma;
+    q.g1 = gamma - T(1);
+    q.g = q.g1 / gamma;
+    q.ig = T(1) / gamma;
+    return q;
+  }
+};
+
+// Magnitude comparisons through the IEEE-754 bit patterns.  For numbers that
+// are not NaN the integer order of |x|'s bit pattern is the numeric order of
+// |x|, so in double precision these run on the integer pipe instead of the
+// FP64 pipe that the triangle kernels saturate.  Results equal the
+// floating-point comparisons for every non-NaN input; other scalar types
+// (float, the operation-counting type) use the plain comparisons.
+RD_HD long long mag_bits(double x) {
+#ifdef __CUDA_ARCH__
+  return __double_as_longlong(x) & 0x7fffffffffffffffLL;
+#else
+  long long b;
+  __builtin_memcpy(&b, &x, sizeof b);
+  return b & 0x7fffffffffffffffLL;
+#endif
+}
+template <class T>
+RD_HD bool mag_less(T a, T b) {  // |a| < |b|
+  return fabs(a) < fabs(b);
+}
+RD_HD bool mag_less(double a, double b) { return mag_bits(a) < mag_bits(b); }
+template <class T>
+RD_HD bool mag_positive(T a) {  // |a| > 0 (false for NaN)
+  return fabs(a) > T(0);
+}
+RD_HD bool mag_positive(double a) {
+  return (unsigned long long)(mag_bits(a) - 1) < 0x7ff0000000000000ULL;
+}
+template <class T>
+RD_HD bool positive(T a) {  // a > 0 (false for NaN)
+  return a > T(0);
+}
+RD_HD bool positive(double a) {
+#ifdef __CUDA_ARCH__
+  long long b = __double_as_longlong(a);
+#else
+  long long b;
+  __builtin_memcpy(&b, &a, sizeof b);
+#endif
+  return (unsigned long long)(b - 1) < 0x7ff0000000000000ULL;
+}
 
 template <class T>
 struct DevGeo {
@@ -69,8 +133,7 @@ struct NodeSys {
 // Regularised |lambda|: (lambda^2 + delta^2) / (2 delta) below delta (C^1), i2d = 1 / (2 delta).
 template <class T>
 RD_HD T abs_reg(T lam, T delta, T i2d) {
-  T a = fabs(lam);
-  return (a < delta) ? (lam * lam + delta * delta) * i2d : a;
+  return mag_less(lam, delta) ? (lam * lam + delta * delta) * i2d : fabs(lam);
 }
 
 // K^{+-} in closed form (App. A).  With the right eigenvectors of App. A,
@@ -107,11 +170,13 @@ struct LU4 {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       int p = k;
-      T best = fabs(a[k][k]);
+      T best = a[k][k];
 #pragma unroll
       for (int r = k + 1; r < 4; ++r) {
-        T v = fabs(a[r][k]);
-        if (v > best) { best = v; p = r; }
+        if (mag_less(best, a[r][k])) {
+          best = a[r][k];
+          p = r;
+        }
       }
       if (k < 3) piv[k] = p;
 #pragma unroll
@@ -124,7 +189,7 @@ struct LU4 {
           a[r][c] = sw ? x : y;
         }
       }
-      ok = ok && (best > T(0));
+      ok = ok && mag_positive(best);
       T inv = T(1) / a[k][k];
       rdiag[k] = inv;
 #pragma unroll
@@ -206,20 +271,20 @@ struct TriLin {
 
 template <class T>
 RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3],
-                                         T gamma, T eps, TriLin<T>& L) {
+                                         const Gas<T>& gas, T eps, TriLin<T>& L) {
   const T third = T(1) / T(3);
   T* Zb = L.Zb;
 #pragma unroll
   for (int k = 0; k < 4; ++k) Zb[k] = (Z[0][k] + Z[1][k] + Z[2][k]) * third;
   RoeState<T>& r = L.r;
-  r.g1 = gamma - T(1);
+  r.g1 = gas.g1;
   T iz = T(1) / Zb[0];
   r.u = Zb[1] * iz;
   r.v = Zb[2] * iz;
   r.h = Zb[3] * iz;
   r.q2h = (r.u * r.u + r.v * r.v) * T(0.5);
   T c2 = r.g1 * (r.h - r.q2h);
-  if (!(c2 > T(0))) return ST_ROE;
+  if (!positive(c2)) return ST_ROE;
   r.c = sqrt(c2);
   r.ic2 = T(1) / c2;
   r.ic2h = r.ic2 * T(0.5);
@@ -243,7 +308,7 @@ RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3]
     }
   }
   {
-    T g = r.g1 / gamma;
+    const T g = gas.g;
     L.phiT[0] = Zb[1] * gx[0] + Zb[0] * gx[1] + Zb[2] * gy[0] + Zb[0] * gy[2];
     L.phiT[1] = g * Zb[3] * gx[0] + (T(2) - g) * Zb[1] * gx[1] - g * Zb[2] * gx[2] + g * Zb[0] * gx[3] +
                 Zb[2] * gy[1] + Zb[1] * gy[2];
@@ -262,7 +327,7 @@ RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3]
     T delta = eps * r.c * hl[i];
     T la[3] = {(n.w + r.c) * hl[i], (n.w - r.c) * hl[i], n.w * hl[i]};
     T i2d = T(0);
-    if (fabs(la[0]) < delta || fabs(la[1]) < delta || fabs(la[2]) < delta) i2d = T(0.5) / delta;
+    if (mag_less(la[0], delta) || mag_less(la[1], delta) || mag_less(la[2], delta)) i2d = T(0.5) / delta;
     T ab[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) ab[k] = abs_reg(la[k], delta, i2d);
@@ -321,7 +386,7 @@ RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3]
   T (*Wh)[4] = L.Wh;
   T S[4] = {T(0), T(0), T(0), T(0)};
   {
-    T g = r.g1 / gamma, ig = T(1) / gamma;
+    const T g = gas.g, ig = gas.ig;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       Wh[i][0] = T(2) * Zb[0] * Z[i][0];
@@ -347,6 +412,11 @@ RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3]
   return 0;
 }
 
+template <class T>
+RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3], T gamma, T eps, TriLin<T>& L) {
+  return linearise(Z, nx, ny, hl, Gas<T>::of(gamma), eps, L);
+}
+
 // beta_i x = -K_i^+ N^ x for the three nodes (Sec. 3.3.2).
 template <class T>
 RD_HD void lda_apply(const TriLin<T>& L, const T x[4], T out[3][4]) {
@@ -368,8 +438,8 @@ RD_HD void blend(const T tot[4], const T N[3][4], const T lda[3][4], T out[3][4]
   for (int k = 0; k < 4; ++k) {
     T num = fabs(tot[k]);
     T den = fabs(N[0][k]) + fabs(N[1][k]) + fabs(N[2][k]);
-    den = den > num ? den : num;
-    T th = den > T(0) ? num / den : T(0);
+    den = mag_less(num, den) ? den : num;
+    T th = mag_positive(den) ? num / den : T(0);
 #pragma unroll
     for (int i = 0; i < 3; ++i) out[i][k] = th * N[i][k] + (T(1) - th) * lda[i][k];
   }
@@ -419,10 +489,10 @@ __device__ __forceinline__ void load_vec4(const T* __restrict__ A, int i, T out[
 // RD_LDA2 -> phi^LDA, RD_B2 -> phi^B (Sec. 3.3).  rec (two-stage schemes):
 // phi^N_0..2 and phi^T at W^n, reused by stage 2.  Returns an ST_* status.
 template <class T, int SCHEME>
-RD_HD int stage1_body(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3], T gamma, T eps,
+RD_HD int stage1_body(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3], const Gas<T>& gas, T eps,
                       T out[3][4], T rec[16]) {
   TriLin<T> L;
-  int st = linearise(Z, nx, ny, hl, gamma, eps, L);
+  int st = linearise(Z, nx, ny, hl, gas, eps, L);
   if (st) return st;
   if (SCHEME == RD_N1) {
 #pragma unroll
@@ -457,9 +527,9 @@ RD_HD int stage1_body(const T Z[3][4], const T nx[3], const T ny[3], const T hl[
 //   Phi_i     = Theta Phi^N_i + (I - Theta) Phi^LDA_i, Theta from (Phi^T, Phi^N)
 template <class T, int SCHEME>
 RD_HD int stage2_body(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], const T rec[16], const T nx[3],
-                      const T ny[3], const T hl[3], T area, T dt, T gamma, T eps, T out[3][4]) {
+                      const T ny[3], const T hl[3], T area, T dt, const Gas<T>& gas, T eps, T out[3][4]) {
   TriLin<T> L;
-  int st = linearise(Zs, nx, ny, hl, gamma, eps, L);
+  int st = linearise(Zs, nx, ny, hl, gas, eps, L);
   if (st) return st;
   T a3 = area * (T(1) / T(3));
   T idt = T(1) / dt;
@@ -489,14 +559,25 @@ RD_HD int stage2_body(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], cons
   return 0;
 }
 
+template <class T, int SCHEME>
+RD_HD int stage1_body(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3], T gamma, T eps, T out[3][4],
+                      T rec[16]) {
+  return stage1_body<T, SCHEME>(Z, nx, ny, hl, Gas<T>::of(gamma), eps, out, rec);
+}
+template <class T, int SCHEME>
+RD_HD int stage2_body(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], const T rec[16], const T nx[3],
+                      const T ny[3], const T hl[3], T area, T dt, T gamma, T eps, T out[3][4]) {
+  return stage2_body<T, SCHEME>(Zs, Wn, Ws, rec, nx, ny, hl, area, dt, Gas<T>::of(gamma), eps, out);
+}
+
 // ---------------------------------------------------------------------------
 // Stage-1 triangle kernel: share [nt][3][4]; rec [nt][16] (two-stage only);
 // cfl [nt] = l_max^T max_j (|v_j| + c_j).
 // ---------------------------------------------------------------------------
 template <class T, int SCHEME>
-__global__ void __launch_bounds__(256, TriOcc<T>::value) k_tri_stage1(int nt, int nv, const int* __restrict__ tri, DevGeo<T> g,
+__global__ void __launch_bounds__(256, (TriOcc<T, 1>::value)) k_tri_stage1(int nt, int nv, const int* __restrict__ tri, DevGeo<T> g,
                                                     const T* __restrict__ Z, const T* __restrict__ spd,
-                                                    T gamma, T eps, T* __restrict__ share,
+                                                    Gas<T> gas, T eps, T* __restrict__ share,
                                                     T* __restrict__ rec, T* __restrict__ cfl, DevCtl* ctl) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt || ctl->stop) return;
@@ -507,12 +588,12 @@ __global__ void __launch_bounds__(256, TriOcc<T>::value) k_tri_stage1(int nt, in
   for (int c = 0; c < 3; ++c) load_vec4(Z, v[c], Zc[c]);
   {
     T s0 = __ldg(spd + v[0]), s1 = __ldg(spd + v[1]), s2 = __ldg(spd + v[2]);
-    T lam = s0 > s1 ? s0 : s1;
-    lam = lam > s2 ? lam : s2;
+    T lam = mag_less(s1, s0) ? s0 : s1;  // speeds are >= 0
+    lam = mag_less(s2, lam) ? lam : s2;
     cfl[t] = __ldg(g.lmax + t) * lam;
   }
   T out[3][4], r[16];
-  int st = stage1_body<T, SCHEME>(Zc, nx, ny, hl, gamma, eps, out, r);
+  int st = stage1_body<T, SCHEME>(Zc, nx, ny, hl, gas, eps, out, r);
   if (st) {
     atomicOr(&ctl->status, st);
     return;
@@ -735,10 +816,10 @@ __global__ void k_prepare(int nv, const T* __restrict__ W, T gamma, T* __restric
 // Stage-2 triangle kernel: total residuals at (W^n, W*) -> share [nt][3][4].
 // ---------------------------------------------------------------------------
 template <class T, int SCHEME>
-__global__ void __launch_bounds__(256, TriOcc<T>::value) k_tri_stage2(int nt, int nv, const int* __restrict__ tri, DevGeo<T> g,
+__global__ void __launch_bounds__(256, (TriOcc<T, 2>::value)) k_tri_stage2(int nt, int nv, const int* __restrict__ tri, DevGeo<T> g,
                                                     const T* __restrict__ Zs, const T* __restrict__ Wn,
                                                     const T* __restrict__ Ws, const T* __restrict__ rec,
-                                                    T gamma, T eps, T* __restrict__ share, DevCtl* ctl,
+                                                    Gas<T> gas, T eps, T* __restrict__ share, DevCtl* ctl,
                                                     const double* __restrict__ dtm = nullptr,
                                                     const uint16_t* __restrict__ tmesh = nullptr) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -757,7 +838,7 @@ __global__ void __launch_bounds__(256, TriOcc<T>::value) k_tri_stage2(int nt, in
   for (int k = 0; k < 4; ++k) ld4(rp + 4 * k, r + 4 * k);
   T out[3][4];
   T dt = dtm ? (T)__ldg(dtm + __ldg(tmesh + t)) : (T)ctl->dt;
-  int st = stage2_body<T, SCHEME>(Zc, wn, ws, r, nx, ny, hl, __ldg(g.area + t), dt, gamma, eps, out);
+  int st = stage2_body<T, SCHEME>(Zc, wn, ws, r, nx, ny, hl, __ldg(g.area + t), dt, gas, eps, out);
   if (st) {
     atomicOr(&ctl->status, st);
     return;

@@ -72,11 +72,12 @@ template <int SCHEME>
 void count(int stage, Counts& out) {
   Flop Z[3][4], Zs[3][4], Wn[3][4], Ws[3][4], nx[3], ny[3], hl[3], area, o[3][4], rec[16];
   sample(Z, Zs, Wn, Ws, nx, ny, hl, area);
+  const rd::Gas<Flop> gas = rd::Gas<Flop>::of(Flop(1.4));  // formed on the host, once per launch
   g_cnt = Counts();
-  rd::stage1_body<Flop, SCHEME>(Z, nx, ny, hl, Flop(1.4), Flop(1e-6), o, rec);
+  rd::stage1_body<Flop, SCHEME>(Z, nx, ny, hl, gas, Flop(1e-6), o, rec);
   if (stage == 2) {
     g_cnt = Counts();
-    rd::stage2_body<Flop, SCHEME>(Zs, Wn, Ws, rec, nx, ny, hl, area, Flop(1e-3), Flop(1.4), Flop(1e-6), o);
+    rd::stage2_body<Flop, SCHEME>(Zs, Wn, Ws, rec, nx, ny, hl, area, Flop(1e-3), gas, Flop(1e-6), o);
   }
   out = g_cnt;
 }

@@ -106,6 +106,109 @@ def periodic_grid(Nx: int, Ny: int | None = None, Lx: float = 1.0, Ly: float | N
                 orig_vertex=orig, Nx=Nx, Ny=Ny)
 
 
+def _incircle(ax, ay, bx, by, cx, cy, dx, dy):
+    """> 0 when d lies inside the circle through the counter-clockwise a, b, c."""
+    adx, ady = ax - dx, ay - dy
+    bdx, bdy = bx - dx, by - dy
+    cdx, cdy = cx - dx, cy - dy
+    return ((adx * adx + ady * ady) * (bdx * cdy - cdx * bdy)
+            - (bdx * bdx + bdy * bdy) * (adx * cdy - cdx * ady)
+            + (cdx * cdx + cdy * cdy) * (adx * bdy - bdx * ady))
+
+
+def jittered_grid(Nx: int, Ny: int | None = None, Lx: float = 1.0, Ly: float | None = None,
+                  jitter: float = 0.2, seed: int = 6, diagonal: str = "delaunay",
+                  relabel_seed: int | None = None) -> Mesh:
+    """Unstructured periodic triangulation: the grid of ``periodic_grid`` with every
+    vertex moved by a seeded offset of at most ``jitter`` cell widths per axis, and
+    each (convex) cell split along the diagonal that the empty-circumcircle (Delaunay)
+    test picks (``diagonal="delaunay"``) or along a seeded random one ("random").
+
+    Vertex valences then range from 4 to 8 instead of being 6 everywhere, the edge
+    lengths and angles vary from triangle to triangle, and the vertex and
+    triangle labels can be scrambled with ``relabel_seed`` -- a stand-in for the
+    unstructured Delaunay meshes of Sec. 4.1 that keeps the vertex count exact.
+    Offsets come from SplitMix64(seed xor (2 id)) and SplitMix64(seed xor (2 id + 1))
+    of the structured vertex id; stored coordinates are wrapped into [0, L).
+    jitter <= 0.2 keeps every cell strictly convex, so both diagonals are valid.
+    """
+    if Ny is None:
+        Ny = Nx
+    if Ly is None:
+        Ly = Lx * Ny / Nx
+    if Nx < 3 or Ny < 3:
+        raise ValueError("jittered_grid needs at least 3 vertices per side")
+    if not (0.0 <= jitter <= 0.2):
+        raise ValueError("jitter must lie in [0, 0.2]")
+    if diagonal not in ("delaunay", "random"):
+        raise ValueError("diagonal must be 'delaunay' or 'random'")
+    hx, hy = Lx / Nx, Ly / Ny
+    i = np.arange(Nx, dtype=np.int64)
+    j = np.arange(Ny, dtype=np.int64)
+    jj, ii = np.meshgrid(j, i, indexing="ij")           # (Ny, Nx)
+    vid = (jj * Nx + ii).ravel()
+    dx = jitter * (2.0 * uniform01(seed, 2 * vid) - 1.0)
+    dy = jitter * (2.0 * uniform01(seed, 2 * vid + 1) - 1.0)
+    bx = (ii.ravel() + dx) * hx                        # home positions, may leave [0, L)
+    by = (jj.ravel() + dy) * hy
+    kx = np.floor(bx / Lx).astype(np.int64)            # home image (periods), -1 or 0
+    ky = np.floor(by / Ly).astype(np.int64)
+    xy = np.stack([bx - kx * Lx, by - ky * Ly], axis=1)
+
+    def corner(ci, cj):
+        """vertex id and periodic shift of grid point (ci, cj), 0 <= ci <= Nx, 0 <= cj <= Ny."""
+        v = (cj % Ny) * Nx + (ci % Nx)
+        return v, kx[v] + ci // Nx, ky[v] + cj // Ny
+
+    ci, cj = ii.ravel(), jj.ravel()
+    a, b, c, d = corner(ci, cj), corner(ci + 1, cj), corner(ci + 1, cj + 1), corner(ci, cj + 1)
+    pos = [(xy[q[0], 0] + q[1] * Lx, xy[q[0], 1] + q[2] * Ly) for q in (a, b, c, d)]
+    if diagonal == "delaunay":
+        # diagonal a-c unless d falls inside the circumcircle of (a, b, c)
+        use_bd = _incircle(*pos[0], *pos[1], *pos[2], *pos[3]) > 0.0
+    else:
+        use_bd = uniform01(seed + 1, vid) < 0.5
+    def pick(q_bd, q_ac):
+        return tuple(np.where(use_bd, x, y) for x, y in zip(q_bd, q_ac))
+
+    # diagonal a-c: (a, b, c) and (a, c, d);  diagonal b-d: (a, b, d) and (b, c, d)
+    first = (a, b, pick(d, c))
+    second = (pick(b, a), c, d)
+    n = Nx * Ny
+    tri = np.empty((2 * n, 3), dtype=np.int64)
+    shift = np.empty((2 * n, 3, 2), dtype=np.int64)
+    for slot, corners in ((0, first), (1, second)):
+        for k, q in enumerate(corners):
+            tri[slot::2, k] = q[0]
+            shift[slot::2, k, 0] = q[1]
+            shift[slot::2, k, 1] = q[2]
+    # every triangle counter-clockwise with positive area
+    P = xy[tri] + shift * np.array([Lx, Ly])
+    area2 = ((P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1])
+             - (P[:, 2, 0] - P[:, 0, 0]) * (P[:, 1, 1] - P[:, 0, 1]))
+    if not np.all(area2 > 0.0):
+        raise AssertionError("jittered_grid produced a non-positive triangle")
+    orig = vid.copy()
+    if relabel_seed is not None:
+        rng = np.random.default_rng(relabel_seed)
+        vperm = rng.permutation(n)
+        inv = np.empty_like(vperm)
+        inv[vperm] = np.arange(n)
+        xy = xy[inv]
+        orig = orig[inv]
+        tri = vperm[tri]
+        tperm = rng.permutation(tri.shape[0])
+        tri = tri[tperm]
+        shift = shift[tperm]
+        rot = rng.integers(0, 3, size=tri.shape[0])
+        idx = (np.arange(3)[None, :] + rot[:, None]) % 3
+        tri = np.take_along_axis(tri, idx, axis=1)
+        shift = np.take_along_axis(shift, idx[:, :, None], axis=1)
+    return Mesh(xy=np.ascontiguousarray(xy), tri=np.ascontiguousarray(tri.astype(np.int32)),
+                shift=np.ascontiguousarray(shift.astype(np.int8)), Lx=float(Lx), Ly=float(Ly),
+                orig_vertex=orig, Nx=Nx, Ny=Ny)
+
+
 # ---------------------------------------------------------------------------
 # conserved state from primitives
 # ---------------------------------------------------------------------------
@@ -212,6 +315,104 @@ def khi_state(mesh: Mesh, seed=1, amp=0.01, gamma=GAMMA) -> np.ndarray:
     U = uniform01(seed, mesh.orig_vertex)
     v = amp * (2.0 * U - 1.0)
     return conserved(rho, u, v, 2.5, gamma)
+
+
+def _smooth_step(t):
+    """g(t) = f(t) / (f(t) + f(1 - t)) with f(t) = exp(-1/t) for t > 0, else 0 (Sec. 5.3):
+    a C-infinity transition from 0 (t <= 0) to 1 (t >= 1)."""
+    t = np.asarray(t, dtype=np.float64)
+
+    def f(z):
+        out = np.zeros_like(z)
+        pos = z > 0
+        out[pos] = np.exp(-1.0 / z[pos])
+        return out
+
+    a, b = f(t), f(1.0 - t)
+    return a / (a + b)
+
+
+def khi_smooth_profiles(y, d=0.25, U0=0.5, rhoL=1.0, rhoH=2.0):
+    """Smoothed shear layer of Sec. 5.3: u_0(y) and rho_0(y) go from the outer values
+    (-U0, rhoL) to the inner ones (+U0, rhoH) over a width d around y = 1/4 and 3/4."""
+    y = np.asarray(y, dtype=np.float64)
+    G = _smooth_step(0.5 + (y - 0.25) / d) * _smooth_step(0.5 - (y - 0.75) / d)
+    return 2.0 * U0 * G - U0, (rhoH - rhoL) * G + rhoL
+
+
+def khi_linear_mode(kx=2.0 * np.pi, d=0.25, U0=0.5, rhoL=1.0, rhoH=2.0, p0=2.5, gamma=GAMMA,
+                    n=128, closure="energy"):
+    """Fastest-growing linear mode of the smoothed shear layer on the periodic unit box.
+
+    Perturbations q(y) exp(i kx x + sigma t) of the Euler equations linearised about
+    (rho_0(y), u_0(y), v = 0, p_0) are expanded in n Fourier modes in y (periodic
+    collocation, spectral derivative), which turns App. C's eigenproblem into a
+    dense n-block matrix eigenproblem.  ``closure`` picks the pressure perturbation:
+
+    * "energy": p_1 from the linearised energy equation,
+      d_t p_1 + u_0 d_x p_1 + gamma p_0 div v_1 = 0 (the Euler equations' own);
+    * "adiabatic": p_1 = c_0(y)^2 rho_1, the closure App. C states.  With rho_0
+      varying and p_0 constant the background entropy varies, so the two differ.
+
+    Returns (sigma, q) with sigma the eigenvalue of largest real part (growth rate
+    Re sigma) and q the eigenvector on y_j = j / n, rows (rho_1, u_1, v_1, p_1),
+    scaled so that the v_1 entry of largest modulus is real and equal to 1.
+    """
+    y = np.arange(n) / n
+    u0, r0 = khi_smooth_profiles(y, d, U0, rhoL, rhoH)
+    k = 2.0 * np.pi * np.fft.fftfreq(n, 1.0 / n)
+    if n % 2 == 0:
+        k[n // 2] = 0.0                      # odd derivative of the Nyquist mode
+    F = np.fft.fft(np.eye(n), axis=0)
+    D = np.real(np.fft.ifft(1j * k[:, None] * F, axis=0))
+    du0 = D @ u0
+    I, Z = np.eye(n), np.zeros((n, n))
+    U, R, Ri = np.diag(u0), np.diag(r0), np.diag(1.0 / r0)
+    ik = 1j * kx
+    if closure == "energy":
+        M = np.block([[-ik * U, -ik * R, -D @ R, Z],
+                      [Z, -ik * U, -np.diag(du0), -ik * Ri],
+                      [Z, Z, -ik * U, -Ri @ D],
+                      [Z, -gamma * p0 * ik * I, -gamma * p0 * D, -ik * U]])
+    elif closure == "adiabatic":
+        C2 = np.diag(gamma * p0 / r0)
+        M = np.block([[-ik * U, -ik * R, -D @ R],
+                      [-ik * Ri @ C2, -ik * U, -np.diag(du0)],
+                      [-Ri @ D @ C2, Z, -ik * U]])
+    else:
+        raise ValueError("closure must be 'energy' or 'adiabatic'")
+    ev, vec = np.linalg.eig(M)
+    i = int(np.argmax(ev.real))
+    q = vec[:, i].reshape(-1, n)
+    if closure == "adiabatic":
+        q = np.vstack([q, (gamma * p0 / r0) * q[0]])
+    j = int(np.argmax(np.abs(q[2])))
+    q = q / q[2, j]
+    return complex(ev[i]), q
+
+
+def khi_smooth_state(mesh: Mesh, amp=1e-3, kx=2.0 * np.pi, d=0.25, U0=0.5, rhoL=1.0, rhoH=2.0,
+                     p0=2.5, gamma=GAMMA, n=128):
+    """Smoothed KHI of Sec. 5.3 seeded with its fastest-growing linear mode
+    (``khi_linear_mode``, energy closure) at vertical-velocity amplitude ``amp``:
+    q(x, y) = background(y) + amp Re[q_hat(y) exp(i kx x)], q_hat interpolated to
+    the vertex heights by its Fourier series."""
+    _, q = khi_linear_mode(kx, d, U0, rhoL, rhoH, p0, gamma, n, "energy")
+    c = np.fft.fft(q, axis=1) / n
+    kk = np.fft.fftfreq(n, 1.0 / n)
+    if n % 2 == 0:
+        c[:, n // 2] = 0.0
+    x, y = mesh.xy[:, 0], mesh.xy[:, 1]
+    yu, inv = np.unique(y, return_inverse=True)
+    qy = (np.exp(2j * np.pi * np.outer(yu, kk)) @ c.T).T[:, inv]
+    pert = amp * np.real(qy * np.exp(1j * kx * x))
+    u0, r0 = khi_smooth_profiles(y, d, U0, rhoL, rhoH)
+    return conserved(r0 + pert[0], u0 + pert[1], pert[2], p0 + pert[3], gamma)
+
+
+def vertical_kinetic_energy(V, W):
+    """E_v = sum_i V_i rho_i v_i^2 / 2, the diagnostic whose growth Sec. 5.3 tracks."""
+    return float(np.sum(V * W[2] * W[2] / W[0]) * 0.5)
 
 
 def smooth_density_state(mesh: Mesh, seed=3, amp=0.05, n_modes=16, kmax=4, gamma=GAMMA) -> np.ndarray:
