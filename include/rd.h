@@ -45,6 +45,25 @@ extern "C" {
 #define RD_N1 0   /* N scheme, forward Euler (first order in space and time)    */
 #define RD_B2 1   /* blended B scheme, two-stage update, m^LDA, global lumping */
 #define RD_LDA2 2 /* LDA scheme, two-stage update                               */
+/* Blended variants of Sec. 3.3.3, two-stage update:
+ *   RD_BMAX2 every diagonal entry of Theta set to max_k Theta_kk (favours N),
+ *   RD_BMIN2 every diagonal entry set to min_k Theta_kk (favours LDA),
+ *   RD_BX2   scalar theta of the shock sensor: theta = min(1, s^2 h_T / L),
+ *            s = max(0, -L div v / (|v|_max - |v|_min)), div v of the linear
+ *            vertex velocities, h_T = sqrt(2 |T|), L = max(Lx, Ly), |v|
+ *            extremes over all vertices of the state being distributed
+ *            (0 when they coincide); on the unit box theta = s^2 h.
+ * In stage 2 Bmax / Bmin reduce the total-residual Theta_kk; Bx evaluates the
+ * sensor at W*.  RD_BX2 is not available in batched mode (RD_ENOTSUP). */
+#define RD_BMAX2 3
+#define RD_BMIN2 4
+#define RD_BX2 5
+
+/* ---- lumping of the stage-2 time derivative (Sec. 3.4) ----------------- */
+#define RD_LUMP_GLOBAL 0    /* mass matrices m^N, m^LDA, global lumping       */
+#define RD_LUMP_SELECTIVE 1 /* + sum_j (|T| delta_ij / 3 - m^G_ij)(W*_j - W^n_j)/dt,
+                               m^G_ij = |T| (delta_ij + 1) / 12 (Galerkin);
+                               two-stage schemes only                        */
 
 /* ---- arithmetic precision of the device path --------------------------- */
 #define RD_FP64 0
@@ -60,20 +79,25 @@ typedef struct rd_state rd_state;
 typedef struct rd_batch rd_batch;
 
 /* Scheme parameters.
- *   scheme    RD_N1 | RD_B2 | RD_LDA2
+ *   scheme    RD_N1 | RD_B2 | RD_LDA2 | RD_BMAX2 | RD_BMIN2 | RD_BX2
  *   precision RD_FP64 | RD_FP32
  *   cfl       Courant number multiplying the stability bound of Sec. 3.2:
  *             dt = cfl * min_i 2 V_i / sum_{T containing i} l_max^T lambda_max^T
  *   gamma     ratio of specific heats (Sec. 3)
  *   eps_fix   |lambda| is replaced below delta = eps_fix * c * |n_i| / 2 by
  *             (lambda^2 + delta^2) / (2 delta) so that N^ = (sum_j K_j^-)^-1
- *             (Sec. 3.3.1) exists at stagnation; 0 disables it.             */
+ *             (Sec. 3.3.1) exists at stagnation; 0 disables it.
+ *   lumping   RD_LUMP_GLOBAL (0, the paper's choice for all its tests) |
+ *             RD_LUMP_SELECTIVE (two-stage schemes; RD_EINVAL with RD_N1)
+ *   reserved  must be 0                                                       */
 typedef struct {
   int32_t scheme;
   int32_t precision;
   double cfl;
   double gamma;
   double eps_fix;
+  int32_t lumping;
+  int32_t reserved;
 } rd_params;
 
 /* Device allocator hook: alloc(bytes, cuda_stream, ctx) returns a device
@@ -208,7 +232,9 @@ int rd_cfl_dt_noalloc(int32_t n_vertex, int32_t n_tri, int32_t precision, const 
  * triangle reverse, gather -- the transposes of Sec. 3.4's updates), which
  * branch on those masks.  Device memory: ckpt_every + 1 state copies, two
  * masks per triangle and step of a segment, and per-corner adjoint records.
- * The state itself is left where rd_adjoint_forward put it.
+ * The state itself is left where rd_adjoint_forward put it.  The adjoint
+ * covers RD_N1, RD_B2 and RD_LDA2 with global lumping; other parameter sets
+ * return RD_ENOTSUP.
  * rd_run_fixed_dt: n_steps steps with the prescribed dt sequence (host,
  * [n_steps]) instead of the CFL dt, e.g. the recorded one, for finite
  * differences of the same map. */

@@ -27,8 +27,25 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rd_oracle.cpp")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 
-N1, B2, LDA2 = 0, 1, 2
-SCHEMES = {"N1": N1, "B2": B2, "LDA2": LDA2}
+N1, B2, LDA2, BMAX2, BMIN2, BX2 = 0, 1, 2, 3, 4, 5
+SELECTIVE_LUMPING = 0x100
+_BASE = {"N1": N1, "B2": B2, "LDA2": LDA2, "BMAX2": BMAX2, "BMIN2": BMIN2, "BX2": BX2}
+
+
+def scheme_code(scheme) -> int:
+    """Scheme name ("B2", "BMIN2", ...; suffix "_SL" for selective lumping) -> oracle code."""
+    if not isinstance(scheme, str):
+        return int(scheme)
+    name, sl = (scheme[:-3], True) if scheme.endswith("_SL") else (scheme, False)
+    return _BASE[name] | (SELECTIVE_LUMPING if sl else 0)
+
+
+class _Schemes(dict):
+    def __missing__(self, key):
+        return scheme_code(key)
+
+
+SCHEMES = _Schemes(_BASE)
 
 _lib = None
 
@@ -70,6 +87,9 @@ def lib():
         _lib.ora_triangle_terms_ld.argtypes = mesh_args + [dp, ctypes.c_double, ctypes.c_double] + [dp] * 4
         _lib.ora_stage2_terms.argtypes = mesh_args + [dp, dp, ctypes.c_double, ctypes.c_double,
                                                       ctypes.c_double, ctypes.c_int] + [dp] * 5
+        for name in ("ora_stage1_shares", "ora_stage1_shares_ld"):
+            getattr(_lib, name).argtypes = mesh_args + [dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                         dp, ctypes.c_int]
         _lib.ora_eigensystem.argtypes = [ctypes.c_double] * 6 + [dp] * 4
         _lib.ora_conserved.argtypes = mesh_args + [dp, dp]
         _lib.ora_num_threads.restype = ctypes.c_int
@@ -112,7 +132,7 @@ def run(mesh, W0, scheme="B2", nsteps=1, cfl=0.8, gamma=1.4, eps=1e-6, dt_fixed=
     dts = np.zeros(max(nsteps, 1))
     dtf = None if dt_fixed is None else np.ascontiguousarray(dt_fixed, dtype=np.float64)
     f = lib().ora_run_ld if long_double else lib().ora_run
-    rc = f(*margs, _p(W), SCHEMES[scheme] if isinstance(scheme, str) else scheme, cfl, gamma, eps,
+    rc = f(*margs, _p(W), scheme_code(scheme), cfl, gamma, eps,
            nsteps, _p(dtf), _p(dts), nthreads)
     _check(rc, "ora_run")
     del keep
@@ -125,7 +145,7 @@ def run_tangent(mesh, W0, dW0, dts, scheme="B2", gamma=1.4, eps=1e-6, nthreads=1
     W = np.ascontiguousarray(np.array(W0, dtype=np.float64, copy=True))
     dW = np.ascontiguousarray(np.array(dW0, dtype=np.float64, copy=True))
     dtf = np.ascontiguousarray(dts, dtype=np.float64)
-    rc = lib().ora_run_tangent(*margs, _p(W), _p(dW), SCHEMES[scheme], gamma, eps, len(dtf),
+    rc = lib().ora_run_tangent(*margs, _p(W), _p(dW), scheme_code(scheme), gamma, eps, len(dtf),
                                _p(dtf), nthreads)
     _check(rc, "ora_run_tangent")
     del keep
@@ -181,6 +201,17 @@ def triangle_terms_ld(mesh, W, gamma=1.4, eps=1e-6):
     return out
 
 
+def stage1_shares(mesh, W, scheme="B2", gamma=1.4, eps=1e-6, nthreads=1, long_double=False):
+    """Stage-1 (forward-Euler) shares of any scheme at state W: (nt, 3, 4)."""
+    keep, margs = _mesh_args(mesh)
+    Wc = np.ascontiguousarray(W, dtype=np.float64)
+    out = np.zeros((mesh.nt, 3, 4))
+    f = lib().ora_stage1_shares_ld if long_double else lib().ora_stage1_shares
+    _check(f(*margs, _p(Wc), gamma, eps, scheme_code(scheme), _p(out), nthreads), "ora_stage1_shares")
+    del keep
+    return out
+
+
 def stage2_terms(mesh, Wn, Ws, dt, gamma=1.4, eps=1e-6, scheme="B2"):
     keep, margs = _mesh_args(mesh)
     nt = mesh.nt
@@ -188,7 +219,7 @@ def stage2_terms(mesh, Wn, Ws, dt, gamma=1.4, eps=1e-6, scheme="B2"):
     b = np.ascontiguousarray(Ws, dtype=np.float64)
     out = dict(PhiT=np.zeros((nt, 4)), PhiN=np.zeros((nt, 3, 4)), PhiLDA=np.zeros((nt, 3, 4)),
                Phi=np.zeros((nt, 3, 4)), theta=np.zeros((nt, 4)))
-    rc = lib().ora_stage2_terms(*margs, _p(a), _p(b), dt, gamma, eps, SCHEMES[scheme],
+    rc = lib().ora_stage2_terms(*margs, _p(a), _p(b), dt, gamma, eps, scheme_code(scheme),
                                 _p(out["PhiT"]), _p(out["PhiN"]), _p(out["PhiLDA"]), _p(out["Phi"]),
                                 _p(out["theta"]))
     _check(rc, "ora_stage2_terms")

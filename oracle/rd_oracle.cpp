@@ -12,10 +12,11 @@
 //   * piecewise-linear Z^h, cell residual phi^T = sum_i K_i Z_i with the
 //     flux Jacobians dF/dZ evaluated at the nodal mean of Z      (Eqs. eqZh..eqLinearA)
 //   * eigen-split K_i^{+-} = R Lambda^{+-} L                      (Sec. 3.2, App. A)
-//   * N, LDA and blended B distributions                          (Sec. 3.3.1-3.3.3)
+//   * N, LDA and blended B distributions, the Bmax / Bmin variants and the
+//     shock-sensor blend Bx                                       (Sec. 3.3.1-3.3.3)
 //   * forward-Euler update with the CFL time step                 (Eq. eqUpdate, Sec. 3.2)
 //   * the explicit two-stage scheme with total residuals Phi^N, Phi^LDA,
-//     mass matrices m^N, m^LDA and global lumping                 (Sec. 3.4, eqRK1/eqRK2)
+//     mass matrices m^N, m^LDA and global or selective lumping    (Sec. 3.4, eqRK1/eqRK2)
 //
 // Everything is written in the paper's order and notation; no fusion, no
 // reordering beyond what the formulas state.  All arithmetic is templated on the
@@ -39,6 +40,14 @@
 //   (R7) V_i = sum_{T containing i} |T|/3.
 //   (R8) dt = CFL * min_i 2 V_i / sum_T l_max^T lambda_max^T, at W^n, used by
 //        both stages.
+//   (R9) Bx: theta = min(1, s^2 h_T / L) with s = max(0, -L div v / (|v|_max -
+//        |v|_min)); div v of the piecewise-linear vertex velocities, h_T =
+//        sqrt(2 |T|), L = max(Lx, Ly), |v| extremes over all vertices of the
+//        state being distributed (W^n in stage 1, W* in stage 2); s = 0 when
+//        |v|_max = |v|_min.  On the unit box theta = s^2 h as printed.
+//   (R10) Bmax / Bmin in stage 2 take max_k / min_k of the total-residual
+//        Theta_kk of (R6); selective lumping adds its correction to the
+//        blended total residual (it sums to zero over the triangle).
 //
 // Build: g++ -O2 -std=c++17 -ffp-contract=off -fPIC -shared [-fopenmp]
 
@@ -56,7 +65,8 @@
 namespace ora {
 
 enum { OK = 0, EINVAL = 1, ENONPHYS = 4 };
-enum { N1 = 0, B2 = 1, LDA2 = 2 };
+enum { N1 = 0, B2 = 1, LDA2 = 2, BMAX2 = 3, BMIN2 = 4, BX2 = 5 };
+enum { SELECTIVE_LUMPING = 0x100 };  // flag or-ed into the scheme code
 
 // ---------------------------------------------------------------------------
 // Forward-mode dual number (value + one directional derivative).
@@ -106,6 +116,7 @@ struct Mesh {
   std::vector<S> area;        // [nt]
   std::vector<S> lmax;        // [nt] longest edge
   std::vector<S> V;           // [nv] nodal volume (R7)
+  S L = S(1);                 // domain size max(Lx, Ly) (R9)
 };
 
 // Geometry of every triangle from the (periodically shifted) corner positions.
@@ -113,6 +124,8 @@ template <class S>
 int build_mesh(int32_t nv, const double* xy, int32_t nt, const int32_t* tri,
                const int8_t* shift, double Lx, double Ly, Mesh<S>& m) {
   m.nv = nv; m.nt = nt;
+  m.L = S(Lx > Ly ? Lx : Ly);
+  if (!(m.L > S(0))) m.L = S(1);
   m.tri.assign(tri, tri + 3 * (size_t)nt);
   m.n.assign(6 * (size_t)nt, S(0));
   m.area.assign(nt, S(0));
@@ -455,13 +468,77 @@ int time_step(const Mesh<S>& m, const std::vector<S>& W, S gamma, S cfl, S& dt) 
   return OK;
 }
 
+// Blend of N and LDA shares (Sec. 3.3.3): B uses the diagonal Theta; Bmax and
+// Bmin put max_k Theta_kk or min_k Theta_kk on every diagonal entry; Bx uses
+// the scalar theta of its shock sensor.  out_i = th phi^N_i + (1 - th) phi^LDA_i.
+template <class S>
+void blend_shares(int base, const S theta[4], S theta_x, const S N[3][4], const S LDA[3][4], S out[3][4]) {
+  S th[4];
+  for (int k = 0; k < 4; ++k) th[k] = theta[k];
+  if (base == BMAX2 || base == BMIN2) {
+    S e = theta[0];
+    for (int k = 1; k < 4; ++k) e = base == BMAX2 ? smax(e, theta[k]) : smin(e, theta[k]);
+    for (int k = 0; k < 4; ++k) th[k] = e;
+  } else if (base == BX2) {
+    for (int k = 0; k < 4; ++k) th[k] = theta_x;
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 4; ++k) out[i][k] = th[k] * N[i][k] + (S(1) - th[k]) * LDA[i][k];
+}
+
+// Range |v|_max - |v|_min of the vertex speeds of a state (Bx sensor, R9).
+template <class S>
+int speed_range(const std::vector<S>& W, S gamma, S& range) {
+  S lo = S(0), hi = S(0);
+  for (size_t i = 0; i < W.size() / 4; ++i) {
+    S Wi[4] = {W[4 * i], W[4 * i + 1], W[4 * i + 2], W[4 * i + 3]};
+    S rho, u, v, p;
+    int e = primitive(Wi, gamma, rho, u, v, p);
+    if (e) return e;
+    S q = sqrt(u * u + v * v);
+    lo = i == 0 ? q : smin(lo, q);
+    hi = i == 0 ? q : smax(hi, q);
+  }
+  range = hi - lo;
+  return OK;
+}
+
+// Bx blending coefficient of triangle t (Sec. 3.3.3, R9) from the vertex
+// velocities u_c = rho u / rho, v_c = rho v / rho of the state being distributed.
+template <class S>
+S bx_theta(const Mesh<S>& m, int32_t t, const S W[3][4], S vrange) {
+  if (!(vrange > S(0))) return S(0);
+  // div v of the linear interpolant: grad phi_c = n_c / (2 |T|), n_c inward, |n_c| = edge length
+  S div = S(0);
+  for (int c = 0; c < 3; ++c) {
+    S u = W[c][1] / W[c][0], v = W[c][2] / W[c][0];
+    div += (u * m.n[6 * (size_t)t + 2 * c] + v * m.n[6 * (size_t)t + 2 * c + 1]) / (S(2) * m.area[t]);
+  }
+  S sens = -m.L * div / vrange;
+  if (!(sens > S(0))) return S(0);
+  S h = sqrt(S(2) * m.area[t]);
+  return smin(S(1), sens * sens * h / m.L);
+}
+
+template <class S>
+void tri_W(const Mesh<S>& m, const std::vector<S>& W, int32_t t, S out[3][4]) {
+  for (int c = 0; c < 3; ++c)
+    for (int k = 0; k < 4; ++k) out[c][k] = W[4 * (size_t)m.tri[3 * t + c] + k];
+}
+
 // Stage-1 / forward-Euler residuals: per triangle the share of each node.
 template <class S>
 int stage1_shares(const Mesh<S>& m, const std::vector<S>& W, S gamma, S eps, int scheme,
                   std::vector<S>& share, int nthreads) {
+  const int base = scheme & 0xff;
   std::vector<S> Zv;
   int e = all_Z(m, W, gamma, Zv);
   if (e) return e;
+  S vrange = S(0);
+  if (base == BX2) {
+    e = speed_range(W, gamma, vrange);
+    if (e) return e;
+  }
   share.assign(12 * (size_t)m.nt, S(0));
   int err = OK;
 #pragma omp parallel for schedule(static) num_threads(nthreads) if (nthreads > 1)
@@ -475,11 +552,21 @@ int stage1_shares(const Mesh<S>& m, const std::vector<S>& W, S gamma, S eps, int
       err = le;
       continue;
     }
-    for (int c = 0; c < 3; ++c)
-      for (int k = 0; k < 4; ++k) {
-        S phi = scheme == N1 ? o.phiN[c][k] : scheme == LDA2 ? o.phiLDA[c][k] : o.phiB[c][k];
-        share[12 * (size_t)t + 4 * c + k] = phi;
+    S out[3][4];
+    if (base == N1 || base == LDA2) {
+      for (int c = 0; c < 3; ++c)
+        for (int k = 0; k < 4; ++k) out[c][k] = base == N1 ? o.phiN[c][k] : o.phiLDA[c][k];
+    } else {
+      S thx = S(0);
+      if (base == BX2) {
+        S Wt[3][4];
+        tri_W(m, W, t, Wt);
+        thx = bx_theta(m, t, Wt, vrange);
       }
+      blend_shares(base, o.theta, thx, o.phiN, o.phiLDA, out);
+    }
+    for (int c = 0; c < 3; ++c)
+      for (int k = 0; k < 4; ++k) share[12 * (size_t)t + 4 * c + k] = out[c][k];
   }
   return err;
 }
@@ -496,7 +583,9 @@ struct TriStage2 {
 
 template <class S>
 int stage2_triangle(const S Zn[3][4], const S Zs[3][4], const S Wn[3][4], const S Ws[3][4],
-                    const S n[3][2], S area, S dt, S gamma, S eps, int scheme, TriStage2<S>& o) {
+                    const S n[3][2], S area, S dt, S gamma, S eps, int scheme, TriStage2<S>& o,
+                    S theta_x = S(0)) {
+  const int base = scheme & 0xff;
   TriLin<S> ln, ls;
   int e = linearise(Zn, n, gamma, eps, ln);
   if (e) return e;
@@ -535,11 +624,19 @@ int stage2_triangle(const S Zn[3][4], const S Zs[3][4], const S Wn[3][4], const 
   for (int k = 0; k < 4; ++k) {
     S num = fabs(o.PhiT[k]);
     S den = smax(fabs(o.PhiN[0][k]) + fabs(o.PhiN[1][k]) + fabs(o.PhiN[2][k]), num);
-    o.theta[k] = (scheme == LDA2 || !(den > S(0))) ? S(0) : num / den;
+    o.theta[k] = (base == LDA2 || !(den > S(0))) ? S(0) : num / den;
   }
-  for (int i = 0; i < 3; ++i)
-    for (int k = 0; k < 4; ++k)
-      o.Phi[i][k] = o.theta[k] * o.PhiN[i][k] + (S(1) - o.theta[k]) * o.PhiLDA[i][k];
+  blend_shares(base, o.theta, theta_x, o.PhiN, o.PhiLDA, o.Phi);
+  // selective lumping: Phi_i += sum_j (|T| delta_ij / 3 - m^G_ij) (W*_j - W^n_j) / dt,
+  // m^G_ij = |T| (delta_ij + 1) / 12 (Galerkin mass matrix)
+  if (scheme & SELECTIVE_LUMPING) {
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        S d = i == j ? S(1) : S(0);
+        S coef = area * d / S(3) - area * (d + S(1)) / S(12);
+        for (int k = 0; k < 4; ++k) o.Phi[i][k] += coef * (Ws[j][k] - Wn[j][k]) / dt;
+      }
+  }
   return OK;
 }
 
@@ -551,6 +648,11 @@ int stage2_shares(const Mesh<S>& m, const std::vector<S>& Wn, const std::vector<
   if (e) return e;
   e = all_Z(m, Ws, gamma, Zs);
   if (e) return e;
+  S vrange = S(0);
+  if ((scheme & 0xff) == BX2) {
+    e = speed_range(Ws, gamma, vrange);
+    if (e) return e;
+  }
   share.assign(12 * (size_t)m.nt, S(0));
   int err = OK;
 #pragma omp parallel for schedule(static) num_threads(nthreads) if (nthreads > 1)
@@ -566,7 +668,8 @@ int stage2_shares(const Mesh<S>& m, const std::vector<S>& Wn, const std::vector<
       }
     }
     TriStage2<S> o;
-    int le = stage2_triangle(zn, zs, wn, ws, n, m.area[t], dt, gamma, eps, scheme, o);
+    S thx = (scheme & 0xff) == BX2 ? bx_theta(m, t, ws, vrange) : S(0);
+    int le = stage2_triangle(zn, zs, wn, ws, n, m.area[t], dt, gamma, eps, scheme, o, thx);
     if (le) {
 #pragma omp atomic write
       err = le;
@@ -597,6 +700,9 @@ void apply_update(const Mesh<S>& m, const std::vector<S>& Win, const std::vector
 template <class S>
 int step(const Mesh<S>& m, std::vector<S>& W, S gamma, S cfl, S eps, int scheme, S dt_fixed,
          S& dt, int nthreads) {
+  const int base = scheme & 0xff;
+  if (base < N1 || base > BX2 || (scheme & ~(0xff | SELECTIVE_LUMPING))) return EINVAL;
+  if (base == N1 && (scheme & SELECTIVE_LUMPING)) return EINVAL;
   if (dt_fixed > S(0)) {
     dt = dt_fixed;
   } else {
@@ -607,7 +713,7 @@ int step(const Mesh<S>& m, std::vector<S>& W, S gamma, S cfl, S eps, int scheme,
   int e = stage1_shares(m, W, gamma, eps, scheme, share, nthreads);
   if (e) return e;
   apply_update(m, W, share, dt, Ws);
-  if (scheme == N1) {
+  if (base == N1) {
     W.swap(Ws);
     return OK;
   }
@@ -838,6 +944,11 @@ int ora_stage2_terms(int32_t nv, const double* xy, int32_t nt, const int32_t* tr
   if (e) return e;
   e = ora::all_Z(m, Wsv, gamma, Zs);
   if (e) return e;
+  double vrange = 0.0;
+  if ((scheme & 0xff) == ora::BX2) {
+    e = ora::speed_range(Wsv, gamma, vrange);
+    if (e) return e;
+  }
   for (int32_t t = 0; t < nt; ++t) {
     double zn[3][4], zs[3][4], wn[3][4], ws[3][4], n[3][2];
     ora::tri_Z(m, Zn, t, zn, n);
@@ -850,7 +961,8 @@ int ora_stage2_terms(int32_t nv, const double* xy, int32_t nt, const int32_t* tr
       }
     }
     ora::TriStage2<double> o;
-    e = ora::stage2_triangle(zn, zs, wn, ws, n, m.area[t], dt, gamma, eps, scheme, o);
+    double thx = (scheme & 0xff) == ora::BX2 ? ora::bx_theta(m, t, ws, vrange) : 0.0;
+    e = ora::stage2_triangle(zn, zs, wn, ws, n, m.area[t], dt, gamma, eps, scheme, o, thx);
     if (e) return e;
     for (int k = 0; k < 4; ++k) {
       if (PhiT) PhiT[4 * (size_t)t + k] = o.PhiT[k];
@@ -865,6 +977,38 @@ int ora_stage2_terms(int32_t nv, const double* xy, int32_t nt, const int32_t* tr
       }
   }
   return ora::OK;
+}
+
+}  // extern "C"
+
+template <class S>
+int stage1_shares_impl(int32_t nv, const double* xy, int32_t nt, const int32_t* tri, const int8_t* shift,
+                       double Lx, double Ly, const double* W, double gamma, double eps, int scheme,
+                       double* out, int nthreads) {
+  ora::Mesh<S> m;
+  int e = ora::build_mesh(nv, xy, nt, tri, shift, Lx, Ly, m);
+  if (e) return e;
+  std::vector<S> Wv, share;
+  ora::soa_to_aos(W, nv, Wv);
+  e = ora::stage1_shares(m, Wv, S(gamma), S(eps), scheme, share, nthreads);
+  if (e) return e;
+  for (size_t i = 0; i < share.size(); ++i) out[i] = ora::val(share[i]);
+  return ora::OK;
+}
+
+extern "C" {
+
+// Stage-1 (forward-Euler) shares of any scheme code at state W: out [nt][3][4].
+int ora_stage1_shares(int32_t nv, const double* xy, int32_t nt, const int32_t* tri, const int8_t* shift,
+                      double Lx, double Ly, const double* W, double gamma, double eps, int scheme,
+                      double* out, int nthreads) {
+  return stage1_shares_impl<double>(nv, xy, nt, tri, shift, Lx, Ly, W, gamma, eps, scheme, out, nthreads);
+}
+int ora_stage1_shares_ld(int32_t nv, const double* xy, int32_t nt, const int32_t* tri, const int8_t* shift,
+                         double Lx, double Ly, const double* W, double gamma, double eps, int scheme,
+                         double* out, int nthreads) {
+  return stage1_shares_impl<long double>(nv, xy, nt, tri, shift, Lx, Ly, W, gamma, eps, scheme, out,
+                                         nthreads);
 }
 
 // App. A pieces at one state and unit normal, for the algebra pins:

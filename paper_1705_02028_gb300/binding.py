@@ -16,7 +16,8 @@ import numpy as np
 from . import build as _build
 
 RD_OK, RD_EINVAL, RD_ENOMEM, RD_ECUDA, RD_ENONPHYSICAL, RD_ETIMEOUT, RD_ENOTSUP = range(7)
-SCHEMES = {"N1": 0, "B2": 1, "LDA2": 2}
+SCHEMES = {"N1": 0, "B2": 1, "LDA2": 2, "BMAX2": 3, "BMIN2": 4, "BX2": 5}
+LUMPING = {"global": 0, "selective": 1}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 ORDERS = {"none": 0, "morton": 1, "rcm": 2}
 
@@ -33,7 +34,8 @@ class RDError(RuntimeError):
 
 class Params(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int32), ("precision", ctypes.c_int32), ("cfl", ctypes.c_double),
-                ("gamma", ctypes.c_double), ("eps_fix", ctypes.c_double)]
+                ("gamma", ctypes.c_double), ("eps_fix", ctypes.c_double), ("lumping", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -185,10 +187,14 @@ def cfl_dt(W, tri, lmax, V, csr_ptr, csr_ent, precision="fp64", gamma=1.4, cfl=0
     return float(out.item())
 
 
-def _params(scheme, precision, cfl, gamma, eps_fix) -> Params:
+def _params(scheme, precision, cfl, gamma, eps_fix, lumping="global") -> Params:
+    """Scheme name ("B2", "BMIN2", ...; the suffix "_SL" selects selective lumping) -> rd_params."""
+    if isinstance(scheme, str) and scheme.endswith("_SL"):
+        scheme, lumping = scheme[:-3], "selective"
     return Params(SCHEMES[scheme] if isinstance(scheme, str) else int(scheme),
                   PRECISIONS[precision] if isinstance(precision, str) else int(precision),
-                  float(cfl), float(gamma), float(eps_fix))
+                  float(cfl), float(gamma), float(eps_fix),
+                  LUMPING[lumping] if isinstance(lumping, str) else int(lumping), 0)
 
 
 class Mesh:
@@ -240,10 +246,11 @@ class Mesh:
 class State:
     """Solver state on one mesh (rd_state_init ... rd_state_destroy)."""
 
-    def __init__(self, mesh: Mesh, W, scheme="B2", precision="fp64", cfl=0.8, gamma=1.4, eps_fix=1e-6):
+    def __init__(self, mesh: Mesh, W, scheme="B2", precision="fp64", cfl=0.8, gamma=1.4, eps_fix=1e-6,
+                 lumping="global"):
         load()
         self.mesh = mesh
-        self.params = _params(scheme, precision, cfl, gamma, eps_fix)
+        self.params = _params(scheme, precision, cfl, gamma, eps_fix, lumping)
         Wc = np.ascontiguousarray(W, dtype=np.float64)
         if Wc.shape != (4, mesh.nv):
             raise ValueError(f"W must have shape (4, {mesh.nv})")
@@ -353,10 +360,11 @@ class State:
 class Batch:
     """Many independent meshes advanced together (rd_batch_create ... rd_batch_destroy)."""
 
-    def __init__(self, meshes, states, scheme="B2", precision="fp64", cfl=0.8, gamma=1.4, eps_fix=1e-6):
+    def __init__(self, meshes, states, scheme="B2", precision="fp64", cfl=0.8, gamma=1.4, eps_fix=1e-6,
+                 lumping="global"):
         load()
         self.meshes = list(meshes)
-        self.params = _params(scheme, precision, cfl, gamma, eps_fix)
+        self.params = _params(scheme, precision, cfl, gamma, eps_fix, lumping)
         self._W = [np.ascontiguousarray(W, dtype=np.float64) for W in states]
         for m, W in zip(self.meshes, self._W):
             if W.shape != (4, m.nv):

@@ -180,7 +180,10 @@ namespace {
 
 bool valid_params(const rd_params* p) {
   if (!p) return false;
-  if (p->scheme != RD_N1 && p->scheme != RD_B2 && p->scheme != RD_LDA2) return false;
+  if (p->scheme < RD_N1 || p->scheme > RD_BX2) return false;
+  if (p->lumping != RD_LUMP_GLOBAL && p->lumping != RD_LUMP_SELECTIVE) return false;
+  if (p->lumping == RD_LUMP_SELECTIVE && p->scheme == RD_N1) return false;
+  if (p->reserved != 0) return false;
   if (p->precision != RD_FP64 && p->precision != RD_FP32) return false;
   if (!(p->cfl > 0.0) || !(p->gamma > 1.0) || !(p->eps_fix >= 0.0)) return false;
   if (!std::isfinite(p->cfl) || !std::isfinite(p->gamma) || !std::isfinite(p->eps_fix)) return false;
@@ -222,6 +225,18 @@ __global__ void k_fix_dt(DevCtl* ctl, double dt) {
   if (!ctl->stop) ctl->dt = dt;
 }
 
+// Blend configuration of a state's two-stage triangle kernels (Sec. 3.3.3, Sec. 3.4).
+template <class T>
+BlendArgs<T> blend_args(const rd_state* s) {
+  BlendArgs<T> ba;
+  ba.mode = s->p.scheme == RD_BMAX2 ? BLEND_MAX : s->p.scheme == RD_BMIN2 ? BLEND_MIN
+            : s->p.scheme == RD_BX2 ? BLEND_X : BLEND_B;
+  ba.sl = s->p.lumping == RD_LUMP_SELECTIVE;
+  double L = s->m->h.Lx > s->m->h.Ly ? s->m->h.Lx : s->m->h.Ly;
+  ba.L = (T)(L > 0.0 ? L : 1.0);
+  return ba;
+}
+
 template <class T>
 int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = true, double fixed_dt = 0.0) {
   rd_mesh* m = s->m;
@@ -244,16 +259,22 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
   auto mark = [&](int k) {
     if (ev) cudaEventRecord(ev[k], st);
   };
+  BlendArgs<T> ba1 = blend_args<T>(s), ba2 = ba1;
+  unsigned long long* vr0 = (unsigned long long*)s->vr.p;          // |v| range of W^n
+  unsigned long long* vr1 = vr0 ? vr0 + 2 : nullptr;              // |v| range of W*
+  ba1.vr = vr0;
+  ba2.vr = vr1;
   mark(0);
   switch (s->p.scheme) {
     case RD_N1:
       k_tri_stage1<T, RD_N1><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, nullptr, cf, ctl);
       break;
-    case RD_B2:
-      k_tri_stage1<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, rec, cf, ctl);
-      break;
-    default:
+    case RD_LDA2:
       k_tri_stage1<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, rec, cf, ctl);
+      break;
+    default:  // RD_B2, RD_BMAX2, RD_BMIN2, RD_BX2
+      k_tri_stage1<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, rec, cf, ctl,
+                                                ba1);
       break;
   }
   mark(1);
@@ -267,18 +288,22 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
     mark(4);
     mark(5);
   } else {
+    if (vr1) k_vr_reset<<<1, 1, 0, st>>>(vr1, ctl, 0);
     k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)s->W[a].p, (const T*)s->R1.p, ptr, ent, nullptr, V, gamma,
-                                          (T*)s->Ws.p, (T*)s->Zs.p, nullptr, ctl);
+                                          (T*)s->Ws.p, (T*)s->Zs.p, nullptr, ctl, nullptr, nullptr, vr1);
     mark(3);
-    if (s->p.scheme == RD_B2)
-      k_tri_stage2<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
-                                                       (const T*)s->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl);
-    else
+    if (s->p.scheme == RD_LDA2)
       k_tri_stage2<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
-                                                         (const T*)s->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl);
+                                                  (const T*)s->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl,
+                                                  nullptr, nullptr, ba2);
+    else
+      k_tri_stage2<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
+                                                (const T*)s->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl,
+                                                nullptr, nullptr, ba2);
     mark(4);
+    if (vr0) k_vr_reset<<<1, 1, 0, st>>>(vr0, ctl, 0);
     k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)s->Ws.p, nullptr, ptr, ent, share, V, gamma,
-                                          (T*)s->W[b].p, (T*)s->Z[b].p, (T*)s->spd[b].p, ctl);
+                                          (T*)s->W[b].p, (T*)s->Z[b].p, (T*)s->spd[b].p, ctl, nullptr, nullptr, vr0);
     mark(5);
   }
   if (commit) k_commit<<<1, 1, 0, st>>>(ctl);
@@ -309,8 +334,10 @@ int upload_state(rd_state* s, const double* W, int buf) {
   CU(cudaMemcpyAsync(s->stage.p, W, 4 * (size_t)nv * sizeof(double), cudaMemcpyHostToDevice, st));
   k_permute_in<T><<<nblk(nv, VTX_BLOCK), VTX_BLOCK, 0, st>>>(nv, (const int*)m->vperm.p, (const double*)s->stage.p,
                                                              (T*)s->W[buf].p, ctl);
+  unsigned long long* vr0 = (unsigned long long*)s->vr.p;
+  if (vr0) k_vr_reset<<<1, 1, 0, st>>>(vr0, ctl, 1);
   k_prepare<T><<<nblk(nv, VTX_BLOCK), VTX_BLOCK, 0, st>>>(nv, (const T*)s->W[buf].p, (T)s->p.gamma,
-                                                          (T*)s->Z[buf].p, (T*)s->spd[buf].p, ctl);
+                                                          (T*)s->Z[buf].p, (T*)s->spd[buf].p, ctl, vr0);
   CU(cudaGetLastError());
   DevCtl c;
   CK(read_ctl(s, c));
@@ -348,6 +375,7 @@ int alloc_state(rd_state* s) {
   CK(dev_alloc(s->cons_partial, (size_t)nblk(nv, VTX_BLOCK) * 4 * sizeof(double), st));
   CK(dev_alloc(s->cons_out, 4 * sizeof(double), st));
   CK(dev_alloc(s->stage, 4 * nv * sizeof(double), st));
+  if (s->p.scheme == RD_BX2) CK(dev_alloc(s->vr, 4 * sizeof(unsigned long long), st));
   if (s->p.scheme != RD_N1) {
     CK(dev_alloc(s->Ws, 4 * nv * ts, st));
     CK(dev_alloc(s->Zs, 4 * nv * ts, st));
@@ -676,7 +704,7 @@ extern "C" void rd_state_destroy(rd_state* s) {
     dev_free(s->spd[b]);
   }
   DevBuf* bufs[] = {&s->Ws, &s->Zs, &s->R1, &s->share, &s->rec, &s->cfl, &s->partial, &s->ctl,
-                    &s->cons_partial, &s->cons_out, &s->stage};
+                    &s->cons_partial, &s->cons_out, &s->stage, &s->vr};
   for (DevBuf* b : bufs) dev_free(*b);
   adjoint_free(s->adj);
   delete s;

@@ -72,15 +72,19 @@ int batch_step(rd_batch* b, int a, cudaEvent_t* ev, bool commit) {
   mark(0);
   const T* Za = (const T*)b->Z[a].p;
   const T* Sa = (const T*)b->spd[a].p;
+  BlendArgs<T> ba;  // Bmax / Bmin and selective lumping; Bx is not offered in batched mode
+  ba.mode = b->p.scheme == RD_BMAX2 ? BLEND_MAX : b->p.scheme == RD_BMIN2 ? BLEND_MIN : BLEND_B;
+  ba.sl = b->p.lumping == RD_LUMP_SELECTIVE;
   switch (b->p.scheme) {
     case RD_N1:
       k_tri_stage1<T, RD_N1><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, nullptr, cf, ctl);
       break;
-    case RD_B2:
-      k_tri_stage1<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, rec, cf, ctl);
+    case RD_LDA2:
+      k_tri_stage1<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, rec, cf, ctl);
       break;
     default:
-      k_tri_stage1<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, rec, cf, ctl);
+      k_tri_stage1<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, rec, cf, ctl,
+                                                ba);
       break;
   }
   mark(1);
@@ -98,12 +102,14 @@ int batch_step(rd_batch* b, int a, cudaEvent_t* ev, bool commit) {
     k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)b->W[a].p, (const T*)b->R1.p, ptr, ent, nullptr, V, gamma,
                                    (T*)b->Ws.p, (T*)b->Zs.p, nullptr, ctl, dtm, vm);
     mark(3);
-    if (b->p.scheme == RD_B2)
-      k_tri_stage2<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)b->Zs.p, (const T*)b->W[a].p,
-                                                (const T*)b->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl, dtm, tm);
-    else
+    if (b->p.scheme == RD_LDA2)
       k_tri_stage2<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)b->Zs.p, (const T*)b->W[a].p,
-                                                  (const T*)b->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl, dtm, tm);
+                                                  (const T*)b->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl, dtm, tm,
+                                                  ba);
+    else
+      k_tri_stage2<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)b->Zs.p, (const T*)b->W[a].p,
+                                                (const T*)b->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl, dtm, tm,
+                                                ba);
     mark(4);
     k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)b->Ws.p, nullptr, ptr, ent, share, V, gamma, (T*)b->W[c].p,
                                    (T*)b->Z[c].p, (T*)b->spd[c].p, ctl, dtm, vm);
@@ -291,7 +297,10 @@ extern "C" int rd_batch_create(int32_t n_mesh, rd_mesh* const* meshes, const dou
   if (!out) return RD_EINVAL;
   *out = nullptr;
   if (n_mesh < 1 || n_mesh > 65535 || !meshes || !W0 || !p) return RD_EINVAL;
-  if (p->scheme != RD_N1 && p->scheme != RD_B2 && p->scheme != RD_LDA2) return RD_EINVAL;
+  if (p->scheme < RD_N1 || p->scheme > RD_BX2) return RD_EINVAL;
+  if (p->lumping != RD_LUMP_GLOBAL && p->lumping != RD_LUMP_SELECTIVE) return RD_EINVAL;
+  if ((p->lumping == RD_LUMP_SELECTIVE && p->scheme == RD_N1) || p->reserved != 0) return RD_EINVAL;
+  if (p->scheme == RD_BX2) return RD_ENOTSUP;  // its |v| range is global per mesh
   if (p->precision != RD_FP64 && p->precision != RD_FP32) return RD_EINVAL;
   if (!(p->cfl > 0.0) || !(p->gamma > 1.0) || !(p->eps_fix >= 0.0)) return RD_EINVAL;
   for (int32_t m = 0; m < n_mesh; ++m)

@@ -79,6 +79,7 @@ struct rd_state {
   rd::DevBuf W[2], Z[2], spd[2];
   rd::DevBuf Ws, Zs, R1, share, rec, cfl, partial, ctl, cons_partial, cons_out;
   rd::DevBuf stage;        // [4][nv] double, caller vertex order (host I/O)
+  rd::DevBuf vr;           // RD_BX2: |v| max / min bits, slot 0 (W^n) and slot 1 (W*)
   long long launched = 0;  // host view of the committed step count (parity of the buffers)
   int tri_block = rd::TRI_BLOCK, vtx_block = rd::VTX_BLOCK;  // launch shapes (autotuned)
   cudaGraphExec_t g2 = nullptr;  // two steps (even -> odd -> even)

@@ -67,6 +67,10 @@ struct Gas {
   }
 };
 
+// Blends of N and LDA (Sec. 3.3.3): diagonal Theta (B), every diagonal entry
+// max_k / min_k Theta_kk (Bmax / Bmin), or the scalar shock-sensor theta (Bx).
+enum : int { BLEND_B = 0, BLEND_MAX = 1, BLEND_MIN = 2, BLEND_X = 3 };
+
 // Magnitude comparisons through the IEEE-754 bit patterns.  For numbers that
 // are not NaN the integer order of |x|'s bit pattern is the numeric order of
 // |x|, so in double precision these run on the integer pipe instead of the
@@ -433,16 +437,68 @@ RD_HD void lda_apply(const TriLin<T>& L, const T x[4], T out[3][4]) {
 
 // Theta_kk = |tot_k| / max(sum_i |N_ik|, |tot_k|) (0/0 -> 0); out = Theta N + (1-Theta) LDA.
 template <class T>
-RD_HD void blend(const T tot[4], const T N[3][4], const T lda[3][4], T out[3][4]) {
+RD_HD void blend(const T tot[4], const T N[3][4], const T lda[3][4], T out[3][4], int mode = BLEND_B,
+                 T theta_x = T(0)) {
+  T th[4];
+  if (mode == BLEND_X) {
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    T num = fabs(tot[k]);
-    T den = fabs(N[0][k]) + fabs(N[1][k]) + fabs(N[2][k]);
-    den = mag_less(num, den) ? den : num;
-    T th = mag_positive(den) ? num / den : T(0);
+    for (int k = 0; k < 4; ++k) th[k] = theta_x;
+  } else {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) out[i][k] = th * N[i][k] + (T(1) - th) * lda[i][k];
+    for (int k = 0; k < 4; ++k) {
+      T num = fabs(tot[k]);
+      T den = fabs(N[0][k]) + fabs(N[1][k]) + fabs(N[2][k]);
+      den = mag_less(num, den) ? den : num;
+      th[k] = mag_positive(den) ? num / den : T(0);
+    }
+    if (mode == BLEND_MAX || mode == BLEND_MIN) {
+      // Bmax / Bmin: one weight, the largest or smallest Theta_kk (all >= 0)
+      T e = th[0];
+#pragma unroll
+      for (int k = 1; k < 4; ++k) {
+        bool take = mode == BLEND_MAX ? mag_less(e, th[k]) : mag_less(th[k], e);
+        e = take ? th[k] : e;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) th[k] = e;
+    }
   }
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) out[i][k] = th[k] * N[i][k] + (T(1) - th[k]) * lda[i][k];
+}
+
+// Shock sensor of the Bx blend (Sec. 3.3.3): theta = min(1, s^2 h_T / L),
+// s = max(0, -L div v / vrange), div v of the linear interpolant of the vertex
+// velocities u_c = Z_c1 / Z_c0, v_c = Z_c2 / Z_c0 (grad phi_c = n_c |e_c| / (2 |T|)
+// with unit inward normals n_c and |e_c| = 2 hl_c), h_T = sqrt(2 |T|).
+template <class T>
+RD_HD T bx_theta(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3], T area, T L, T vrange) {
+  if (!positive(vrange)) return T(0);
+  T div = T(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    T iz = T(1) / Z[c][0];
+    div += (Z[c][1] * iz * nx[c] + Z[c][2] * iz * ny[c]) * hl[c];
+  }
+  T s = -L * (div / area) / vrange;
+  if (!positive(s)) return T(0);
+  T th = s * s * sqrt(T(2) * area) / L;
+  return mag_less(th, T(1)) ? th : T(1);
+}
+
+// Run-time blend configuration of the two-stage triangle kernels.
+template <class T>
+struct BlendArgs {
+  int mode = BLEND_B;                      // BLEND_B | BLEND_MAX | BLEND_MIN | BLEND_X
+  int sl = 0;                              // stage 2: selective lumping
+  T L = T(1);                              // domain size max(Lx, Ly) (Bx)
+  const unsigned long long* vr = nullptr;  // Bx: bits of |v|_max, |v|_min of the distributed state
+};
+template <class T>
+__device__ __forceinline__ T vrange_of(const unsigned long long* vr) {
+  return (T)(__longlong_as_double((long long)vr[0]) - __longlong_as_double((long long)vr[1]));
 }
 
 template <class T>
@@ -490,7 +546,7 @@ __device__ __forceinline__ void load_vec4(const T* __restrict__ A, int i, T out[
 // phi^N_0..2 and phi^T at W^n, reused by stage 2.  Returns an ST_* status.
 template <class T, int SCHEME>
 RD_HD int stage1_body(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3], const Gas<T>& gas, T eps,
-                      T out[3][4], T rec[16]) {
+                      T out[3][4], T rec[16], int bmode = BLEND_B, T theta_x = T(0)) {
   TriLin<T> L;
   int st = linearise(Z, nx, ny, hl, gas, eps, L);
   if (st) return st;
@@ -509,7 +565,7 @@ RD_HD int stage1_body(const T Z[3][4], const T nx[3], const T ny[3], const T hl[
 #pragma unroll
       for (int k = 0; k < 4; ++k) out[i][k] = lda[i][k];
   } else {
-    blend(L.phiT, L.phiN, lda, out);
+    blend(L.phiT, L.phiN, lda, out, bmode, theta_x);
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -527,7 +583,8 @@ RD_HD int stage1_body(const T Z[3][4], const T nx[3], const T ny[3], const T hl[
 //   Phi_i     = Theta Phi^N_i + (I - Theta) Phi^LDA_i, Theta from (Phi^T, Phi^N)
 template <class T, int SCHEME>
 RD_HD int stage2_body(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], const T rec[16], const T nx[3],
-                      const T ny[3], const T hl[3], T area, T dt, const Gas<T>& gas, T eps, T out[3][4]) {
+                      const T ny[3], const T hl[3], T area, T dt, const Gas<T>& gas, T eps, T out[3][4],
+                      int bmode = BLEND_B, T theta_x = T(0), int sl = 0) {
   TriLin<T> L;
   int st = linearise(Zs, nx, ny, hl, gas, eps, L);
   if (st) return st;
@@ -554,7 +611,20 @@ RD_HD int stage2_body(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], cons
 #pragma unroll
       for (int k = 0; k < 4; ++k) out[i][k] = lda[i][k];
   } else {
-    blend(PhiT, PhiN, lda, out);
+    blend(PhiT, PhiN, lda, out, bmode, theta_x);
+  }
+  if (sl) {
+    // selective lumping: + sum_j (|T| delta_ij / 3 - |T| (delta_ij + 1) / 12) (W*_j - W^n_j) / dt
+    //                    = |T| / 4 dW_i / dt - |T| / 12 sum_j dW_j / dt
+    const T q = area * T(0.25) * idt, tw = area * (T(1) / T(12)) * idt;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      T d0 = Ws[0][k] - Wn[0][k], d1 = Ws[1][k] - Wn[1][k], d2 = Ws[2][k] - Wn[2][k];
+      T sum = tw * (d0 + d1 + d2);
+      out[0][k] += q * d0 - sum;
+      out[1][k] += q * d1 - sum;
+      out[2][k] += q * d2 - sum;
+    }
   }
   return 0;
 }
@@ -578,7 +648,8 @@ template <class T, int SCHEME>
 __global__ void __launch_bounds__(256, (TriOcc<T, 1>::value)) k_tri_stage1(int nt, int nv, const int* __restrict__ tri, DevGeo<T> g,
                                                     const T* __restrict__ Z, const T* __restrict__ spd,
                                                     Gas<T> gas, T eps, T* __restrict__ share,
-                                                    T* __restrict__ rec, T* __restrict__ cfl, DevCtl* ctl) {
+                                                    T* __restrict__ rec, T* __restrict__ cfl, DevCtl* ctl,
+                                                    BlendArgs<T> ba = BlendArgs<T>()) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt || ctl->stop) return;
   int v[3];
@@ -593,7 +664,10 @@ __global__ void __launch_bounds__(256, (TriOcc<T, 1>::value)) k_tri_stage1(int n
     cfl[t] = __ldg(g.lmax + t) * lam;
   }
   T out[3][4], r[16];
-  int st = stage1_body<T, SCHEME>(Zc, nx, ny, hl, gas, eps, out, r);
+  T thx = T(0);
+  if (SCHEME == RD_B2 && ba.mode == BLEND_X)
+    thx = bx_theta(Zc, nx, ny, hl, __ldg(g.area + t), ba.L, vrange_of<T>(ba.vr));
+  int st = stage1_body<T, SCHEME>(Zc, nx, ny, hl, gas, eps, out, r, ba.mode, thx);
   if (st) {
     atomicOr(&ctl->status, st);
     return;
@@ -747,7 +821,7 @@ __global__ void __launch_bounds__(BLOCK) k_gather_cfl(int nv, const int* __restr
 
 // Vertex state -> parameter vector Z and |v| + c; returns false if non-physical.
 template <class T>
-RD_HD bool vertex_Z(const T W[4], T gamma, T Z[4], T& spd) {
+RD_HD bool vertex_Z(const T W[4], T gamma, T Z[4], T& spd, T* vmag = nullptr) {
   T rho = W[0];
   if (!(rho > T(0))) return false;
   T u = W[1] / rho, v = W[2] / rho;
@@ -759,8 +833,51 @@ RD_HD bool vertex_Z(const T W[4], T gamma, T Z[4], T& spd) {
   Z[1] = sr * u;
   Z[2] = sr * v;
   Z[3] = sr * h;
-  spd = sqrt(u * u + v * v) + sqrt(gamma * p / rho);
+  T q = sqrt(u * u + v * v);
+  spd = q + sqrt(gamma * p / rho);
+  if (vmag) *vmag = q;
   return true;
+}
+
+// Block-wide max and min of the non-negative vertex speeds |v| (Bx sensor),
+// folded into vr[0] (max) and vr[1] (min) through their IEEE bit patterns (the
+// integer order of non-negative doubles is their numeric order), one pair of
+// atomics per block.  Every thread of the block calls it (blockDim a multiple
+// of 32, at most 512); has = false contributes nothing.
+__device__ __forceinline__ void vrange_fold(bool has, double q, unsigned long long* vr) {
+  unsigned long long hi = has ? (unsigned long long)__double_as_longlong(q) : 0ull;
+  unsigned long long lo = has ? hi : 0x7ff0000000000000ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    hi = h2 > hi ? h2 : hi;
+    lo = l2 < lo ? l2 : lo;
+  }
+  __shared__ unsigned long long sh[2][16];
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][w] = hi;
+    sh[1][w] = lo;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int j = 1; j < nw; ++j) {
+      hi = sh[0][j] > hi ? sh[0][j] : hi;
+      lo = sh[1][j] < lo ? sh[1][j] : lo;
+    }
+    atomicMax(vr, hi);
+    atomicMin(vr + 1, lo);
+  }
+}
+
+// Empty |v| range (max = +0, min = +inf) before a pass reduces into vr;
+// skipped once the run has stopped, so that the last reduced range stays valid.
+static __global__ void k_vr_reset(unsigned long long* vr, const DevCtl* ctl, int force) {
+  if (force || !ctl->stop) {
+    vr[0] = 0ull;
+    vr[1] = 0x7ff0000000000000ull;
+  }
 }
 
 // W_out = W_in - dt/V R; Z_out = Z(W_out); spd_out (nullable) = |v| + c.
@@ -771,9 +888,14 @@ __global__ void __launch_bounds__(512) k_update(int nv, const T* __restrict__ Wi
                                                 const T* __restrict__ share, const T* __restrict__ V, T gamma,
                                                 T* __restrict__ Wout, T* __restrict__ Zout, T* __restrict__ spdout,
                                                 DevCtl* ctl, const double* __restrict__ dtm = nullptr,
-                                                const uint16_t* __restrict__ vmesh = nullptr) {
+                                                const uint16_t* __restrict__ vmesh = nullptr,
+                                                unsigned long long* __restrict__ vr_out = nullptr) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nv || ctl->stop) return;
+  const bool act = i < nv && !ctl->stop;
+  if (!act && !vr_out) return;
+  bool has = false;
+  T q = T(0);
+  if (act) {
   T r[4];
   if (share) {
     r[0] = r[1] = r[2] = r[3] = T(0);
@@ -788,7 +910,7 @@ __global__ void __launch_bounds__(512) k_update(int nv, const T* __restrict__ Wi
   load_vec4(Win, i, W);
 #pragma unroll
   for (int k = 0; k < 4; ++k) W[k] = W[k] - f * r[k];
-  bool ok = vertex_Z(W, gamma, Z, spd);
+  bool ok = vertex_Z(W, gamma, Z, spd, &q);
   st4(Wout + 4 * (size_t)i, W);
   st4(Zout + 4 * (size_t)i, Z);
   if (spdout) spdout[i] = spd;
@@ -796,20 +918,29 @@ __global__ void __launch_bounds__(512) k_update(int nv, const T* __restrict__ Wi
     atomicOr(&ctl->status, ST_NONPHYS_VERTEX);
     ctl->stop = 1;
   }
+  has = ok;
+  }
+  if (vr_out) vrange_fold(has, (double)q, vr_out);
 }
 
 // Z and |v|+c of a freshly uploaded state.
 template <class T>
 __global__ void k_prepare(int nv, const T* __restrict__ W, T gamma, T* __restrict__ Z, T* __restrict__ spd,
-                          DevCtl* ctl) {
+                          DevCtl* ctl, unsigned long long* __restrict__ vr_out = nullptr) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nv) return;
-  T w[4], z[4], s;
-  load_vec4(W, i, w);
-  bool ok = vertex_Z(w, gamma, z, s);
-  st4(Z + 4 * (size_t)i, z);
-  spd[i] = s;
-  if (!ok) atomicOr(&ctl->status, ST_NONPHYS_VERTEX);
+  if (i >= nv && !vr_out) return;
+  bool has = false;
+  T q = T(0);
+  if (i < nv) {
+    T w[4], z[4], s;
+    load_vec4(W, i, w);
+    bool ok = vertex_Z(w, gamma, z, s, &q);
+    st4(Z + 4 * (size_t)i, z);
+    spd[i] = s;
+    if (!ok) atomicOr(&ctl->status, ST_NONPHYS_VERTEX);
+    has = ok;
+  }
+  if (vr_out) vrange_fold(has, (double)q, vr_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -821,7 +952,8 @@ __global__ void __launch_bounds__(256, (TriOcc<T, 2>::value)) k_tri_stage2(int n
                                                     const T* __restrict__ Ws, const T* __restrict__ rec,
                                                     Gas<T> gas, T eps, T* __restrict__ share, DevCtl* ctl,
                                                     const double* __restrict__ dtm = nullptr,
-                                                    const uint16_t* __restrict__ tmesh = nullptr) {
+                                                    const uint16_t* __restrict__ tmesh = nullptr,
+                                                    BlendArgs<T> ba = BlendArgs<T>()) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt || ctl->stop) return;
   int v[3];
@@ -838,7 +970,10 @@ __global__ void __launch_bounds__(256, (TriOcc<T, 2>::value)) k_tri_stage2(int n
   for (int k = 0; k < 4; ++k) ld4(rp + 4 * k, r + 4 * k);
   T out[3][4];
   T dt = dtm ? (T)__ldg(dtm + __ldg(tmesh + t)) : (T)ctl->dt;
-  int st = stage2_body<T, SCHEME>(Zc, wn, ws, r, nx, ny, hl, __ldg(g.area + t), dt, gas, eps, out);
+  const T area = __ldg(g.area + t);
+  T thx = T(0);
+  if (SCHEME == RD_B2 && ba.mode == BLEND_X) thx = bx_theta(Zc, nx, ny, hl, area, ba.L, vrange_of<T>(ba.vr));
+  int st = stage2_body<T, SCHEME>(Zc, wn, ws, r, nx, ny, hl, area, dt, gas, eps, out, ba.mode, thx, ba.sl);
   if (st) {
     atomicOr(&ctl->status, st);
     return;
