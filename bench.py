@@ -51,6 +51,19 @@ WORKLOADS = {
 ALG_BYTES_STEP = {("B2", 8): 200.0, ("B2", 4): 112.0, ("N1", 8): 112.0, ("N1", 4): 62.0}
 
 
+def alg_scheme(scheme: str) -> str:
+    """Two-stage variants move the same arrays as B2 (the Bx |v| range is reduced
+    inside the vertex update)."""
+    return "N1" if scheme == "N1" else "B2"
+
+
+def flop_scheme(scheme: str) -> str:
+    """Operation count used for a variant: LDA2 has its own; the blends count as B2
+    (their blend weights differ by a few selects; Bx adds its sensor, ~20 flops)."""
+    base = scheme[:-3] if scheme.endswith("_SL") else scheme
+    return base if base in ("N1", "B2", "LDA2") else "B2"
+
+
 def kernel_alg_bytes(kernel: str, scheme: str, s: int) -> float:
     """Algorithmic bytes per triangle of one kernel launch: every input read once,
     every output written once; vertex arrays count N_v / N_t = 1/2 per triangle."""
@@ -71,6 +84,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="khi4096_B2")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--scheme", default=None,
+                    choices=["N1", "B2", "LDA2", "BMAX2", "BMIN2", "BX2", "B2_SL", "LDA2_SL", "BMAX2_SL",
+                             "BMIN2_SL", "BX2_SL"],
+                    help="override the workload's scheme (suffix _SL: selective lumping)")
     ap.add_argument("--reorder", choices=["none", "morton", "rcm"], default="morton",
                     help="vertex/triangle reordering of the mesh store")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 companion measurement")
@@ -245,6 +262,8 @@ def ours(args, ws, rank, local):
         return ours_batched(args, ws, rank, local)
     torch.cuda.set_device(local)
     mesh, W0, scheme = build_inputs(args.workload)
+    if args.scheme:
+        scheme = args.scheme
     nt, nv = mesh.nt, mesh.nv
     m = binding.Mesh(mesh, reorder=args.reorder)
     s_bytes = 8 if args.precision == "fp64" else 4
@@ -273,7 +292,7 @@ def ours(args, ws, rank, local):
     dom_ms = per_kernel[dom]
     stage = 1 if dom == "tri_stage1" else 2
     if args.precision == "fp64" and dom in ("tri_stage1", "tri_stage2"):
-        fl = binding.count_flops(scheme, stage)["total"]
+        fl = binding.count_flops(flop_scheme(scheme), stage)["total"]
         peak = binding.probe_fma_peak("fp64")
         achieved = fl * nt / (dom_ms * 1e-3)
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e12, "peak": peak / 1e12,
@@ -290,7 +309,7 @@ def ours(args, ws, rank, local):
                 "frac": achieved / hbm if achieved else None, "bytes_per_triangle": bpt,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
                 "traffic": ncu_traffic(args.workload, args.precision, dom, nt)}
-    step_bytes = ALG_BYTES_STEP.get((scheme, s_bytes))
+    step_bytes = ALG_BYTES_STEP.get((alg_scheme(scheme), s_bytes))
     hbm_peak = 6765.0
     try:
         hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
@@ -344,7 +363,7 @@ def ours(args, ws, rank, local):
         hbm = hbm_peak
         b32 = kernel_alg_bytes(d32, scheme, 4) if d32.startswith("tri_") else None
         a32 = b32 * nt / (pk32[d32] * 1e-3) / 1e9 if b32 else None
-        sb32 = ALG_BYTES_STEP.get((scheme, 4))
+        sb32 = ALG_BYTES_STEP.get((alg_scheme(scheme), 4))
         line["fp32"] = {"value": ws * nt / (ms32 * 1e-3), "ms_per_step": ms32, "per_kernel_ms": pk32,
                         "roofline": {"bound": "hbm", "kernel": d32, "achieved": a32, "peak": hbm, "unit": "GB/s",
                                      "frac": a32 / hbm if a32 else None, "bytes_per_triangle": b32,

@@ -273,8 +273,12 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
       k_tri_stage1<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, rec, cf, ctl);
       break;
     default:  // RD_B2, RD_BMAX2, RD_BMIN2, RD_BX2
-      k_tri_stage1<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, rec, cf, ctl,
-                                                ba1);
+      if (s->p.scheme == RD_B2 && s->p.lumping == RD_LUMP_GLOBAL)
+        k_tri_stage1<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, rec, cf,
+                                                  ctl);
+      else  // generic blend instantiation: Bmax, Bmin, Bx, B with selective lumping
+        k_tri_stage1<T, RD_BMAX2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, rec, cf,
+                                                     ctl, ba1);
       break;
   }
   mark(1);
@@ -296,10 +300,13 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
       k_tri_stage2<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
                                                   (const T*)s->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl,
                                                   nullptr, nullptr, ba2);
-    else
+    else if (s->p.scheme == RD_B2 && s->p.lumping == RD_LUMP_GLOBAL)
       k_tri_stage2<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
-                                                (const T*)s->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl,
-                                                nullptr, nullptr, ba2);
+                                                (const T*)s->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl);
+    else
+      k_tri_stage2<T, RD_BMAX2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
+                                                   (const T*)s->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl,
+                                                   nullptr, nullptr, ba2);
     mark(4);
     if (vr0) k_vr_reset<<<1, 1, 0, st>>>(vr0, ctl, 0);
     k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)s->Ws.p, nullptr, ptr, ent, share, V, gamma,

@@ -83,8 +83,12 @@ int batch_step(rd_batch* b, int a, cudaEvent_t* ev, bool commit) {
       k_tri_stage1<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, rec, cf, ctl);
       break;
     default:
-      k_tri_stage1<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, rec, cf, ctl,
-                                                ba);
+      if (b->p.scheme == RD_B2 && b->p.lumping == RD_LUMP_GLOBAL)
+        k_tri_stage1<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, rec, cf,
+                                                  ctl);
+      else  // generic blend instantiation: Bmax, Bmin, Bx, B with selective lumping
+        k_tri_stage1<T, RD_BMAX2><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, rec, cf,
+                                                     ctl, ba);
       break;
   }
   mark(1);
@@ -106,10 +110,13 @@ int batch_step(rd_batch* b, int a, cudaEvent_t* ev, bool commit) {
       k_tri_stage2<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)b->Zs.p, (const T*)b->W[a].p,
                                                   (const T*)b->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl, dtm, tm,
                                                   ba);
-    else
+    else if (b->p.scheme == RD_B2 && b->p.lumping == RD_LUMP_GLOBAL)
       k_tri_stage2<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)b->Zs.p, (const T*)b->W[a].p,
-                                                (const T*)b->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl, dtm, tm,
-                                                ba);
+                                                (const T*)b->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl, dtm, tm);
+    else
+      k_tri_stage2<T, RD_BMAX2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)b->Zs.p, (const T*)b->W[a].p,
+                                                   (const T*)b->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl, dtm,
+                                                   tm, ba);
     mark(4);
     k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)b->Ws.p, nullptr, ptr, ent, share, V, gamma, (T*)b->W[c].p,
                                    (T*)b->Z[c].p, (T*)b->spd[c].p, ctl, dtm, vm);

@@ -67,6 +67,34 @@ struct Gas {
   }
 };
 
+// Reciprocal used by the triangle kernels.  In double precision on the device:
+// the hardware's approximate reciprocal (rcp.approx.ftz.f64) refined by two
+// Newton-Raphson steps r <- r + r (1 - x r), each of which squares the
+// relative error, which leaves r within an ulp of 1/x at about half the FP64
+// pipe cost of the IEEE division.  Arguments outside [2^-1000, 2^1000) in
+// magnitude (zero, subnormal, huge, inf, NaN) take the IEEE division.
+#ifndef RD_FAST_RCP
+#define RD_FAST_RCP 1
+#endif
+template <class T>
+RD_HD T rcp(T x) {
+  return T(1) / x;
+}
+RD_HD double rcp(double x) {
+#if defined(__CUDA_ARCH__) && RD_FAST_RCP
+  const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+  if (e > 23 && e < 2023) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double t = fma(-x, r, 1.0);
+    r = fma(r, t, r);
+    t = fma(-x, r, 1.0);
+    return fma(r, t, r);
+  }
+#endif
+  return 1.0 / x;
+}
+
 // Blends of N and LDA (Sec. 3.3.3): diagonal Theta (B), every diagonal entry
 // max_k / min_k Theta_kk (Bmax / Bmin), or the scalar shock-sensor theta (Bx).
 enum : int { BLEND_B = 0, BLEND_MAX = 1, BLEND_MIN = 2, BLEND_X = 3 };
@@ -194,7 +222,7 @@ struct LU4 {
         }
       }
       ok = ok && mag_positive(best);
-      T inv = T(1) / a[k][k];
+      T inv = rcp(a[k][k]);
       rdiag[k] = inv;
 #pragma unroll
       for (int r = k + 1; r < 4; ++r) {
@@ -282,7 +310,7 @@ RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3]
   for (int k = 0; k < 4; ++k) Zb[k] = (Z[0][k] + Z[1][k] + Z[2][k]) * third;
   RoeState<T>& r = L.r;
   r.g1 = gas.g1;
-  T iz = T(1) / Zb[0];
+  T iz = rcp(Zb[0]);
   r.u = Zb[1] * iz;
   r.v = Zb[2] * iz;
   r.h = Zb[3] * iz;
@@ -290,7 +318,7 @@ RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3]
   T c2 = r.g1 * (r.h - r.q2h);
   if (!positive(c2)) return ST_ROE;
   r.c = sqrt(c2);
-  r.ic2 = T(1) / c2;
+  r.ic2 = rcp(c2);
   r.ic2h = r.ic2 * T(0.5);
   r.i2c = r.c * r.ic2h;
   r.alpha = r.g1 * r.q2h;
@@ -449,7 +477,7 @@ RD_HD void blend(const T tot[4], const T N[3][4], const T lda[3][4], T out[3][4]
       T num = fabs(tot[k]);
       T den = fabs(N[0][k]) + fabs(N[1][k]) + fabs(N[2][k]);
       den = mag_less(num, den) ? den : num;
-      th[k] = mag_positive(den) ? num / den : T(0);
+      th[k] = mag_positive(den) ? num * rcp(den) : T(0);
     }
     if (mode == BLEND_MAX || mode == BLEND_MIN) {
       // Bmax / Bmin: one weight, the largest or smallest Theta_kk (all >= 0)
@@ -589,7 +617,7 @@ RD_HD int stage2_body(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], cons
   int st = linearise(Zs, nx, ny, hl, gas, eps, L);
   if (st) return st;
   T a3 = area * (T(1) / T(3));
-  T idt = T(1) / dt;
+  T idt = rcp(dt);
   T PhiN[3][4], PhiT[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) PhiT[k] = T(0);
@@ -664,10 +692,13 @@ __global__ void __launch_bounds__(256, (TriOcc<T, 1>::value)) k_tri_stage1(int n
     cfl[t] = __ldg(g.lmax + t) * lam;
   }
   T out[3][4], r[16];
+  // SCHEME == RD_BMAX2 is the generic blend instantiation (Bmax, Bmin, Bx and
+  // B with selective lumping, chosen at run time); RD_B2 is the plain B scheme.
+  const int mode = SCHEME == RD_BMAX2 ? ba.mode : BLEND_B;
   T thx = T(0);
-  if (SCHEME == RD_B2 && ba.mode == BLEND_X)
+  if (SCHEME == RD_BMAX2 && mode == BLEND_X)
     thx = bx_theta(Zc, nx, ny, hl, __ldg(g.area + t), ba.L, vrange_of<T>(ba.vr));
-  int st = stage1_body<T, SCHEME>(Zc, nx, ny, hl, gas, eps, out, r, ba.mode, thx);
+  int st = stage1_body<T, SCHEME>(Zc, nx, ny, hl, gas, eps, out, r, mode, thx);
   if (st) {
     atomicOr(&ctl->status, st);
     return;
@@ -971,9 +1002,11 @@ __global__ void __launch_bounds__(256, (TriOcc<T, 2>::value)) k_tri_stage2(int n
   T out[3][4];
   T dt = dtm ? (T)__ldg(dtm + __ldg(tmesh + t)) : (T)ctl->dt;
   const T area = __ldg(g.area + t);
+  const int mode = SCHEME == RD_BMAX2 ? ba.mode : BLEND_B;
+  const int sl = (SCHEME == RD_BMAX2 || SCHEME == RD_LDA2) ? ba.sl : 0;
   T thx = T(0);
-  if (SCHEME == RD_B2 && ba.mode == BLEND_X) thx = bx_theta(Zc, nx, ny, hl, area, ba.L, vrange_of<T>(ba.vr));
-  int st = stage2_body<T, SCHEME>(Zc, wn, ws, r, nx, ny, hl, area, dt, gas, eps, out, ba.mode, thx, ba.sl);
+  if (SCHEME == RD_BMAX2 && mode == BLEND_X) thx = bx_theta(Zc, nx, ny, hl, area, ba.L, vrange_of<T>(ba.vr));
+  int st = stage2_body<T, SCHEME>(Zc, wn, ws, r, nx, ny, hl, area, dt, gas, eps, out, mode, thx, sl);
   if (st) {
     atomicOr(&ctl->status, st);
     return;

@@ -2,7 +2,10 @@
 Bmax, Bmin, the Bx shock-sensor blend and selective lumping.  Tolerance as for
 the B scheme: 1e-12 relative in the max norm against the oracle's long-double
 instantiation (Sod-like runs over their first 20 steps, where the blended
-schemes' round-off growth at the resting interface is still below it)."""
+schemes' round-off growth at the resting interface is still below it: 20
+steps, 10 for Bmax, whose single max-weight amplifies round-off fastest -- the
+oracle's own double and long-double runs part by 6.4e-12 after 20 Bmax steps
+on the 48^2 Sod-like state and by 1.7e-13 after 10)."""
 import os
 
 import numpy as np
@@ -30,7 +33,7 @@ STATES = {"vortex": inputs.vortex_state, "khi": inputs.khi_state, "sod": inputs.
 
 
 @pytest.mark.parametrize("scheme,state,N,mesh_kind,steps", [
-    ("BMAX2", "sod", 48, "grid", 20), ("BMAX2", "khi", 48, "jit", 100),
+    ("BMAX2", "sod", 48, "grid", 10), ("BMAX2", "khi", 48, "jit", 100),
     ("BMIN2", "vortex", 48, "jit", 100), ("BMIN2", "khis", 40, "grid", 100),
     ("BX2", "khi", 40, "jit", 100), ("BX2", "sod", 40, "grid", 20), ("BX2", "vortex", 32, "grid", 100),
     ("B2_SL", "vortex", 48, "jit", 100), ("LDA2_SL", "vortex", 40, "grid", 100),
@@ -44,8 +47,10 @@ def test_variant_parity(rd, scheme, state, N, mesh_kind, steps):
     s = binding.State(m, W0, scheme=scheme)
     assert s.run(steps) == steps
     Wld, dto = oracle.run(mesh, W0, scheme, nsteps=steps, nthreads=NTH, long_double=True)
-    err = rel_max_err(s.get(), Wld)
-    print(f"{scheme} {state} {N}^2 {mesh_kind} {steps} steps: {err:.2e}")
+    Wd, _ = oracle.run(mesh, W0, scheme, nsteps=steps, nthreads=NTH)
+    err, floor = rel_max_err(s.get(), Wld), rel_max_err(Wd, Wld)
+    print(f"{scheme} {state} {N}^2 {mesh_kind} {steps} steps: GPU vs oracle(ld) {err:.2e}, "
+          f"oracle(double) vs oracle(ld) {floor:.2e}")
     assert err < TOL
     t, _ = s.time()
     assert t == pytest.approx(dto.sum(), rel=1e-13)
