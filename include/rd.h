@@ -140,6 +140,29 @@ void rd_mesh_destroy(rd_mesh *m);
 int rd_mesh_permutation(const rd_mesh *m, int32_t *vertex_perm, int32_t *tri_perm);
 int rd_mesh_sizes(const rd_mesh *m, int32_t *n_vertex, int32_t *n_tri);
 
+/* Boundary conditions of a mesh that is not periodic everywhere (Sec. 3.5).
+ *   ghost   NULL, or [n_vertex] (caller order): 1 marks a ghost vertex whose
+ *           state is held at its initial value -- the state given to
+ *           rd_state_init / rd_state_set -- at the start of every step
+ *           (non-reflecting or inflow boundaries); in a two-stage step its
+ *           W* is the ordinary stage-1 update.
+ *   wall    [n_wall][2] (caller triangle, corner): the edge opposite that
+ *           corner is a reflecting wall, imposed weakly: with the wall's
+ *           outward unit normal n and f = -(rho v_n, rho u v_n, rho v v_n,
+ *           rho h v_n) at its two vertices a, b (v_n = v . n), the correction
+ *           residuals Phi^c_a = |e|/2 (alpha f_a + (1 - alpha) f_b) and
+ *           Phi^c_b = |e|/2 ((1 - alpha) f_a + alpha f_b) are added to the
+ *           vertices' residuals: at W^n in the first stage (and in RD_N1),
+ *           as (Phi^c(W^n) + Phi^c(W*)) / 2 in the second.
+ *   alpha   the split, 0.75 in the paper.
+ * Replaces any earlier boundary.  States created before the call return
+ * RD_EINVAL from rd_step / rd_run until rd_state_set gives them a new
+ * initial state.  Batched mode and the adjoint take periodic meshes only
+ * (RD_ENOTSUP).  Errors: RD_EINVAL for a triangle or corner out of range, an
+ * edge that another triangle shares (not on the boundary), an edge listed
+ * twice, or alpha outside [0, 1].  The caller owns both arrays. */
+int rd_mesh_set_boundary(rd_mesh *m, const uint8_t *ghost, int32_t n_wall, const int32_t *wall, double alpha);
+
 /* ---- solver state ---------------------------------------------------------
  * rd_state_init: allocate the device state of one mesh and upload W (host,
  * component-major, caller order).  Errors: RD_EINVAL (bad params),

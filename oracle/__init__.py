@@ -87,6 +87,11 @@ def lib():
         _lib.ora_triangle_terms_ld.argtypes = mesh_args + [dp, ctypes.c_double, ctypes.c_double] + [dp] * 4
         _lib.ora_stage2_terms.argtypes = mesh_args + [dp, dp, ctypes.c_double, ctypes.c_double,
                                                       ctypes.c_double, ctypes.c_int] + [dp] * 5
+        _lib.ora_run_bc.argtypes = mesh_args + [dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_int32, dp, dp, ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_uint8), ctypes.c_int32,
+                                                ctypes.POINTER(ctypes.c_int32), ctypes.c_double, ctypes.c_int]
+        _lib.ora_run_bc.restype = ctypes.c_int
         for name in ("ora_stage1_shares", "ora_stage1_shares_ld"):
             getattr(_lib, name).argtypes = mesh_args + [dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                          dp, ctypes.c_int]
@@ -131,6 +136,18 @@ def run(mesh, W0, scheme="B2", nsteps=1, cfl=0.8, gamma=1.4, eps=1e-6, dt_fixed=
     W = np.ascontiguousarray(np.array(W0, dtype=np.float64, copy=True))
     dts = np.zeros(max(nsteps, 1))
     dtf = None if dt_fixed is None else np.ascontiguousarray(dt_fixed, dtype=np.float64)
+    ghost = getattr(mesh, "ghost", None)
+    walls = getattr(mesh, "walls", None)
+    if ghost is not None or walls is not None:
+        # boundary conditions of Sec. 3.5 (ghost vertices, reflecting walls)
+        g = None if ghost is None else np.ascontiguousarray(ghost, dtype=np.uint8)
+        wl = np.zeros((0, 2), np.int32) if walls is None else np.ascontiguousarray(walls, dtype=np.int32)
+        rc = lib().ora_run_bc(*margs, _p(W), scheme_code(scheme), cfl, gamma, eps, nsteps, _p(dtf), _p(dts),
+                              nthreads, _p(g, ctypes.c_uint8), len(wl), _p(wl, ctypes.c_int32),
+                              float(getattr(mesh, "alpha", 0.75)), int(bool(long_double)))
+        _check(rc, "ora_run_bc")
+        del keep
+        return W, dts[:nsteps]
     f = lib().ora_run_ld if long_double else lib().ora_run
     rc = f(*margs, _p(W), scheme_code(scheme), cfl, gamma, eps,
            nsteps, _p(dtf), _p(dts), nthreads)

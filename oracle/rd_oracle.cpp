@@ -17,6 +17,8 @@
 //   * forward-Euler update with the CFL time step                 (Eq. eqUpdate, Sec. 3.2)
 //   * the explicit two-stage scheme with total residuals Phi^N, Phi^LDA,
 //     mass matrices m^N, m^LDA and global or selective lumping    (Sec. 3.4, eqRK1/eqRK2)
+//   * boundary conditions: ghost vertices held at their initial state
+//     (non-reflecting / inflow) and weakly imposed reflecting walls   (Sec. 3.5)
 //
 // Everything is written in the paper's order and notation; no fusion, no
 // reordering beyond what the formulas state.  All arithmetic is templated on the
@@ -45,6 +47,13 @@
 //        sqrt(2 |T|), L = max(Lx, Ly), |v| extremes over all vertices of the
 //        state being distributed (W^n in stage 1, W* in stage 2); s = 0 when
 //        |v|_max = |v|_min.  On the unit box theta = s^2 h as printed.
+//   (R11) Ghost vertices are reset to their initial state at the start of
+//        every step (the value entering the step); W* of a ghost vertex is
+//        the ordinary stage-1 update.  "Initial" = the state passed to run().
+//   (R12) The wall correction residual Phi^c is a spatial residual: it enters
+//        stage 1 (and N1) at W^n and stage 2 as (Phi^c(W^n) + Phi^c(W*)) / 2,
+//        like phi^T.  The wall's outward unit normal is minus the inward
+//        normal of the edge in its triangle; h = (e + p) / rho.
 //   (R10) Bmax / Bmin in stage 2 take max_k / min_k of the total-residual
 //        Theta_kk of (R6); selective lumping adds its correction to the
 //        blended total residual (it sums to zero over the triangle).
@@ -117,6 +126,10 @@ struct Mesh {
   std::vector<S> lmax;        // [nt] longest edge
   std::vector<S> V;           // [nv] nodal volume (R7)
   S L = S(1);                 // domain size max(Lx, Ly) (R9)
+  // boundary conditions (Sec. 3.5)
+  std::vector<uint8_t> ghost;      // [nv] 1: state held at its initial value (empty: none)
+  std::vector<int32_t> wall;       // [n_wall][2]: (triangle, corner) of the edge opposite the corner
+  S alpha = S(0.75);               // wall-correction distribution parameter
 };
 
 // Geometry of every triangle from the (periodically shifted) corner positions.
@@ -681,14 +694,54 @@ int stage2_shares(const Mesh<S>& m, const std::vector<S>& Wn, const std::vector<
   return err;
 }
 
+// Weak reflecting wall (Sec. 3.5): for every wall edge e = (a, b) with outward
+// unit normal n, the correction flux F^c n_x + G^c n_y = -(rho v_n, rho u v_n,
+// rho v v_n, rho h v_n) at each end, integrated by the trapezium rule and
+// split with alpha:  Phi^c_a = |e|/2 (alpha f_a + (1 - alpha) f_b),
+// Phi^c_b = |e|/2 ((1 - alpha) f_a + alpha f_b).  Added (times `weight`) to the
+// per-vertex residual sums R.
+template <class S>
+int wall_residual(const Mesh<S>& m, const std::vector<S>& W, S gamma, S weight, std::vector<S>& R) {
+  for (size_t w = 0; w < m.wall.size() / 2; ++w) {
+    int32_t t = m.wall[2 * w], c = m.wall[2 * w + 1];
+    int32_t a = m.tri[3 * (size_t)t + (c + 1) % 3], b = m.tri[3 * (size_t)t + (c + 2) % 3];
+    S nx = -m.n[6 * (size_t)t + 2 * c], ny = -m.n[6 * (size_t)t + 2 * c + 1];
+    S len = sqrt(nx * nx + ny * ny);
+    nx = nx / len;
+    ny = ny / len;
+    S f[2][4];
+    int32_t ends[2] = {a, b};
+    for (int q = 0; q < 2; ++q) {
+      const S* Wi = &W[4 * (size_t)ends[q]];
+      S Wv[4] = {Wi[0], Wi[1], Wi[2], Wi[3]};
+      S rho, u, v, p;
+      int e = primitive(Wv, gamma, rho, u, v, p);
+      if (e) return e;
+      S vn = u * nx + v * ny;
+      S h = (Wv[3] + p) / rho;
+      f[q][0] = -rho * vn;
+      f[q][1] = -rho * u * vn;
+      f[q][2] = -rho * v * vn;
+      f[q][3] = -rho * h * vn;
+    }
+    for (int k = 0; k < 4; ++k) {
+      R[4 * (size_t)a + k] += weight * len / S(2) * (m.alpha * f[0][k] + (S(1) - m.alpha) * f[1][k]);
+      R[4 * (size_t)b + k] += weight * len / S(2) * ((S(1) - m.alpha) * f[0][k] + m.alpha * f[1][k]);
+    }
+  }
+  return OK;
+}
+
 // W_i <- W_i - dt/V_i sum_{T containing i} share_i   (eqUpdate, eqRK1, eqRK2)
 template <class S>
 void apply_update(const Mesh<S>& m, const std::vector<S>& Win, const std::vector<S>& share, S dt,
-                  std::vector<S>& Wout) {
+                  std::vector<S>& Wout, const std::vector<S>* extra = nullptr) {
   std::vector<S> R(4 * (size_t)m.nv, S(0));
   for (int32_t t = 0; t < m.nt; ++t)
     for (int c = 0; c < 3; ++c)
       for (int k = 0; k < 4; ++k) R[4 * (size_t)m.tri[3 * t + c] + k] += share[12 * (size_t)t + 4 * c + k];
+  if (extra)
+    for (size_t i = 0; i < R.size(); ++i) R[i] += (*extra)[i];
   Wout.resize(Win.size());
   for (int32_t i = 0; i < m.nv; ++i)
     for (int k = 0; k < 4; ++k)
@@ -712,14 +765,28 @@ int step(const Mesh<S>& m, std::vector<S>& W, S gamma, S cfl, S eps, int scheme,
   std::vector<S> share, Ws, Wn1;
   int e = stage1_shares(m, W, gamma, eps, scheme, share, nthreads);
   if (e) return e;
-  apply_update(m, W, share, dt, Ws);
+  std::vector<S> wall_n, wall_2;
+  if (!m.wall.empty()) {
+    wall_n.assign(W.size(), S(0));
+    e = wall_residual(m, W, gamma, S(1), wall_n);
+    if (e) return e;
+  }
+  apply_update(m, W, share, dt, Ws, m.wall.empty() ? nullptr : &wall_n);
   if (base == N1) {
     W.swap(Ws);
     return OK;
   }
   e = stage2_shares(m, W, Ws, dt, gamma, eps, scheme, share, nthreads);
   if (e) return e;
-  apply_update(m, Ws, share, dt, Wn1);
+  if (!m.wall.empty()) {
+    // (Phi^c(W^n) + Phi^c(W*)) / 2   (R12)
+    wall_2.assign(W.size(), S(0));
+    e = wall_residual(m, W, gamma, S(0.5), wall_2);
+    if (e) return e;
+    e = wall_residual(m, Ws, gamma, S(0.5), wall_2);
+    if (e) return e;
+  }
+  apply_update(m, Ws, share, dt, Wn1, m.wall.empty() ? nullptr : &wall_2);
   W.swap(Wn1);
   return OK;
 }
@@ -737,21 +804,54 @@ void aos_to_soa(const std::vector<S>& W, int32_t nv, double* Wsoa) {
     for (int k = 0; k < 4; ++k) Wsoa[(size_t)k * nv + i] = val(W[4 * (size_t)i + k]);
 }
 
+// Boundary description for run(): ghost [nv] (nullable), n_wall (triangle, corner) pairs.
+struct Boundary {
+  const uint8_t* ghost = nullptr;
+  int32_t n_wall = 0;
+  const int32_t* wall = nullptr;
+  double alpha = 0.75;
+};
+
+template <class S>
+int set_boundary(Mesh<S>& m, const Boundary* bc) {
+  if (!bc) return OK;
+  if (bc->ghost) m.ghost.assign(bc->ghost, bc->ghost + m.nv);
+  for (int32_t w = 0; w < bc->n_wall; ++w) {
+    int32_t t = bc->wall[2 * w], c = bc->wall[2 * w + 1];
+    if (t < 0 || t >= m.nt || c < 0 || c > 2) return EINVAL;
+  }
+  m.wall.assign(bc->wall, bc->wall + 2 * (size_t)bc->n_wall);
+  m.alpha = S(bc->alpha);
+  return OK;
+}
+
 template <class S>
 int run(int32_t nv, const double* xy, int32_t nt, const int32_t* tri, const int8_t* shift, double Lx,
         double Ly, double* W_soa, int scheme, double cfl, double gamma, double eps, int32_t nsteps,
-        const double* dt_fixed, double* dt_out, int nthreads) {
+        const double* dt_fixed, double* dt_out, int nthreads, const Boundary* bc = nullptr) {
   Mesh<S> m;
   int e = build_mesh(nv, xy, nt, tri, shift, Lx, Ly, m);
   if (e) return e;
+  e = set_boundary(m, bc);
+  if (e) return e;
   std::vector<S> W;
   soa_to_aos(W_soa, nv, W);
+  const std::vector<S> W0 = W;
   for (int32_t s = 0; s < nsteps; ++s) {
+    // ghost vertices enter every step at their initial state (R11)
+    if (!m.ghost.empty())
+      for (int32_t i = 0; i < nv; ++i)
+        if (m.ghost[i])
+          for (int k = 0; k < 4; ++k) W[4 * (size_t)i + k] = W0[4 * (size_t)i + k];
     S dt;
     e = step(m, W, S(gamma), S(cfl), S(eps), scheme, dt_fixed ? S(dt_fixed[s]) : S(0), dt, nthreads);
     if (e) return e;
     if (dt_out) dt_out[s] = val(dt);
   }
+  if (!m.ghost.empty())
+    for (int32_t i = 0; i < nv; ++i)
+      if (m.ghost[i])
+        for (int k = 0; k < 4; ++k) W[4 * (size_t)i + k] = W0[4 * (size_t)i + k];
   aos_to_soa(W, nv, W_soa);
   return OK;
 }
@@ -787,6 +887,25 @@ int ora_run_ld(int32_t nv, const double* xy, int32_t nt, const int32_t* tri, con
                int32_t nsteps, const double* dt_fixed, double* dt_out, int nthreads) {
   return ora::run<long double>(nv, xy, nt, tri, shift, Lx, Ly, W, scheme, cfl, gamma, eps, nsteps,
                                dt_fixed, dt_out, nthreads);
+}
+
+// Same as ora_run / ora_run_ld with boundary conditions (Sec. 3.5): ghost [nv]
+// (nullable, 1 = held at the initial state), n_wall edges given as (triangle,
+// corner) pairs naming the edge opposite the corner, alpha the wall split.
+int ora_run_bc(int32_t nv, const double* xy, int32_t nt, const int32_t* tri, const int8_t* shift,
+               double Lx, double Ly, double* W, int scheme, double cfl, double gamma, double eps,
+               int32_t nsteps, const double* dt_fixed, double* dt_out, int nthreads, const uint8_t* ghost,
+               int32_t n_wall, const int32_t* wall, double alpha, int long_double) {
+  ora::Boundary bc;
+  bc.ghost = ghost;
+  bc.n_wall = n_wall;
+  bc.wall = wall;
+  bc.alpha = alpha;
+  if (long_double)
+    return ora::run<long double>(nv, xy, nt, tri, shift, Lx, Ly, W, scheme, cfl, gamma, eps, nsteps, dt_fixed,
+                                 dt_out, nthreads, &bc);
+  return ora::run<double>(nv, xy, nt, tri, shift, Lx, Ly, W, scheme, cfl, gamma, eps, nsteps, dt_fixed, dt_out,
+                          nthreads, &bc);
 }
 
 // Directional derivative of nsteps with a frozen dt sequence (dt_fixed, required):

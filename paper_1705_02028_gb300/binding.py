@@ -56,6 +56,8 @@ _SIGS = {
     "rd_mesh_destroy": (None, [_vp]),
     "rd_mesh_permutation": (ctypes.c_int, [_vp, _i32p, _i32p]),
     "rd_mesh_sizes": (ctypes.c_int, [_vp, _i32p, _i32p]),
+    "rd_mesh_set_boundary": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint8), ctypes.c_int32, _i32p,
+                                            ctypes.c_double]),
     "rd_state_init": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(Params), ctypes.POINTER(_vp)]),
     "rd_state_set": (ctypes.c_int, [_vp, _dp]),
     "rd_step": (ctypes.c_int, [_vp, _dp]),
@@ -217,6 +219,16 @@ class Mesh:
         _check(rc, "rd_mesh_create")
         self.handle = h
         self.states = []
+        ghost, walls = getattr(mesh, "ghost", None), getattr(mesh, "walls", None)
+        if ghost is not None or walls is not None:
+            self.set_boundary(ghost, walls, getattr(mesh, "alpha", 0.75))
+
+    def set_boundary(self, ghost=None, walls=None, alpha: float = 0.75):
+        """Ghost vertices ([nv] flags) and reflecting walls ([n][2] (triangle, corner)), Sec. 3.5."""
+        g = None if ghost is None else np.ascontiguousarray(ghost, dtype=np.uint8)
+        w = np.zeros((0, 2), np.int32) if walls is None else np.ascontiguousarray(walls, dtype=np.int32)
+        _check(_lib.rd_mesh_set_boundary(self.handle, _ptr(g, ctypes.c_uint8), len(w), _ptr(w, ctypes.c_int32),
+                                         float(alpha)), "rd_mesh_set_boundary")
 
     @property
     def stream(self):

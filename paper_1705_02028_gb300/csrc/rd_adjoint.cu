@@ -360,7 +360,8 @@ int backward(rd_state* s, rd_adjoint_store* A, const double* dLdWf, double* dLdW
 }  // namespace
 
 extern "C" int rd_adjoint_forward(rd_state* s, int32_t n_steps, int32_t ckpt_every, double* dts_out) {
-  if (s && (s->p.scheme > RD_LDA2 || s->p.lumping != RD_LUMP_GLOBAL)) return RD_ENOTSUP;
+  if (s && (s->p.scheme > RD_LDA2 || s->p.lumping != RD_LUMP_GLOBAL || s->m->n_ghost || s->m->n_wall))
+    return RD_ENOTSUP;
   if (!s || n_steps < 1 || ckpt_every < 1) return RD_EINVAL;
   rd_mesh* m = s->m;
   cudaStream_t st = m->stream;
@@ -404,7 +405,8 @@ extern "C" int rd_adjoint_forward(rd_state* s, int32_t n_steps, int32_t ckpt_eve
 }
 
 extern "C" int rd_adjoint_backward(rd_state* s, const double* dL_dW_final, double* dL_dW0) {
-  if (s && (s->p.scheme > RD_LDA2 || s->p.lumping != RD_LUMP_GLOBAL)) return RD_ENOTSUP;
+  if (s && (s->p.scheme > RD_LDA2 || s->p.lumping != RD_LUMP_GLOBAL || s->m->n_ghost || s->m->n_wall))
+    return RD_ENOTSUP;
   if (!s || !dL_dW_final || !dL_dW0 || !s->adj || s->adj->n_steps < 1) return RD_EINVAL;
   rd_adjoint_store* A = s->adj;
   if (s->pi == 0) {
@@ -471,7 +473,8 @@ int branch_masks(rd_state* s, uint64_t* mask1, uint64_t* mask2) {
 }  // namespace
 
 extern "C" int rd_state_branch_masks(rd_state* s, uint64_t* mask1, uint64_t* mask2) {
-  if (s && (s->p.scheme > RD_LDA2 || s->p.lumping != RD_LUMP_GLOBAL)) return RD_ENOTSUP;
+  if (s && (s->p.scheme > RD_LDA2 || s->p.lumping != RD_LUMP_GLOBAL || s->m->n_ghost || s->m->n_wall))
+    return RD_ENOTSUP;
   if (!s) return RD_EINVAL;
   cudaStream_t st = s->m->stream;
   if (!s->adj) {

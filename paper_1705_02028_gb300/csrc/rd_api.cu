@@ -154,6 +154,7 @@ extern "C" void rd_mesh_destroy(rd_mesh* m) {
   dev_free(m->vperm);
   for (int p = 0; p < 2; ++p)
     for (int k = 0; k < 6; ++k) dev_free(m->geo[p][k]);
+  mesh_boundary_free(m);
   if (m->own_stream) cudaStreamDestroy(m->stream);
   delete m;
 }
@@ -260,6 +261,20 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
     if (ev) cudaEventRecord(ev[k], st);
   };
   BlendArgs<T> ba1 = blend_args<T>(s), ba2 = ba1;
+  WallArgs<T> wa1, wa2;  // stage 1 / N1 at the pass's state; stage 2 half at W*, half at W^n
+  GhostArgs<T> ga;       // the final update of the step resets ghost vertices
+  if (m->n_wall > 0) {
+    wa1.ptr = (const int*)m->wptr.p;
+    wa1.other = (const int*)m->wother.p;
+    wa1.geo = (const T*)m->wgeo[s->pi].p;
+    wa1.alpha = (T)m->wall_alpha;
+    wa2 = wa1;
+    wa2.Wn = (const T*)s->W[a].p;
+  }
+  if (m->n_ghost > 0) {
+    ga.of = (const int*)m->ghost_of.p;
+    ga.W = (const T*)s->ghostW.p;
+  }
   unsigned long long* vr0 = (unsigned long long*)s->vr.p;          // |v| range of W^n
   unsigned long long* vr1 = vr0 ? vr0 + 2 : nullptr;              // |v| range of W*
   ba1.vr = vr0;
@@ -287,14 +302,15 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
   mark(2);
   if (s->p.scheme == RD_N1) {
     k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)s->W[a].p, (const T*)s->R1.p, ptr, ent, nullptr, V, gamma,
-                                          (T*)s->W[b].p, (T*)s->Z[b].p, (T*)s->spd[b].p, ctl);
+                                          (T*)s->W[b].p, (T*)s->Z[b].p, (T*)s->spd[b].p, ctl, nullptr, nullptr,
+                                          nullptr, wa1, ga);
     mark(3);
     mark(4);
     mark(5);
   } else {
     if (vr1) k_vr_reset<<<1, 1, 0, st>>>(vr1, ctl, 0);
     k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)s->W[a].p, (const T*)s->R1.p, ptr, ent, nullptr, V, gamma,
-                                          (T*)s->Ws.p, (T*)s->Zs.p, nullptr, ctl, nullptr, nullptr, vr1);
+                                          (T*)s->Ws.p, (T*)s->Zs.p, nullptr, ctl, nullptr, nullptr, vr1, wa1);
     mark(3);
     if (s->p.scheme == RD_LDA2)
       k_tri_stage2<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
@@ -310,7 +326,8 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
     mark(4);
     if (vr0) k_vr_reset<<<1, 1, 0, st>>>(vr0, ctl, 0);
     k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)s->Ws.p, nullptr, ptr, ent, share, V, gamma,
-                                          (T*)s->W[b].p, (T*)s->Z[b].p, (T*)s->spd[b].p, ctl, nullptr, nullptr, vr0);
+                                          (T*)s->W[b].p, (T*)s->Z[b].p, (T*)s->spd[b].p, ctl, nullptr, nullptr, vr0,
+                                          wa2, ga);
     mark(5);
   }
   if (commit) k_commit<<<1, 1, 0, st>>>(ctl);
@@ -320,6 +337,7 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
 }
 
 int launch_step_any(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = true, double fixed_dt = 0.0) {
+  if (s->bc_version != s->m->bc_version) return RD_EINVAL;  // boundary changed: rd_state_set first
   return s->pi == 0 ? launch_step<double>(s, a, ev, commit, fixed_dt) : launch_step<float>(s, a, ev, commit, fixed_dt);
 }
 
@@ -341,6 +359,21 @@ int upload_state(rd_state* s, const double* W, int buf) {
   CU(cudaMemcpyAsync(s->stage.p, W, 4 * (size_t)nv * sizeof(double), cudaMemcpyHostToDevice, st));
   k_permute_in<T><<<nblk(nv, VTX_BLOCK), VTX_BLOCK, 0, st>>>(nv, (const int*)m->vperm.p, (const double*)s->stage.p,
                                                              (T*)s->W[buf].p, ctl);
+  // boundary data for this state: wall geometry in T and the ghosts' initial state
+  if (!s->bc_init || s->bc_version != m->bc_version) {
+    CK(mesh_wall_geometry<T>(m));
+    dev_free(s->ghostW);
+    if (m->n_ghost > 0) CK(dev_alloc(s->ghostW, 4 * (size_t)m->n_ghost * sizeof(T), st));
+    if (s->g2) {  // the captured steps hold the old boundary arrays
+      cudaGraphExecDestroy(s->g2);
+      s->g2 = nullptr;
+    }
+    s->bc_version = m->bc_version;
+    s->bc_init = true;
+  }
+  if (m->n_ghost > 0)
+    k_ghost_capture<T><<<nblk(m->n_ghost, VTX_BLOCK), VTX_BLOCK, 0, st>>>(m->n_ghost, (const int*)m->ghost_ids.p,
+                                                                         (const T*)s->W[buf].p, (T*)s->ghostW.p);
   unsigned long long* vr0 = (unsigned long long*)s->vr.p;
   if (vr0) k_vr_reset<<<1, 1, 0, st>>>(vr0, ctl, 1);
   k_prepare<T><<<nblk(nv, VTX_BLOCK), VTX_BLOCK, 0, st>>>(nv, (const T*)s->W[buf].p, (T)s->p.gamma,
@@ -497,6 +530,7 @@ extern "C" int rd_step(rd_state* s, double* dt_out) {
 
 extern "C" int rd_run(rd_state* s, int32_t n_steps, double t_end, int32_t* steps_done) {
   if (!s || n_steps < 0) return RD_EINVAL;
+  if (s->bc_version != s->m->bc_version) return RD_EINVAL;
   cudaStream_t st = s->m->stream;
   DevCtl c0;
   CK(read_ctl(s, c0));
@@ -711,7 +745,7 @@ extern "C" void rd_state_destroy(rd_state* s) {
     dev_free(s->spd[b]);
   }
   DevBuf* bufs[] = {&s->Ws, &s->Zs, &s->R1, &s->share, &s->rec, &s->cfl, &s->partial, &s->ctl,
-                    &s->cons_partial, &s->cons_out, &s->stage, &s->vr};
+                    &s->cons_partial, &s->cons_out, &s->stage, &s->vr, &s->ghostW};
   for (DevBuf* b : bufs) dev_free(*b);
   adjoint_free(s->adj);
   delete s;

@@ -312,6 +312,8 @@ extern "C" int rd_batch_create(int32_t n_mesh, rd_mesh* const* meshes, const dou
   if (!(p->cfl > 0.0) || !(p->gamma > 1.0) || !(p->eps_fix >= 0.0)) return RD_EINVAL;
   for (int32_t m = 0; m < n_mesh; ++m)
     if (!meshes[m] || meshes[m]->stream != meshes[0]->stream) return RD_EINVAL;
+  for (int32_t m = 0; m < n_mesh; ++m)
+    if (meshes[m]->n_ghost || meshes[m]->n_wall) return RD_ENOTSUP;  // periodic meshes only
   rd_batch* b = new (std::nothrow) rd_batch();
   if (!b) return RD_ENOMEM;
   b->n_mesh = n_mesh;

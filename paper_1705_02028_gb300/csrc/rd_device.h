@@ -55,6 +55,10 @@ namespace rd {
 void adjoint_free(rd_adjoint_store* a);
 // One committed step of a state reading buffer a (fixed_dt > 0 replaces the CFL dt).
 int state_step(rd_state* s, int a, double fixed_dt);
+// Boundary data of a mesh (rd_boundary.cu).
+template <class T>
+int mesh_wall_geometry(rd_mesh* m);
+void mesh_boundary_free(rd_mesh* m);
 int state_read_ctl(const rd_state* s, DevCtl& c);
 }
 
@@ -67,6 +71,17 @@ struct rd_mesh {
   // geometry per precision (0: double, 1: float): nx, ny, hl, area, lmax, V
   rd::DevBuf geo[2][6];
   bool geo_ready[2] = {false, false};
+  // boundary conditions (Sec. 3.5), set by rd_mesh_set_boundary
+  int bc_version = 0;
+  int32_t n_ghost = 0, n_wall = 0;
+  double wall_alpha = 0.75;
+  rd::DevBuf ghost_of;   // [nv] int32: ghost slot of each internal vertex, -1 if none
+  rd::DevBuf ghost_ids;  // [n_ghost] internal vertex ids
+  rd::DevBuf wptr;       // [nv + 1] wall CSR: internal vertex -> wall-edge ends
+  rd::DevBuf wother;     // [2 n_wall] the other vertex of each end's edge
+  rd::DevBuf wgeo[2];    // per precision: [2 n_wall][3] outward unit normal x, y, half length
+  std::vector<double> wgeo_host;
+  bool wgeo_ready[2] = {false, false};
 };
 
 // The state handle: double-buffered vertex state, step scratch and the device
@@ -80,6 +95,9 @@ struct rd_state {
   rd::DevBuf Ws, Zs, R1, share, rec, cfl, partial, ctl, cons_partial, cons_out;
   rd::DevBuf stage;        // [4][nv] double, caller vertex order (host I/O)
   rd::DevBuf vr;           // RD_BX2: |v| max / min bits, slot 0 (W^n) and slot 1 (W*)
+  rd::DevBuf ghostW;       // [n_ghost][4] T: initial state of the ghost vertices
+  int bc_version = 0;      // mesh boundary version the state was set up for
+  bool bc_init = false;
   long long launched = 0;  // host view of the committed step count (parity of the buffers)
   int tri_block = rd::TRI_BLOCK, vtx_block = rd::VTX_BLOCK;  // launch shapes (autotuned)
   cudaGraphExec_t g2 = nullptr;  // two steps (even -> odd -> even)

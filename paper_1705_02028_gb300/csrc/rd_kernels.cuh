@@ -911,6 +911,58 @@ static __global__ void k_vr_reset(unsigned long long* vr, const DevCtl* ctl, int
   }
 }
 
+// Boundary conditions of Sec. 3.5 as seen by the vertex update.
+//   Walls: per internal vertex a CSR of wall-edge ends (the other vertex b, the
+//   edge's outward unit normal and half length hl); the correction residual
+//   hl (alpha f_self + (1 - alpha) f_other) with f = -(rho v_n, rho u v_n,
+//   rho v v_n, rho h v_n) is added to R at the pass's state (Win), or, in
+//   stage 2 (Wn != nullptr), as half of it at W* plus half at W^n.
+//   Ghosts: the final update of a step writes the stored initial state of a
+//   ghost vertex instead of its update.
+template <class T>
+struct WallArgs {
+  const int* ptr = nullptr;
+  const int* other = nullptr;
+  const T* geo = nullptr;
+  const T* Wn = nullptr;
+  T alpha = T(0.75);
+};
+template <class T>
+struct GhostArgs {
+  const int* of = nullptr;
+  const T* W = nullptr;
+};
+
+template <class T>
+RD_HD void wall_flux(const T W[4], T nx, T ny, T gamma, T f[4]) {
+  T rho = W[0];
+  T u = W[1] / rho, v = W[2] / rho;
+  T p = (gamma - T(1)) * (W[3] - T(0.5) * rho * (u * u + v * v));
+  T vn = u * nx + v * ny;
+  f[0] = -rho * vn;
+  f[1] = -W[1] * vn;
+  f[2] = -W[2] * vn;
+  f[3] = -(W[3] + p) * vn;
+}
+
+template <class T>
+__device__ __forceinline__ void wall_add(const WallArgs<T>& wa, const T* __restrict__ Ws, int i, T gamma, T weight,
+                                         T r[4]) {
+  const int e0 = __ldg(wa.ptr + i), e1 = __ldg(wa.ptr + i + 1);
+  for (int e = e0; e < e1; ++e) {
+    const int o = __ldg(wa.other + e);
+    const T nx = __ldg(wa.geo + 3 * (size_t)e), ny = __ldg(wa.geo + 3 * (size_t)e + 1);
+    const T hl = __ldg(wa.geo + 3 * (size_t)e + 2);
+    T ws[4], wo[4], fs[4], fo[4];
+    load_vec4(Ws, i, ws);
+    load_vec4(Ws, o, wo);
+    wall_flux(ws, nx, ny, gamma, fs);
+    wall_flux(wo, nx, ny, gamma, fo);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r[k] += weight * hl * (wa.alpha * fs[k] + (T(1) - wa.alpha) * fo[k]);
+  }
+}
+
 // W_out = W_in - dt/V R; Z_out = Z(W_out); spd_out (nullable) = |v| + c.
 // If R2 != nullptr, W_in is W* and R = R2 gathered here from share (stage 2).
 template <class T>
@@ -920,7 +972,8 @@ __global__ void __launch_bounds__(512) k_update(int nv, const T* __restrict__ Wi
                                                 T* __restrict__ Wout, T* __restrict__ Zout, T* __restrict__ spdout,
                                                 DevCtl* ctl, const double* __restrict__ dtm = nullptr,
                                                 const uint16_t* __restrict__ vmesh = nullptr,
-                                                unsigned long long* __restrict__ vr_out = nullptr) {
+                                                unsigned long long* __restrict__ vr_out = nullptr,
+                                                WallArgs<T> wa = WallArgs<T>(), GhostArgs<T> ga = GhostArgs<T>()) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool act = i < nv && !ctl->stop;
   if (!act && !vr_out) return;
@@ -935,12 +988,24 @@ __global__ void __launch_bounds__(512) k_update(int nv, const T* __restrict__ Wi
   } else {
     load_vec4(R, i, r);
   }
+  if (wa.ptr) {
+    if (wa.Wn) {
+      wall_add(wa, Win, i, gamma, T(0.5), r);
+      wall_add(wa, wa.Wn, i, gamma, T(0.5), r);
+    } else {
+      wall_add(wa, Win, i, gamma, T(1), r);
+    }
+  }
   T dt = dtm ? (T)__ldg(dtm + __ldg(vmesh + i)) : (T)ctl->dt;
   T f = dt / __ldg(V + i);
   T W[4], Z[4], spd;
   load_vec4(Win, i, W);
 #pragma unroll
   for (int k = 0; k < 4; ++k) W[k] = W[k] - f * r[k];
+  if (ga.of) {
+    const int gi = __ldg(ga.of + i);
+    if (gi >= 0) load_vec4(ga.W, gi, W);
+  }
   bool ok = vertex_Z(W, gamma, Z, spd, &q);
   st4(Wout + 4 * (size_t)i, W);
   st4(Zout + 4 * (size_t)i, Z);
@@ -952,6 +1017,16 @@ __global__ void __launch_bounds__(512) k_update(int nv, const T* __restrict__ Wi
   has = ok;
   }
   if (vr_out) vrange_fold(has, (double)q, vr_out);
+}
+
+// Initial state of the ghost vertices: Wg[g] = W[ids[g]].
+template <class T>
+__global__ void k_ghost_capture(int n, const int* __restrict__ ids, const T* __restrict__ W, T* __restrict__ Wg) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  T w[4];
+  load_vec4(W, __ldg(ids + g), w);
+  st4(Wg + 4 * (size_t)g, w);
 }
 
 // Z and |v|+c of a freshly uploaded state.

@@ -41,6 +41,10 @@ class Mesh:
     orig_vertex: np.ndarray  # (nv,) int64: structured id j*Nx+i of each vertex
     Nx: int = 0
     Ny: int = 0
+    # boundary conditions (Sec. 3.5); None on fully periodic meshes
+    ghost: np.ndarray | None = None   # (nv,) uint8: 1 = state held at its initial value
+    walls: np.ndarray | None = None   # (n_wall, 2) int32: (triangle, corner) of the wall edge
+    alpha: float = 0.75               # wall-correction split
 
     @property
     def nv(self) -> int:
@@ -85,25 +89,41 @@ def periodic_grid(Nx: int, Ny: int | None = None, Lx: float = 1.0, Ly: float | N
     shift[0::2], shift[1::2] = s1, s2
     orig = vid.copy()
 
-    if relabel_seed is not None:
-        rng = np.random.default_rng(relabel_seed)
-        vperm = rng.permutation(Nx * Ny)          # new label of old vertex
-        inv = np.empty_like(vperm)
-        inv[vperm] = np.arange(Nx * Ny)
-        xy = xy[inv]
-        orig = orig[inv]
-        tri = vperm[tri]
-        tperm = rng.permutation(tri.shape[0])
-        tri = tri[tperm]
-        shift = shift[tperm]
-        # rotate the corner order of each triangle (keeps orientation)
-        rot = rng.integers(0, 3, size=tri.shape[0])
-        idx = (np.arange(3)[None, :] + rot[:, None]) % 3
-        tri = np.take_along_axis(tri, idx, axis=1)
-        shift = np.take_along_axis(shift, idx[:, :, None], axis=1)
-    return Mesh(xy=np.ascontiguousarray(xy), tri=np.ascontiguousarray(tri.astype(np.int32)),
+    mesh = Mesh(xy=np.ascontiguousarray(xy), tri=np.ascontiguousarray(tri.astype(np.int32)),
                 shift=np.ascontiguousarray(shift), Lx=float(Lx), Ly=float(Ly),
                 orig_vertex=orig, Nx=Nx, Ny=Ny)
+    return relabel(mesh, relabel_seed) if relabel_seed is not None else mesh
+
+
+def relabel(mesh: Mesh, seed: int) -> Mesh:
+    """Seeded random permutation of vertex and triangle labels and a rotation of
+    each triangle's corner order (orientation kept); boundary data follow."""
+    rng = np.random.default_rng(seed)
+    n = mesh.nv
+    vperm = rng.permutation(n)          # new label of old vertex
+    inv = np.empty_like(vperm)
+    inv[vperm] = np.arange(n)
+    xy = mesh.xy[inv]
+    orig = mesh.orig_vertex[inv]
+    tri = vperm[mesh.tri.astype(np.int64)]
+    tperm = rng.permutation(tri.shape[0])   # old triangle of each new slot
+    tri = tri[tperm]
+    shift = mesh.shift[tperm]
+    rot = rng.integers(0, 3, size=tri.shape[0])
+    idx = (np.arange(3)[None, :] + rot[:, None]) % 3
+    tri = np.take_along_axis(tri, idx, axis=1)
+    shift = np.take_along_axis(shift, idx[:, :, None], axis=1)
+    ghost = None if mesh.ghost is None else np.ascontiguousarray(mesh.ghost[inv])
+    walls = None
+    if mesh.walls is not None:
+        tnew = np.empty_like(tperm)
+        tnew[tperm] = np.arange(tperm.size)
+        t_new = tnew[mesh.walls[:, 0]]
+        c_new = (mesh.walls[:, 1] - rot[t_new]) % 3     # new corner k holds old corner (k + rot) % 3
+        walls = np.ascontiguousarray(np.stack([t_new, c_new], axis=1).astype(np.int32))
+    return Mesh(xy=np.ascontiguousarray(xy), tri=np.ascontiguousarray(tri.astype(np.int32)),
+                shift=np.ascontiguousarray(shift), Lx=mesh.Lx, Ly=mesh.Ly, orig_vertex=orig,
+                Nx=mesh.Nx, Ny=mesh.Ny, ghost=ghost, walls=walls, alpha=mesh.alpha)
 
 
 def _incircle(ax, ay, bx, by, cx, cy, dx, dy):
@@ -188,25 +208,72 @@ def jittered_grid(Nx: int, Ny: int | None = None, Lx: float = 1.0, Ly: float | N
              - (P[:, 2, 0] - P[:, 0, 0]) * (P[:, 1, 1] - P[:, 0, 1]))
     if not np.all(area2 > 0.0):
         raise AssertionError("jittered_grid produced a non-positive triangle")
-    orig = vid.copy()
-    if relabel_seed is not None:
-        rng = np.random.default_rng(relabel_seed)
-        vperm = rng.permutation(n)
-        inv = np.empty_like(vperm)
-        inv[vperm] = np.arange(n)
-        xy = xy[inv]
-        orig = orig[inv]
-        tri = vperm[tri]
-        tperm = rng.permutation(tri.shape[0])
-        tri = tri[tperm]
-        shift = shift[tperm]
-        rot = rng.integers(0, 3, size=tri.shape[0])
-        idx = (np.arange(3)[None, :] + rot[:, None]) % 3
-        tri = np.take_along_axis(tri, idx, axis=1)
-        shift = np.take_along_axis(shift, idx[:, :, None], axis=1)
-    return Mesh(xy=np.ascontiguousarray(xy), tri=np.ascontiguousarray(tri.astype(np.int32)),
+    mesh = Mesh(xy=np.ascontiguousarray(xy), tri=np.ascontiguousarray(tri.astype(np.int32)),
                 shift=np.ascontiguousarray(shift.astype(np.int8)), Lx=float(Lx), Ly=float(Ly),
-                orig_vertex=orig, Nx=Nx, Ny=Ny)
+                orig_vertex=vid.copy(), Nx=Nx, Ny=Ny)
+    return relabel(mesh, relabel_seed) if relabel_seed is not None else mesh
+
+
+def bounded_grid(Nx: int, Ny: int | None = None, Lx: float = 1.0, Ly: float | None = None,
+                 periodic_x: bool = False, periodic_y: bool = False, bc_x: str = "wall", bc_y: str = "wall",
+                 relabel_seed: int | None = None) -> Mesh:
+    """Structured triangulation of [0, Lx] x [0, Ly] with Nx x Ny cells (split along
+    the diagonal a-c as in ``periodic_grid``), periodic in the directions asked for
+    and bounded in the others.  A bounded side is a reflecting wall ("wall": its
+    edges are listed as (triangle, corner) pairs, Sec. 3.5) or a non-reflecting /
+    inflow side ("ghost": its vertices are held at their initial state)."""
+    if Ny is None:
+        Ny = Nx
+    if Ly is None:
+        Ly = Lx * Ny / Nx
+    for bc in (bc_x, bc_y):
+        if bc not in ("wall", "ghost"):
+            raise ValueError("bc must be 'wall' or 'ghost'")
+    nxv = Nx if periodic_x else Nx + 1
+    nyv = Ny if periodic_y else Ny + 1
+    hx, hy = Lx / Nx, Ly / Ny
+    jj, ii = np.meshgrid(np.arange(nyv), np.arange(nxv), indexing="ij")
+    xy = np.stack([ii.ravel() * hx, jj.ravel() * hy], axis=1).astype(np.float64)
+    ci, cj = np.meshgrid(np.arange(Nx), np.arange(Ny), indexing="xy")
+    ci, cj = ci.ravel(), cj.ravel()
+
+    def vid(i, j):
+        return (j % nyv) * nxv + (i % nxv)
+
+    def sh(i, j):
+        sx = (i // nxv) if periodic_x else np.zeros_like(i)
+        sy = (j // nyv) if periodic_y else np.zeros_like(j)
+        return np.stack([sx, sy], axis=-1)
+
+    A, B, C, D = (ci, cj), (ci + 1, cj), (ci + 1, cj + 1), (ci, cj + 1)
+    n = Nx * Ny
+    tri = np.empty((2 * n, 3), dtype=np.int64)
+    shift = np.empty((2 * n, 3, 2), dtype=np.int64)
+    for slot, corners in ((0, (A, B, C)), (1, (A, C, D))):
+        for k, (i, j) in enumerate(corners):
+            tri[slot::2, k] = vid(i, j)
+            shift[slot::2, k] = sh(i, j)
+    cell = cj * Nx + ci
+    ghost = np.zeros(nxv * nyv, dtype=np.uint8)
+    walls = []
+    if not periodic_y:
+        if bc_y == "ghost":
+            ghost[(jj.ravel() == 0) | (jj.ravel() == Ny)] = 1
+        else:
+            bot, top = cell[cj == 0], cell[cj == Ny - 1]
+            walls += [np.stack([2 * bot, np.full_like(bot, 2)], 1), np.stack([2 * top + 1, np.zeros_like(top)], 1)]
+    if not periodic_x:
+        if bc_x == "ghost":
+            ghost[(ii.ravel() == 0) | (ii.ravel() == Nx)] = 1
+        else:
+            left, right = cell[ci == 0], cell[ci == Nx - 1]
+            walls += [np.stack([2 * left + 1, np.ones_like(left)], 1), np.stack([2 * right, np.zeros_like(right)], 1)]
+    mesh = Mesh(xy=np.ascontiguousarray(xy), tri=np.ascontiguousarray(tri.astype(np.int32)),
+                shift=np.ascontiguousarray(shift.astype(np.int8)), Lx=float(Lx), Ly=float(Ly),
+                orig_vertex=(jj * nxv + ii).ravel().astype(np.int64), Nx=nxv, Ny=nyv,
+                ghost=ghost if ghost.any() else None,
+                walls=np.ascontiguousarray(np.concatenate(walls).astype(np.int32)) if walls else None)
+    return relabel(mesh, relabel_seed) if relabel_seed is not None else mesh
 
 
 # ---------------------------------------------------------------------------

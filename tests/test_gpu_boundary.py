@@ -1,0 +1,122 @@
+"""Boundary conditions (Sec. 3.5) on the GPU path vs the oracle: reflecting
+walls (weak correction, alpha = 0.75) and ghost vertices, on closed tubes,
+channels and boxes, every reorder; 1e-12 relative max-norm parity against the
+oracle's long-double instantiation, plus the exact reflected-shock pin in FP64
+and FP32 and the API's rules for changing a boundary."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1705_02028_gb300 import inputs
+from tests._gpu import rel_max_err, require_gpu
+from tests.test_oracle_boundary import reflection, tube
+
+pytestmark = pytest.mark.gpu
+NTH = max(1, min(16, os.cpu_count() or 1))
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def rd():
+    torch = require_gpu()
+    from paper_1705_02028_gb300 import binding
+    return torch, binding
+
+
+def _parity(binding, mesh, W0, scheme, steps, reorder="morton"):
+    m = binding.Mesh(mesh, reorder=reorder)
+    s = binding.State(m, W0, scheme=scheme)
+    assert s.run(steps) == steps
+    Wld, dto = oracle.run(mesh, W0, scheme, nsteps=steps, nthreads=NTH, long_double=True)
+    Wd, _ = oracle.run(mesh, W0, scheme, nsteps=steps, nthreads=NTH)
+    err, floor = rel_max_err(s.get(), Wld), rel_max_err(Wd, Wld)
+    t, _ = s.time()
+    assert t == pytest.approx(dto.sum(), rel=1e-13)
+    return err, floor
+
+
+@pytest.mark.parametrize("reorder", ["none", "morton", "rcm"])
+@pytest.mark.parametrize("scheme", ["N1", "B2"])
+def test_closed_tube(rd, reorder, scheme):
+    _, binding = rd
+    mesh, W0 = tube(100, "wall", relabel=5)
+    steps = 100 if scheme == "N1" else 20      # B2 amplifies round-off at the resting interface
+    err, floor = _parity(binding, mesh, W0, scheme, steps, reorder)
+    print(f"closed tube {scheme} {reorder}: {err:.2e} (oracle floor {floor:.2e})")
+    assert err < TOL
+
+
+@pytest.mark.parametrize("scheme", ["B2", "LDA2", "BX2", "BMIN2_SL"])
+def test_channel_and_ghost_box(rd, scheme):
+    _, binding = rd
+    chan = inputs.bounded_grid(40, 24, Ly=0.6, periodic_x=True, bc_y="wall", relabel_seed=2)
+    W0 = inputs.khi_state(chan)
+    err, floor = _parity(binding, chan, W0, scheme, 100)
+    print(f"KHI channel {scheme}: {err:.2e} (oracle floor {floor:.2e})")
+    assert err < TOL
+    box = inputs.bounded_grid(36, 30, bc_x="ghost", bc_y="wall", relabel_seed=3)
+    W0 = inputs.vortex_state(box, u0=0.5, v0=0.0)
+    err, floor = _parity(binding, box, W0, scheme, 100)
+    print(f"vortex, ghost x / wall y {scheme}: {err:.2e} (oracle floor {floor:.2e})")
+    assert err < TOL
+
+
+@pytest.mark.parametrize("precision,tol_cells", [("fp64", 0.5), ("fp32", 1.0)])
+def test_reflected_shock_position(rd, precision, tol_cells):
+    _, binding = rd
+    ex = reflection()
+    Nx, T = 400, 0.34
+    mesh, W0 = tube(Nx, "wall")
+    m = binding.Mesh(mesh)
+    s = binding.State(m, W0, scheme="B2", precision=precision)
+    s.run(100000, t_end=T)
+    t, _ = s.time()
+    assert t == pytest.approx(T, rel=1e-12)
+    W = s.get()
+    x, y = mesh.xy[:, 0], mesh.xy[:, 1]
+    row = y == y.min()
+    o = np.argsort(x[row])
+    xs, rho = x[row][o], W[0][row][o]
+    xr = 1 + ex["Wr"] * (T - ex["t1"])
+    half = 0.5 * (ex["r2"] + ex["r5"])
+    win = np.where((xs > 0.88) & (xs < 0.995))[0]
+    k = [i for i in win[:-1] if (rho[i] - half) * (rho[i + 1] - half) <= 0][-1]
+    x_num = xs[k] + (half - rho[k]) * (xs[k + 1] - xs[k]) / (rho[k + 1] - rho[k])
+    print(f"{precision}: reflected shock at {x_num:.5f}, exact {xr:.5f}")
+    assert abs(x_num - xr) < tol_cells / Nx
+    assert rho[xs > xr + 0.01].mean() == pytest.approx(ex["r5"], rel=0.01)
+
+
+def test_boundary_changes_and_limits(rd):
+    torch, binding = rd
+    mesh, W0 = tube(30, "ghost", relabel=1)
+    m = binding.Mesh(mesh)
+    s = binding.State(m, W0, scheme="B2")
+    s.run(5)
+    # a new boundary invalidates the state until it gets a new initial state
+    walls = inputs.bounded_grid(30, 4, Lx=1.0, Ly=4.0 / 30, periodic_y=True, bc_x="wall")
+    assert walls.nt == mesh.nt
+    m.set_boundary(None, inputs.relabel(walls, 1).walls)
+    with pytest.raises(binding.RDError) as e:
+        s.run(1)
+    assert e.value.status == binding.RD_EINVAL
+    s.set(W0)
+    s.run(10)
+    ref_mesh = inputs.relabel(walls, 1)
+    Wo, _ = oracle.run(ref_mesh, W0, "B2", nsteps=10, long_double=True)
+    assert rel_max_err(s.get(), Wo) < TOL
+    # an interior edge is not a wall
+    bad = np.array([[0, 0]], np.int32)
+    tri_interior = next(t for t in range(mesh.nt) if not np.any((ref_mesh.walls[:, 0] == t)))
+    bad[0, 0] = tri_interior
+    with pytest.raises(binding.RDError) as e:
+        m.set_boundary(None, bad)
+    assert e.value.status == binding.RD_EINVAL
+    with pytest.raises(binding.RDError) as e:
+        binding.Batch([m], [W0])
+    assert e.value.status == binding.RD_ENOTSUP
+    with pytest.raises(binding.RDError) as e:
+        s.adjoint_forward(3)
+    assert e.value.status == binding.RD_ENOTSUP

@@ -1,0 +1,139 @@
+"""Boundary conditions of Sec. 3.5 in the oracle, pinned by exact solutions.
+
+* Reflecting wall (weak correction flux, alpha = 0.75): Sod's shock reflects
+  off the closed end of the tube; the reflected shock's position and the state
+  it leaves behind (at rest) follow from the Rankine-Hugoniot relations and the
+  exact Riemann solver (the symmetric problem between the post-shock state and
+  its mirror image), independently of the scheme.
+* Ghost (non-reflecting) boundary: with the tube's ends held at the initial
+  states, the shock leaves the domain and the interior keeps converging to the
+  open-domain Riemann solution, while a wall sends the reflection back.
+* Uniform states and the conservation of the wall correction's split.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import exact
+from paper_1705_02028_gb300 import inputs
+
+G = 1.4
+MU = (G - 1) / (G + 1)
+
+
+def tube(Nx, bc, relabel=None):
+    m = inputs.bounded_grid(Nx, 4, Lx=1.0, Ly=4.0 / Nx, periodic_y=True, bc_x=bc, relabel_seed=relabel)
+    left = m.xy[:, 0] < 0.5
+    W0 = inputs.conserved(np.where(left, 1.0, 0.125), 0.0, 0.0, np.where(left, 1.0, 0.1))
+    return m, W0
+
+
+def advance(m, W0, T, scheme, nthreads=4):
+    n = int(np.ceil(T / oracle.time_step(m, W0)))
+    W, _ = oracle.run(m, W0, scheme, nsteps=n, dt_fixed=np.full(n, T / n), nthreads=nthreads)
+    return W
+
+
+def reflection():
+    """Exact state behind Sod's shock (2), its speed, and the reflected state (5)."""
+    p2, u2 = exact.star_state((1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
+    r2 = 0.125 * (p2 / 0.1 + MU) / (MU * p2 / 0.1 + 1)
+    S = np.sqrt(G * 0.1 / 0.125) * np.sqrt((G + 1) / (2 * G) * p2 / 0.1 + (G - 1) / (2 * G))
+    p5, u5 = exact.star_state((r2, u2, p2), (r2, -u2, p2))       # wall = mirror image
+    r5 = r2 * (p5 / p2 + MU) / (MU * p5 / p2 + 1)
+    Wr = u2 - np.sqrt(G * p2 / r2) * np.sqrt((G + 1) / (2 * G) * p5 / p2 + (G - 1) / (2 * G))
+    return dict(r2=r2, u2=u2, p2=p2, S=S, t1=0.5 / S, p5=p5, u5=u5, r5=r5, Wr=Wr)
+
+
+def test_bounded_grid_walls_are_boundary_edges():
+    m = inputs.bounded_grid(7, 5, periodic_x=True, bc_y="wall", relabel_seed=2)
+    P = m.xy[m.tri] + m.shift * np.array([m.Lx, m.Ly])
+    keys = {}
+    for t in range(m.nt):
+        for c in range(3):
+            a, b = P[t, (c + 1) % 3], P[t, (c + 2) % 3]
+            k = tuple(np.round(np.concatenate([np.minimum(a, b), np.maximum(a, b)]), 12))
+            keys[k] = keys.get(k, 0) + 1
+    for t, c in m.walls:
+        a, b = P[t, (c + 1) % 3], P[t, (c + 2) % 3]
+        assert keys[tuple(np.round(np.concatenate([np.minimum(a, b), np.maximum(a, b)]), 12))] == 1
+        assert abs(a[1] - b[1]) < 1e-15                          # on y = 0 or y = Ly
+        assert min(abs(a[1]), abs(a[1] - m.Ly)) < 1e-12
+    assert len(m.walls) == 2 * 7
+    g = oracle.geometry(m)
+    assert g["V"].sum() == pytest.approx(m.Lx * m.Ly, rel=1e-13)
+
+
+@pytest.mark.parametrize("scheme", ["N1", "B2", "LDA2", "BMIN2_SL"])
+def test_uniform_states_are_kept(scheme):
+    box = inputs.bounded_grid(9, 8, bc_x="wall", bc_y="wall", relabel_seed=1)
+    W0 = inputs.uniform_state(box, rho=1.2, p=0.9)
+    W, _ = oracle.run(box, W0, scheme, nsteps=30)
+    assert np.abs(W - W0).max() < 1e-14                          # at rest in a closed box
+    chan = inputs.bounded_grid(9, 8, periodic_x=True, bc_y="wall", relabel_seed=3)
+    W0 = inputs.uniform_state(chan, rho=1.1, u=1.3, p=0.8)
+    W, _ = oracle.run(chan, W0, scheme, nsteps=30)
+    assert np.abs(W - W0).max() < 1e-13                          # flow along the walls
+    gbox = inputs.bounded_grid(9, 8, bc_x="ghost", bc_y="ghost", relabel_seed=4)
+    W0 = inputs.uniform_state(gbox, rho=0.9, u=0.4, v=-0.7, p=1.1)
+    W, _ = oracle.run(gbox, W0, scheme, nsteps=30)
+    assert np.abs(W - W0).max() < 1e-13                          # in- and outflow through ghosts
+
+
+@pytest.mark.parametrize("scheme,tol_cells", [("B2", 0.5), ("N1", 1.0)])
+def test_shock_reflects_off_wall(scheme, tol_cells):
+    ex = reflection()
+    Nx, T = 200, 0.34
+    m, W0 = tube(Nx, "wall", relabel=5)
+    W = advance(m, W0, T, scheme)
+    x, y = m.xy[:, 0], m.xy[:, 1]
+    row = y == y.min()
+    o = np.argsort(x[row])
+    xs, rho = x[row][o], W[0][row][o]
+    u = (W[1] / W[0])[row][o]
+    p = ((G - 1) * (W[3] - 0.5 * (W[1] ** 2 + W[2] ** 2) / W[0]))[row][o]
+    xr = 1 + ex["Wr"] * (T - ex["t1"])                            # reflected shock position
+    half = 0.5 * (ex["r2"] + ex["r5"])
+    win = np.where((xs > 0.88) & (xs < 0.995))[0]
+    k = [i for i in win[:-1] if (rho[i] - half) * (rho[i + 1] - half) <= 0][-1]
+    x_num = xs[k] + (half - rho[k]) * (xs[k + 1] - xs[k]) / (rho[k + 1] - rho[k])
+    behind = xs > xr + 0.02
+    print(f"{scheme}: reflected shock {x_num:.4f} (exact {xr:.4f}), rho5 {rho[behind].mean():.4f} "
+          f"(exact {ex['r5']:.4f}), p5 {p[behind].mean():.4f} (exact {ex['p5']:.4f})")
+    assert abs(x_num - xr) < tol_cells / Nx
+    assert rho[behind].mean() == pytest.approx(ex["r5"], rel=0.01)
+    assert p[behind].mean() == pytest.approx(ex["p5"], rel=0.015)
+    assert np.abs(u[xs >= 0.97]).max() < 5e-3 * ex["u2"]          # brought to rest by the wall
+    c0, c1 = oracle.conserved(m, W0), oracle.conserved(m, W)
+    assert abs(c1[0] - c0[0]) < 1e-8 * c0[0]                       # a closed tube keeps its mass
+
+
+def test_ghost_boundary_lets_the_shock_leave():
+    T = 0.35                                                      # the shock left x = 1 at t = 0.285
+    err = {}
+    for Nx in (100, 200):
+        for bc in ("ghost", "wall"):
+            m, W0 = tube(Nx, bc)
+            W = advance(m, W0, T, "B2")
+            x, y = m.xy[:, 0], m.xy[:, 1]
+            sel = (y == y.min()) & (x <= 0.98)
+            ref = exact.riemann_exact((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), (x[sel] - 0.5) / T)[0]
+            err[(Nx, bc)] = exact.l1_error(oracle.geometry(m)["V"][sel], W[0][sel], ref)
+    print(err)
+    assert err[(200, "ghost")] < 0.6 * err[(100, "ghost")]        # converges to the open-domain solution
+    assert err[(200, "ghost")] < 0.4 * err[(200, "wall")]         # the wall reflects the shock
+
+
+def test_wall_split_conserves_the_correction():
+    """Phi^c_a + Phi^c_b = |e|/2 (f_a + f_b) whatever alpha is: one N1 step with
+    alpha = 0.75 and alpha = 0.5 changes sum_i V_i W_i identically."""
+    m = inputs.bounded_grid(12, 10, bc_x="wall", bc_y="wall", relabel_seed=6)
+    W0 = inputs.vortex_state(m, u0=0.3, v0=-0.2)
+    dt = np.array([oracle.time_step(m, W0)])
+    out = {}
+    for alpha in (0.75, 0.5):
+        m.alpha = alpha
+        W, _ = oracle.run(m, W0, "N1", nsteps=1, dt_fixed=dt)
+        out[alpha] = (W, oracle.conserved(m, W))
+    assert np.allclose(out[0.75][1], out[0.5][1], rtol=1e-14, atol=1e-16)
+    assert np.abs(out[0.75][0] - out[0.5][0]).max() > 1e-9        # but the split itself differs
