@@ -42,6 +42,8 @@ WORKLOADS = {
     # unstructured: jittered vertices, Delaunay diagonals, labels scrambled (seed 6)
     "khi4096j_B2": (4096, "khi", "B2", "jittered"),
     "khi2048j_B2": (2048, "khi", "B2", "jittered"),
+    # bounded: periodic in x, reflecting walls at y = 0 and y = 1 (Sec. 3.5)
+    "khi4096w_B2": (4096, "khi", "B2", "channel"),
 }
 # algorithmic HBM bytes of one triangle-update (whole step) for the two-stage
 # scheme: W^n, xy, V read and R1, sigma written in the first pass; W^n, R1, V,
@@ -134,6 +136,8 @@ def build_inputs(workload):
     side, state, scheme, kind = WORKLOADS[workload]
     if kind == "jittered":
         mesh = inputs.jittered_grid(side, relabel_seed=6)
+    elif kind == "channel":
+        mesh = inputs.bounded_grid(side, side, periodic_x=True, bc_y="wall")
     else:
         mesh = inputs.periodic_grid(side)
     W0 = {"khi": inputs.khi_state, "sod": inputs.sod_like_state, "vortex": inputs.vortex_state}[state](mesh)
@@ -470,6 +474,8 @@ def sample_mesh(workload):
     from paper_1705_02028_gb300 import inputs
     if WORKLOADS[workload][3] == "jittered":
         return inputs.jittered_grid(1024, relabel_seed=6)
+    if WORKLOADS[workload][3] == "channel":
+        return inputs.bounded_grid(1024, 1024, periodic_x=True, bc_y="wall")
     return inputs.periodic_grid(1024)
 
 

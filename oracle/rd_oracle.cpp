@@ -47,10 +47,10 @@
 //        sqrt(2 |T|), L = max(Lx, Ly), |v| extremes over all vertices of the
 //        state being distributed (W^n in stage 1, W* in stage 2); s = 0 when
 //        |v|_max = |v|_min.  On the unit box theta = s^2 h as printed.
-//   (R11) Ghost vertices are reset to their initial state at the start of
+//   (R12) Ghost vertices are reset to their initial state at the start of
 //        every step (the value entering the step); W* of a ghost vertex is
 //        the ordinary stage-1 update.  "Initial" = the state passed to run().
-//   (R12) The wall correction residual Phi^c is a spatial residual: it enters
+//   (R13) The wall correction residual Phi^c is a spatial residual: it enters
 //        stage 1 (and N1) at W^n and stage 2 as (Phi^c(W^n) + Phi^c(W*)) / 2,
 //        like phi^T.  The wall's outward unit normal is minus the inward
 //        normal of the edge in its triangle; h = (e + p) / rho.
@@ -779,7 +779,7 @@ int step(const Mesh<S>& m, std::vector<S>& W, S gamma, S cfl, S eps, int scheme,
   e = stage2_shares(m, W, Ws, dt, gamma, eps, scheme, share, nthreads);
   if (e) return e;
   if (!m.wall.empty()) {
-    // (Phi^c(W^n) + Phi^c(W*)) / 2   (R12)
+    // (Phi^c(W^n) + Phi^c(W*)) / 2   (R13)
     wall_2.assign(W.size(), S(0));
     e = wall_residual(m, W, gamma, S(0.5), wall_2);
     if (e) return e;
@@ -838,7 +838,7 @@ int run(int32_t nv, const double* xy, int32_t nt, const int32_t* tri, const int8
   soa_to_aos(W_soa, nv, W);
   const std::vector<S> W0 = W;
   for (int32_t s = 0; s < nsteps; ++s) {
-    // ghost vertices enter every step at their initial state (R11)
+    // ghost vertices enter every step at their initial state (R12)
     if (!m.ghost.empty())
       for (int32_t i = 0; i < nv; ++i)
         if (m.ghost[i])

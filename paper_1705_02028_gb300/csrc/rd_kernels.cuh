@@ -95,6 +95,13 @@ RD_HD double rcp(double x) {
   return 1.0 / x;
 }
 
+// dt of the current step in the kernel's precision (the FP32 kernels read the
+// float copy instead of converting the double on the FP64 pipe).
+template <class T>
+__device__ __forceinline__ T ctl_dt(const DevCtl* ctl) {
+  return sizeof(T) == 8 ? (T)ctl->dt : (T)ctl->dtf;
+}
+
 // Blends of N and LDA (Sec. 3.3.3): diagonal Theta (B), every diagonal entry
 // max_k / min_k Theta_kk (Bmax / Bmin), or the scalar shock-sensor theta (Bx).
 enum : int { BLEND_B = 0, BLEND_MAX = 1, BLEND_MIN = 2, BLEND_X = 3 };
@@ -467,6 +474,18 @@ RD_HD void lda_apply(const TriLin<T>& L, const T x[4], T out[3][4]) {
 template <class T>
 RD_HD void blend(const T tot[4], const T N[3][4], const T lda[3][4], T out[3][4], int mode = BLEND_B,
                  T theta_x = T(0)) {
+  if (mode == BLEND_B) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      T num = fabs(tot[k]);
+      T den = fabs(N[0][k]) + fabs(N[1][k]) + fabs(N[2][k]);
+      den = mag_less(num, den) ? den : num;
+      T th = mag_positive(den) ? num * rcp(den) : T(0);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) out[i][k] = th * N[i][k] + (T(1) - th) * lda[i][k];
+    }
+    return;
+  }
   T th[4];
   if (mode == BLEND_X) {
 #pragma unroll
@@ -845,6 +864,7 @@ __global__ void __launch_bounds__(BLOCK) k_gather_cfl(int nv, const int* __restr
         if (!(rem > 0.0)) ctl->stop = 1;  // t_end reached: the rest of this step is a no-op
       }
       ctl->dt = (double)(T)dt;
+      ctl->dtf = (float)dt;
       ctl->ticket = 0u;
     }
   }
@@ -996,7 +1016,7 @@ __global__ void __launch_bounds__(512) k_update(int nv, const T* __restrict__ Wi
       wall_add(wa, Win, i, gamma, T(1), r);
     }
   }
-  T dt = dtm ? (T)__ldg(dtm + __ldg(vmesh + i)) : (T)ctl->dt;
+  T dt = dtm ? (T)__ldg(dtm + __ldg(vmesh + i)) : ctl_dt<T>(ctl);
   T f = dt / __ldg(V + i);
   T W[4], Z[4], spd;
   load_vec4(Win, i, W);
@@ -1075,7 +1095,7 @@ __global__ void __launch_bounds__(256, (TriOcc<T, 2>::value)) k_tri_stage2(int n
 #pragma unroll
   for (int k = 0; k < 4; ++k) ld4(rp + 4 * k, r + 4 * k);
   T out[3][4];
-  T dt = dtm ? (T)__ldg(dtm + __ldg(tmesh + t)) : (T)ctl->dt;
+  T dt = dtm ? (T)__ldg(dtm + __ldg(tmesh + t)) : ctl_dt<T>(ctl);
   const T area = __ldg(g.area + t);
   const int mode = SCHEME == RD_BMAX2 ? ba.mode : BLEND_B;
   const int sl = (SCHEME == RD_BMAX2 || SCHEME == RD_LDA2) ? ba.sl : 0;
