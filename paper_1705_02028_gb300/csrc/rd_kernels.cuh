@@ -474,18 +474,6 @@ RD_HD void lda_apply(const TriLin<T>& L, const T x[4], T out[3][4]) {
 template <class T>
 RD_HD void blend(const T tot[4], const T N[3][4], const T lda[3][4], T out[3][4], int mode = BLEND_B,
                  T theta_x = T(0)) {
-  if (mode == BLEND_B) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      T num = fabs(tot[k]);
-      T den = fabs(N[0][k]) + fabs(N[1][k]) + fabs(N[2][k]);
-      den = mag_less(num, den) ? den : num;
-      T th = mag_positive(den) ? num * rcp(den) : T(0);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) out[i][k] = th * N[i][k] + (T(1) - th) * lda[i][k];
-    }
-    return;
-  }
   T th[4];
   if (mode == BLEND_X) {
 #pragma unroll
@@ -895,8 +883,41 @@ RD_HD bool vertex_Z(const T W[4], T gamma, T Z[4], T& spd, T* vmag = nullptr) {
 // integer order of non-negative doubles is their numeric order), one pair of
 // atomics per block.  Every thread of the block calls it (blockDim a multiple
 // of 32, at most 512); has = false contributes nothing.
-__device__ __forceinline__ void vrange_fold(bool has, double q, unsigned long long* vr) {
-  unsigned long long hi = has ? (unsigned long long)__double_as_longlong(q) : 0ull;
+__device__ __forceinline__ unsigned long long speed_bits(double q) { return (unsigned long long)__double_as_longlong(q); }
+__device__ __forceinline__ unsigned long long speed_bits(float q) {
+  // float -> double is exact; done here, once per block, off the per-thread path
+  return (unsigned long long)__double_as_longlong((double)q);
+}
+template <class T>
+__device__ __forceinline__ void vrange_fold(bool has, T q, unsigned long long* vr) {
+  if (sizeof(T) == 4) {
+    // reduce the 32-bit patterns (same order argument), widen only the block's result
+    unsigned int h32 = has ? __float_as_uint((float)q) : 0u;
+    unsigned int l32 = has ? h32 : 0x7f800000u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned int a = __shfl_xor_sync(0xffffffffu, h32, o), b = __shfl_xor_sync(0xffffffffu, l32, o);
+      h32 = a > h32 ? a : h32;
+      l32 = b < l32 ? b : l32;
+    }
+    __shared__ unsigned int s32[2][16];
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+      s32[0][w] = h32;
+      s32[1][w] = l32;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int j = 1; j < nw; ++j) {
+        h32 = s32[0][j] > h32 ? s32[0][j] : h32;
+        l32 = s32[1][j] < l32 ? s32[1][j] : l32;
+      }
+      atomicMax(vr, speed_bits(__uint_as_float(h32)));
+      atomicMin(vr + 1, speed_bits(__uint_as_float(l32)));
+    }
+    return;
+  }
+  unsigned long long hi = has ? speed_bits(q) : 0ull;
   unsigned long long lo = has ? hi : 0x7ff0000000000000ull;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -1036,7 +1057,7 @@ __global__ void __launch_bounds__(512) k_update(int nv, const T* __restrict__ Wi
   }
   has = ok;
   }
-  if (vr_out) vrange_fold(has, (double)q, vr_out);
+  if (vr_out) vrange_fold(has, q, vr_out);
 }
 
 // Initial state of the ghost vertices: Wg[g] = W[ids[g]].
@@ -1066,7 +1087,7 @@ __global__ void k_prepare(int nv, const T* __restrict__ W, T gamma, T* __restric
     if (!ok) atomicOr(&ctl->status, ST_NONPHYS_VERTEX);
     has = ok;
   }
-  if (vr_out) vrange_fold(has, (double)q, vr_out);
+  if (vr_out) vrange_fold(has, q, vr_out);
 }
 
 // ---------------------------------------------------------------------------
