@@ -97,6 +97,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form companion measurement")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-rollout companion measurement")
+    ap.add_argument("--no-meshgen", action="store_true", help="skip the mesh-generation companion measurement")
     return ap.parse_args()
 
 
@@ -382,6 +383,8 @@ def ours(args, ws, rank, local):
         line["batched"] = bt
     if not args.no_adjoint and args.precision == "fp64":
         line["adjoint"] = adjoint_measure(args, ws)
+    if not args.no_meshgen:
+        line["meshgen"] = meshgen_measure(args)
 
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
@@ -422,6 +425,25 @@ def batched(args, ws, steps):
             "sides": [int(mm.Nx) for mm, _, _ in work], "dt_min": float(dts.min()), "dt_max": float(dts.max()),
             "launch_shapes": {"tri_block": shapes[0], "vtx_block": shapes[1], "source": "rd_batch_autotune"}
             if shapes else None, "per_kernel_ms": pk, "precision": args.precision}
+
+
+def meshgen_measure(args, R=7.3e-4):
+    """Delaunay refinement of the periodic unit square to circumradius <= R and
+    beta <= sqrt 2 on the GPU (about 1.3 million vertices for R = 7.3e-4, the
+    size of the paper's mesh-generation test), timed with CUDA events."""
+    import torch
+    from paper_1705_02028_gb300 import binding
+    binding.meshgen(0.05)          # warm-up: module load, first launches
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mesh, info = binding.meshgen(R)
+    wall = time.perf_counter() - t0
+    ms = info["ms"]
+    return {"vertices": mesh.nv, "triangles": mesh.nt, "max_circumradius": R, "quality_bound": 2.0 ** 0.5,
+            "status": info["status"], "rounds": info["rounds"], "flips": info["flips"],
+            "device_ms": ms["total"], "wall_s": wall, "vertices_per_s": mesh.nv / (ms["total"] * 1e-3),
+            "phase_ms": {k: v for k, v in ms.items() if k != "total"},
+            "note": "device time of rd_meshgen_run (CUDA events around the whole run, host control loop included)"}
 
 
 def adjoint_measure(args, ws, n_steps=200, ckpt_every=20):

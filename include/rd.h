@@ -163,6 +163,49 @@ int rd_mesh_sizes(const rd_mesh *m, int32_t *n_vertex, int32_t *n_tri);
  * twice, or alpha outside [0, 1].  The caller owns both arrays. */
 int rd_mesh_set_boundary(rd_mesh *m, const uint8_t *ghost, int32_t n_wall, const int32_t *wall, double alpha);
 
+/* ---- periodic Delaunay refinement mesh generator (Sec. 2.3, 2.4, 4.1) -----
+ * rd_meshgen_run builds, on the device, a Delaunay triangulation of the
+ * periodic rectangle [0, Lx) x [0, Ly) in which every triangle has
+ * circumradius <= max_circumradius (size bound R) and circumradius over
+ * shortest edge <= quality (bound B >= 1; sqrt 2 in Ruppert's algorithm).
+ * It starts from an nx0 x ny0 grid (>= 3 each) with seeded jitter, restores
+ * the Delaunay property by edge flips, and then repeats: test every triangle
+ * (Sec. 2.4.1), locate the circumcentres of the bad ones by walking (Sec.
+ * 2.4.2), select insertions with disjoint cavities by random-priority locks
+ * (Sec. 4.1.1), split the containing triangles, and flip non-Delaunay edges
+ * in parallel independent sets until none is left (Sec. 2.4.6, 4.1.4).
+ * Predicates are exact: coordinates are integers on 2^30 units per period of
+ * x (Ly is rounded to that unit; rd_meshgen_domain returns the periods used),
+ * and Orient2D / InCircle2D are evaluated in 64/128-bit integers (exact while
+ * coordinate differences stay below half a period, which holds with >= 3
+ * initial cells per period).  Runs are deterministic for a given seed.
+ * Bounds: max_vertices (capacity), max_rounds insertion rounds and
+ * max_flip_rounds flip rounds per restoration; reaching a round bound returns
+ * RD_ETIMEOUT, a full capacity RD_ENOMEM (the handle is still returned with
+ * the mesh as far as it got).  Output (rd_meshgen_get, host arrays): xy
+ * [nv][2], tri [nt][3] counter-clockwise, shift [nt][3][2] in {0, 1} periods --
+ * the input format of rd_mesh_create -- and optionally the integer
+ * coordinates xy_units [nv][2].  times: ms in quality test + location,
+ * cavities, insertion, flips, and the whole run (CUDA events). */
+typedef struct rd_meshgen rd_meshgen;
+typedef struct {
+  double Lx, Ly;
+  double max_circumradius;
+  double quality;
+  int32_t nx0, ny0;
+  int32_t max_vertices;
+  int32_t max_rounds;
+  int32_t max_flip_rounds;
+  int32_t reserved;
+  uint64_t seed;
+} rd_meshgen_params;
+int rd_meshgen_run(const rd_meshgen_params *p, void *cuda_stream, rd_meshgen **out);
+int rd_meshgen_sizes(const rd_meshgen *g, int32_t *n_vertex, int32_t *n_tri, int32_t *rounds, int32_t *flips);
+int rd_meshgen_times(const rd_meshgen *g, double ms[5]);
+int rd_meshgen_get(const rd_meshgen *g, double *xy, int32_t *tri, int8_t *shift, int64_t *xy_units);
+int rd_meshgen_domain(const rd_meshgen *g, double *Lx, double *Ly, int64_t *Px, int64_t *Py);
+void rd_meshgen_destroy(rd_meshgen *g);
+
 /* ---- solver state ---------------------------------------------------------
  * rd_state_init: allocate the device state of one mesh and upload W (host,
  * component-major, caller order).  Errors: RD_EINVAL (bad params),

@@ -32,6 +32,13 @@ class RDError(RuntimeError):
         super().__init__(f"{what}: {msg} (status {status})")
 
 
+class MeshgenParams(ctypes.Structure):
+    _fields_ = [("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("max_circumradius", ctypes.c_double),
+                ("quality", ctypes.c_double), ("nx0", ctypes.c_int32), ("ny0", ctypes.c_int32),
+                ("max_vertices", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
+                ("max_flip_rounds", ctypes.c_int32), ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
 class Params(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int32), ("precision", ctypes.c_int32), ("cfl", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("eps_fix", ctypes.c_double), ("lumping", ctypes.c_int32),
@@ -58,6 +65,12 @@ _SIGS = {
     "rd_mesh_sizes": (ctypes.c_int, [_vp, _i32p, _i32p]),
     "rd_mesh_set_boundary": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint8), ctypes.c_int32, _i32p,
                                             ctypes.c_double]),
+    "rd_meshgen_run": (ctypes.c_int, [_vp, _vp, _vp]),
+    "rd_meshgen_sizes": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i32p]),
+    "rd_meshgen_times": (ctypes.c_int, [_vp, _dp]),
+    "rd_meshgen_get": (ctypes.c_int, [_vp, _dp, _i32p, ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_int64)]),
+    "rd_meshgen_domain": (ctypes.c_int, [_vp, _dp, _dp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "rd_meshgen_destroy": (None, [_vp]),
     "rd_state_init": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(Params), ctypes.POINTER(_vp)]),
     "rd_state_set": (ctypes.c_int, [_vp, _dp]),
     "rd_step": (ctypes.c_int, [_vp, _dp]),
@@ -462,3 +475,49 @@ def rollout(state: "State", W0, n_steps: int, ckpt_every: int = 20):
             return torch.from_numpy(g0)
 
     return _Rollout.apply(W0)
+
+
+def meshgen(max_circumradius: float, Lx: float = 1.0, Ly: float = 1.0, quality: float = 2.0 ** 0.5,
+            nx0: int = 4, ny0: int = 4, max_vertices: int | None = None, seed: int = 7,
+            max_rounds: int = 10000, max_flip_rounds: int = 10000, stream=None):
+    """Periodic Delaunay refinement on the GPU (rd_meshgen_run).  Returns (mesh, info):
+    an inputs.Mesh of the generated triangulation (xy, tri, shift, periods) and a dict
+    with the integer coordinates, round / flip counts, per-phase times and the status."""
+    torch = _require_gpu()
+    lib = load()
+    from . import inputs
+    if max_vertices is None:
+        # about 1.3 vertices per (R^2) of area for beta <= sqrt 2 meshes, with headroom
+        max_vertices = int(4.0 * Lx * Ly / (max_circumradius ** 2)) + 4 * nx0 * ny0 + 1024
+    p = MeshgenParams(float(Lx), float(Ly), float(max_circumradius), float(quality), int(nx0), int(ny0),
+                      int(max_vertices), int(max_rounds), int(max_flip_rounds), 0, int(seed))
+    st = stream if stream is not None else torch.cuda.Stream()
+    h = _vp()
+    rc = lib.rd_meshgen_run(ctypes.byref(p), _vp(st.cuda_stream), ctypes.byref(h))
+    if not h:
+        _check(rc, "rd_meshgen_run")
+    try:
+        nv, nt, rounds, flips = (ctypes.c_int32() for _ in range(4))
+        _check(lib.rd_meshgen_sizes(h, ctypes.byref(nv), ctypes.byref(nt), ctypes.byref(rounds), ctypes.byref(flips)),
+               "rd_meshgen_sizes")
+        nv, nt = nv.value, nt.value
+        xy = np.empty((nv, 2))
+        tri = np.empty((nt, 3), dtype=np.int32)
+        shift = np.empty((nt, 3, 2), dtype=np.int8)
+        xyu = np.empty((nv, 2), dtype=np.int64)
+        _check(lib.rd_meshgen_get(h, _ptr(xy), _ptr(tri, ctypes.c_int32), _ptr(shift, ctypes.c_int8),
+                                  _ptr(xyu, ctypes.c_int64)), "rd_meshgen_get")
+        ms = np.zeros(5)
+        _check(lib.rd_meshgen_times(h, _ptr(ms)), "rd_meshgen_times")
+        lx, ly = ctypes.c_double(), ctypes.c_double()
+        px, py = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.rd_meshgen_domain(h, ctypes.byref(lx), ctypes.byref(ly), ctypes.byref(px), ctypes.byref(py)),
+               "rd_meshgen_domain")
+    finally:
+        lib.rd_meshgen_destroy(h)
+    mesh = inputs.Mesh(xy=xy, tri=tri, shift=shift, Lx=lx.value, Ly=ly.value,
+                       orig_vertex=np.arange(nv, dtype=np.int64))
+    info = dict(status=rc, rounds=rounds.value, flips=flips.value, xy_units=xyu, Px=px.value, Py=py.value,
+                unit=lx.value / px.value,
+                ms=dict(zip(("quality_locate", "cavities", "insert", "flips", "total"), ms.tolist())))
+    return mesh, info
