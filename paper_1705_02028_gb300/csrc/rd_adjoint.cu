@@ -41,10 +41,7 @@ __device__ __forceinline__ void load_tri3(int t, int nt, const int* __restrict__
   }
 }
 
-__global__ void k_set_dt(DevCtl* ctl, double dt) {
-  ctl->dt = dt;
-  ctl->dtf = (float)dt;
-}
+__global__ void k_set_dt(DevCtl* ctl, double dt) { ctl->dt = dt; }
 __global__ void k_record_dt(const DevCtl* ctl, double* out) { *out = ctl->dt; }
 
 template <class T, int SCHEME>

@@ -223,10 +223,7 @@ namespace {
 // Launches one step reading buffer a and writing buffer 1-a.  ev (nullable):
 // seven events recorded before each kernel and after the last one.
 __global__ void k_fix_dt(DevCtl* ctl, double dt) {
-  if (!ctl->stop) {
-    ctl->dt = dt;
-    ctl->dtf = (float)dt;
-  }
+  if (!ctl->stop) ctl->dt = dt;
 }
 
 // Blend configuration of a state's two-stage triangle kernels (Sec. 3.3.3, Sec. 3.4).

@@ -39,7 +39,7 @@ struct DevCtl {
   int status;             // sticky error bits (RD_ST_*)
   int stop;               // nonzero: remaining kernels of this run are no-ops
   unsigned int ticket;    // last-block-done counter of the dt reduction
-  float dtf;              // dt rounded to float, for the FP32 kernels
+  int pad;
 };
 
 // Control word of the standalone CFL reduction (must start at zero).

@@ -95,13 +95,6 @@ RD_HD double rcp(double x) {
   return 1.0 / x;
 }
 
-// dt of the current step in the kernel's precision (the FP32 kernels read the
-// float copy instead of converting the double on the FP64 pipe).
-template <class T>
-__device__ __forceinline__ T ctl_dt(const DevCtl* ctl) {
-  return sizeof(T) == 8 ? (T)ctl->dt : (T)ctl->dtf;
-}
-
 // Blends of N and LDA (Sec. 3.3.3): diagonal Theta (B), every diagonal entry
 // max_k / min_k Theta_kk (Bmax / Bmin), or the scalar shock-sensor theta (Bx).
 enum : int { BLEND_B = 0, BLEND_MAX = 1, BLEND_MIN = 2, BLEND_X = 3 };
@@ -852,7 +845,6 @@ __global__ void __launch_bounds__(BLOCK) k_gather_cfl(int nv, const int* __restr
         if (!(rem > 0.0)) ctl->stop = 1;  // t_end reached: the rest of this step is a no-op
       }
       ctl->dt = (double)(T)dt;
-      ctl->dtf = (float)dt;
       ctl->ticket = 0u;
     }
   }
@@ -1037,7 +1029,7 @@ __global__ void __launch_bounds__(512) k_update(int nv, const T* __restrict__ Wi
       wall_add(wa, Win, i, gamma, T(1), r);
     }
   }
-  T dt = dtm ? (T)__ldg(dtm + __ldg(vmesh + i)) : ctl_dt<T>(ctl);
+  T dt = dtm ? (T)__ldg(dtm + __ldg(vmesh + i)) : (T)ctl->dt;
   T f = dt / __ldg(V + i);
   T W[4], Z[4], spd;
   load_vec4(Win, i, W);
@@ -1116,7 +1108,7 @@ __global__ void __launch_bounds__(256, (TriOcc<T, 2>::value)) k_tri_stage2(int n
 #pragma unroll
   for (int k = 0; k < 4; ++k) ld4(rp + 4 * k, r + 4 * k);
   T out[3][4];
-  T dt = dtm ? (T)__ldg(dtm + __ldg(tmesh + t)) : ctl_dt<T>(ctl);
+  T dt = dtm ? (T)__ldg(dtm + __ldg(tmesh + t)) : (T)ctl->dt;
   const T area = __ldg(g.area + t);
   const int mode = SCHEME == RD_BMAX2 ? ba.mode : BLEND_B;
   const int sl = (SCHEME == RD_BMAX2 || SCHEME == RD_LDA2) ? ba.sl : 0;

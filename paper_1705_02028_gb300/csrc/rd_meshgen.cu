@@ -29,7 +29,7 @@ struct rd_meshgen {
   int32_t cap_v = 0, cap_t = 0, nv = 0, nt = 0;
   int32_t rounds = 0, flips = 0, deferred = 0;
   DevBuf vx, vy, tv, ts, tn, tc;         // mesh
-  DevBuf flag, offs, cand, ctri, cpt, lock, win, part, total;
+  DevBuf flag, offs, cand, ctri, cedge, cpt, lock, win, part, total;
   double ms[5] = {0, 0, 0, 0, 0};        // quality+locate, cavities, insertion, flips, total
   Mesh dev() const {
     Mesh m;
@@ -125,36 +125,39 @@ __global__ void k_quality(Mesh m, int nt, double R_units, double B, int* __restr
 // compacted candidates: cand[i] = bad triangle, its circumcentre located
 __global__ void k_locate(Mesh m, int nt, const int* __restrict__ flag, const int* __restrict__ offs,
                          const P64* __restrict__ centre, int* __restrict__ cand, int* __restrict__ ctri,
-                         P64* __restrict__ cpt) {
+                         int* __restrict__ cedge, P64* __restrict__ cpt) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt || !flag[t]) return;
   const int i = offs[t];
   P64 p = centre[t];
+  int edge = -1;
   cand[i] = t;
-  ctri[i] = locate(m, t, p);
+  ctri[i] = locate(m, t, p, edge);
+  cedge[i] = edge;
   cpt[i] = p;
 }
 
-__global__ void k_cavity_lock(Mesh m, int nc, const int* __restrict__ ctri, const P64* __restrict__ cpt,
-                              unsigned long long* __restrict__ lock, uint64_t seed, uint32_t round) {
+__global__ void k_cavity_lock(Mesh m, int nc, const int* __restrict__ ctri, const int* __restrict__ cedge,
+                              const P64* __restrict__ cpt, unsigned long long* __restrict__ lock, uint64_t seed,
+                              uint32_t round) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nc || ctri[i] < 0) return;
   int32_t list[MAX_CAVITY];
-  const int n = cavity(m, ctri[i], cpt[i], list);
+  const int n = cavity(m, ctri[i], cpt[i], cedge[i], list);
   if (n < 0) return;
   const unsigned long long pr = priority(seed, round, (uint32_t)i);
   for (int q = 0; q < n; ++q) atomicMax(lock + list[q], pr);
 }
 
-__global__ void k_cavity_win(Mesh m, int nc, const int* __restrict__ ctri, const P64* __restrict__ cpt,
-                             const unsigned long long* __restrict__ lock, uint64_t seed, uint32_t round,
-                             int* __restrict__ win) {
+__global__ void k_cavity_win(Mesh m, int nc, const int* __restrict__ ctri, const int* __restrict__ cedge,
+                             const P64* __restrict__ cpt, const unsigned long long* __restrict__ lock, uint64_t seed,
+                             uint32_t round, int* __restrict__ win) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nc) return;
   int w = 0;
   if (ctri[i] >= 0) {
     int32_t list[MAX_CAVITY];
-    const int n = cavity(m, ctri[i], cpt[i], list);
+    const int n = cavity(m, ctri[i], cpt[i], cedge[i], list);
     if (n > 0) {
       const unsigned long long pr = priority(seed, round, (uint32_t)i);
       w = 1;
@@ -165,12 +168,16 @@ __global__ void k_cavity_win(Mesh m, int nc, const int* __restrict__ ctri, const
 }
 
 __global__ void k_insert(Mesh m, int nc, const int* __restrict__ win, const int* __restrict__ rank,
-                         const int* __restrict__ ctri, const P64* __restrict__ cpt, int nv0, int nt0, int n_ins) {
+                         const int* __restrict__ ctri, const int* __restrict__ cedge, const P64* __restrict__ cpt,
+                         int nv0, int nt0, int n_ins) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nc || !win[i]) return;
   const int r = rank[i];
   if (r >= n_ins) return;  // beyond capacity this round
-  split3(m, ctri[i], nv0 + r, cpt[i], nt0 + 2 * r, nt0 + 2 * r + 1);
+  if (cedge[i] >= 0)       // on an edge: split the two triangles that share it
+    split4(m, ctri[i], cedge[i], nv0 + r, cpt[i], nt0 + 2 * r, nt0 + 2 * r + 1);
+  else
+    split3(m, ctri[i], nv0 + r, cpt[i], nt0 + 2 * r, nt0 + 2 * r + 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -352,6 +359,7 @@ int run(rd_meshgen* g) {
   CK(dev_alloc(g->win, ct * sizeof(int), st));
   CK(dev_alloc(g->cand, ct * sizeof(int), st));
   CK(dev_alloc(g->ctri, ct * sizeof(int), st));
+  CK(dev_alloc(g->cedge, ct * sizeof(int), st));
   CK(dev_alloc(g->cpt, ct * sizeof(P64), st));
   CK(dev_alloc(g->lock, ct * sizeof(unsigned long long), st));
   CK(dev_alloc(g->part, ((ct + BLK - 1) / BLK + 1) * sizeof(int), st));
@@ -383,13 +391,14 @@ int run(rd_meshgen* g) {
       break;
     }
     k_locate<<<nb(nt), BLK, 0, st>>>(m, nt, (const int*)g->flag.p, (const int*)g->offs.p, (const P64*)centre.p,
-                                     (int*)g->cand.p, (int*)g->ctri.p, (P64*)g->cpt.p);
+                                     (int*)g->cand.p, (int*)g->ctri.p, (int*)g->cedge.p, (P64*)g->cpt.p);
     cudaEventRecord(e[1], st);
     CU(cudaMemsetAsync(g->lock.p, 0, (size_t)nt * sizeof(unsigned long long), st));
-    k_cavity_lock<<<nb(nc), BLK, 0, st>>>(m, nc, (const int*)g->ctri.p, (const P64*)g->cpt.p,
-                                          (unsigned long long*)g->lock.p, p.seed, (uint32_t)r);
-    k_cavity_win<<<nb(nc), BLK, 0, st>>>(m, nc, (const int*)g->ctri.p, (const P64*)g->cpt.p,
-                                         (const unsigned long long*)g->lock.p, p.seed, (uint32_t)r, (int*)g->win.p);
+    k_cavity_lock<<<nb(nc), BLK, 0, st>>>(m, nc, (const int*)g->ctri.p, (const int*)g->cedge.p,
+                                          (const P64*)g->cpt.p, (unsigned long long*)g->lock.p, p.seed, (uint32_t)r);
+    k_cavity_win<<<nb(nc), BLK, 0, st>>>(m, nc, (const int*)g->ctri.p, (const int*)g->cedge.p,
+                                         (const P64*)g->cpt.p, (const unsigned long long*)g->lock.p, p.seed,
+                                         (uint32_t)r, (int*)g->win.p);
     CU(cudaGetLastError());
     std::swap(g->flag, g->win);  // scan the winners: offs = rank of each winner
     int nwin = 0;
@@ -407,7 +416,7 @@ int run(rd_meshgen* g) {
       break;
     }
     k_insert<<<nb(nc), BLK, 0, st>>>(m, nc, (const int*)g->win.p, (const int*)g->offs.p, (const int*)g->ctri.p,
-                                     (const P64*)g->cpt.p, g->nv, g->nt, n_ins);
+                                     (const int*)g->cedge.p, (const P64*)g->cpt.p, g->nv, g->nt, n_ins);
     CU(cudaGetLastError());
     g->nv += n_ins;
     g->nt += 2 * n_ins;
@@ -520,7 +529,7 @@ extern "C" void rd_meshgen_destroy(rd_meshgen* g) {
   if (!g) return;
   if (g->stream) cudaStreamSynchronize(g->stream);
   DevBuf* bufs[] = {&g->vx, &g->vy, &g->tv, &g->ts, &g->tn, &g->tc, &g->flag, &g->offs, &g->cand,
-                    &g->ctri, &g->cpt, &g->lock, &g->win, &g->part, &g->total};
+                    &g->ctri, &g->cedge, &g->cpt, &g->lock, &g->win, &g->part, &g->total};
   for (DevBuf* b : bufs) dev_free(*b);
   if (g->own_stream) cudaStreamDestroy(g->stream);
   delete g;

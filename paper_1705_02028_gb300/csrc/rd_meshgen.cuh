@@ -113,12 +113,14 @@ MG_HD bool quality_test(const Mesh& m, int32_t t, double R_units, double B, P64&
 
 // Point location by walking (Sec. 2.4.2): start in t, cross an edge that has p
 // on its outer side, mapping p into each new frame.  Returns the containing
-// triangle with p in its frame, -1 if p falls on an edge or vertex (the
-// candidate is deferred), -2 if the walk did not end within MAX_WALK steps.
-MG_HD int32_t locate(const Mesh& m, int32_t t, P64& p) {
-  int from = -1;  // edge we entered through (not re-tested first)
+// triangle with p in its frame and sets `edge` to the corner opposite the edge
+// p lies on (-1 if p is strictly inside); -1 if p falls on a vertex, -2 if the
+// walk did not end within MAX_WALK steps (the candidate is deferred).
+MG_HD int32_t locate(const Mesh& m, int32_t t, P64& p, int& edge) {
+  int from = -1;  // edge we entered through (tested last)
+  edge = -1;
   for (int step = 0; step < MAX_WALK; ++step) {
-    int out = -1, zero = 0;
+    int out = -1, zeros = 0, zk = -1;
     for (int q = 0; q < 3; ++q) {
       const int k = (from < 0 ? q : (from + 1 + q) % 3);
       const int o = orient(corner(m, t, (k + 1) % 3), corner(m, t, (k + 2) % 3), p);
@@ -126,9 +128,16 @@ MG_HD int32_t locate(const Mesh& m, int32_t t, P64& p) {
         out = k;
         break;
       }
-      if (o == 0) zero = 1;
+      if (o == 0) {
+        ++zeros;
+        zk = k;
+      }
     }
-    if (out < 0) return zero ? -1 : t;
+    if (out < 0) {
+      if (zeros > 1) return -1;
+      edge = zk;
+      return t;
+    }
     const P64 off = frame_offset(m, t, out);
     p.x += off.x;
     p.y += off.y;
@@ -143,19 +152,29 @@ MG_HD int32_t locate(const Mesh& m, int32_t t, P64& p) {
 // grown from the containing triangle across edges, plus the containing
 // triangle's three neighbours (whose adjacency the split rewrites).  Fills
 // list[0..n) and returns n, or -1 if more than MAX_CAVITY triangles.
-MG_HD int cavity(const Mesh& m, int32_t t0, P64 p0, int32_t* list) {
+MG_HD int cavity(const Mesh& m, int32_t t0, P64 p0, int edge, int32_t* list) {
   int n = 0;
   P64 pts[MAX_CAVITY];
   list[n] = t0;
   pts[n++] = p0;
-  for (int k = 0; k < 3; ++k) {
-    const int32_t nb = m.tn[3 * (size_t)t0 + k];
-    bool dup = false;
-    for (int q = 0; q < n; ++q) dup = dup || list[q] == nb;
-    if (dup) continue;
-    const P64 off = frame_offset(m, t0, k);
-    list[n] = nb;
-    pts[n++] = P64{p0.x + off.x, p0.y + off.y};
+  // the triangles the split rewrites and their neighbours: t0's 1-ring, and for a
+  // point on an edge also the 1-ring of the triangle across it
+  for (int side = 0; side < (edge >= 0 ? 2 : 1); ++side) {
+    const int32_t tt = side == 0 ? t0 : m.tn[3 * (size_t)t0 + edge];
+    P64 pt = p0;
+    if (side == 1) {
+      const P64 off = frame_offset(m, t0, edge);
+      pt = P64{p0.x + off.x, p0.y + off.y};
+    }
+    for (int k = 0; k < 3; ++k) {
+      const int32_t nb = m.tn[3 * (size_t)tt + k];
+      bool dup = false;
+      for (int q = 0; q < n; ++q) dup = dup || list[q] == nb;
+      if (dup) continue;
+      const P64 off = frame_offset(m, tt, k);
+      list[n] = nb;
+      pts[n++] = P64{pt.x + off.x, pt.y + off.y};
+    }
   }
   // breadth-first growth through triangles whose circumcircle contains p
   for (int h = 0; h < n; ++h) {
@@ -237,6 +256,70 @@ MG_HD void split3(Mesh& m, int32_t t, int32_t pv, P64 p, int32_t t1, int32_t t2)
     m.tn[3 * (size_t)nb[k] + nc[k]] = id[k];
     m.tc[3 * (size_t)nb[k] + nc[k]] = 2;
   }
+}
+
+// Split of the two triangles on either side of the edge opposite corner k of t
+// by the new vertex pv lying on that edge (p in t's frame): with t = (c, a, b)
+// and n = (d, b, a), the four triangles (c, a, p) [id t], (c, p, b) [t1],
+// (d, b, p) [id n] and (d, p, a) [t2].
+MG_HD void split4(Mesh& m, int32_t t, int k, int32_t pv, P64 p, int32_t t1, int32_t t2) {
+  const int32_t n = m.tn[3 * (size_t)t + k];
+  const int j = m.tc[3 * (size_t)t + k];
+  const int ka = (k + 1) % 3, kb = (k + 2) % 3, jb = (j + 1) % 3, ja = (j + 2) % 3;
+  const P64 off = frame_offset(m, t, k);
+  const int32_t c = m.tv[3 * (size_t)t + k], a = m.tv[3 * (size_t)t + ka], b = m.tv[3 * (size_t)t + kb];
+  const int32_t d = m.tv[3 * (size_t)n + j];
+  const int8_t* st = m.ts + 6 * (size_t)t;
+  const int8_t* sn = m.ts + 6 * (size_t)n;
+  const int8_t dsx = (int8_t)(sn[2 * j] - off.x / m.Px), dsy = (int8_t)(sn[2 * j + 1] - off.y / m.Py);
+  const int32_t o_ca = m.tn[3 * (size_t)t + kb], o_bc = m.tn[3 * (size_t)t + ka];
+  const int8_t c_ca = m.tc[3 * (size_t)t + kb], c_bc = m.tc[3 * (size_t)t + ka];
+  const int32_t o_db = m.tn[3 * (size_t)n + ja], o_ad = m.tn[3 * (size_t)n + jb];
+  const int8_t c_db = m.tc[3 * (size_t)n + ja], c_ad = m.tc[3 * (size_t)n + jb];
+  const int8_t s_c[2] = {st[2 * k], st[2 * k + 1]}, s_a[2] = {st[2 * ka], st[2 * ka + 1]},
+               s_b[2] = {st[2 * kb], st[2 * kb + 1]};
+  int64_t wx = p.x % m.Px, wy = p.y % m.Py;
+  if (wx < 0) wx += m.Px;
+  if (wy < 0) wy += m.Py;
+  m.vx[pv] = (int32_t)wx;
+  m.vy[pv] = (int32_t)wy;
+  const int8_t psx = (int8_t)((p.x - wx) / m.Px), psy = (int8_t)((p.y - wy) / m.Py);
+  {  // (c, a, p): c faces (a, p) -> (d, p, a) corner 0; a faces (p, c) -> (c, p, b) corner 2; p faces (c, a)
+    const int32_t v[3] = {c, a, pv};
+    const int8_t s[6] = {s_c[0], s_c[1], s_a[0], s_a[1], psx, psy};
+    const int32_t nb[3] = {t2, t1, o_ca};
+    const int8_t nc[3] = {0, 2, c_ca};
+    write_triangle(m, t, v, s, nb, nc);
+  }
+  {  // (c, p, b): c faces (p, b) -> (d, b, p) corner 0; p faces (b, c); b faces (c, p) -> (c, a, p) corner 1
+    const int32_t v[3] = {c, pv, b};
+    const int8_t s[6] = {s_c[0], s_c[1], psx, psy, s_b[0], s_b[1]};
+    const int32_t nb[3] = {n, o_bc, t};
+    const int8_t nc[3] = {0, c_bc, 1};
+    write_triangle(m, t1, v, s, nb, nc);
+  }
+  {  // (d, b, p): d faces (b, p) -> (c, p, b) corner 0; b faces (p, d) -> (d, p, a) corner 2; p faces (d, b)
+    const int32_t v[3] = {d, b, pv};
+    const int8_t s[6] = {dsx, dsy, s_b[0], s_b[1], psx, psy};
+    const int32_t nb[3] = {t1, t2, o_db};
+    const int8_t nc[3] = {0, 2, c_db};
+    write_triangle(m, n, v, s, nb, nc);
+  }
+  {  // (d, p, a): d faces (p, a) -> (c, a, p) corner 0; p faces (a, d); a faces (d, p) -> (d, b, p) corner 1
+    const int32_t v[3] = {d, pv, a};
+    const int8_t s[6] = {dsx, dsy, psx, psy, s_a[0], s_a[1]};
+    const int32_t nb[3] = {t, o_ad, n};
+    const int8_t nc[3] = {0, c_ad, 1};
+    write_triangle(m, t2, v, s, nb, nc);
+  }
+  m.tn[3 * (size_t)o_ca + c_ca] = t;
+  m.tc[3 * (size_t)o_ca + c_ca] = 2;
+  m.tn[3 * (size_t)o_bc + c_bc] = t1;
+  m.tc[3 * (size_t)o_bc + c_bc] = 1;
+  m.tn[3 * (size_t)o_db + c_db] = n;
+  m.tc[3 * (size_t)o_db + c_db] = 2;
+  m.tn[3 * (size_t)o_ad + c_ad] = t2;
+  m.tc[3 * (size_t)o_ad + c_ad] = 1;
 }
 
 // Is the edge opposite corner k of t (shared with n = tn[t][k], t < n) not
