@@ -76,6 +76,110 @@ __global__ void __launch_bounds__(ADJ_TRI_BLOCK) k_mask2(int nt, const int* __re
   mask[t] = stage2_mask<T, SCHEME>(Zc, wn, ws, r, nx, ny, hl, __ldg(g.area + t), dt, gamma, eps);
 }
 
+// Forward re-run kernels that also record the branch masks, so each triangle is
+// linearised once per stage: the same steps as k_tri_stage1 / k_tri_stage2
+// (linearise, LDA, blend, total residuals), with the masks read off the same
+// intermediate values stage1_mask / stage2_mask compute.
+template <class T, int SCHEME>
+__global__ void __launch_bounds__(ADJ_TRI_BLOCK) k_stage1_masked(int nt, const int* __restrict__ tri, DevGeo<T> g,
+                                                                 const T* __restrict__ Z, const T* __restrict__ spd,
+                                                                 Gas<T> gas, T eps, T* __restrict__ share,
+                                                                 T* __restrict__ rec, T* __restrict__ cfl,
+                                                                 DevCtl* ctl, Mask* __restrict__ mask) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  int v[3];
+  T nx[3], ny[3], hl[3], Zc[3][4];
+  load_tri3(t, nt, tri, g, v, nx, ny, hl);
+  for (int c = 0; c < 3; ++c) load_vec4(Z, v[c], Zc[c]);
+  {
+    T s0 = __ldg(spd + v[0]), s1 = __ldg(spd + v[1]), s2 = __ldg(spd + v[2]);
+    T lam = mag_less(s1, s0) ? s0 : s1;
+    lam = mag_less(s2, lam) ? lam : s2;
+    cfl[t] = __ldg(g.lmax + t) * lam;
+  }
+  TriLin<T> L;
+  int st = linearise(Zc, nx, ny, hl, gas, eps, L);
+  if (st) {
+    mask[t] = 0;
+    atomicOr(&ctl->status, st);
+    return;
+  }
+  Mask mk = node_mask(L, hl, eps);
+  T out[3][4];
+  if (SCHEME == RD_N1) {
+    for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 4; ++k) out[i][k] = L.phiN[i][k];
+  } else {
+    T lda[3][4];
+    lda_apply(L, L.phiT, lda);
+    if (SCHEME == RD_LDA2) {
+      for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 4; ++k) out[i][k] = lda[i][k];
+    } else {
+      mk |= blend_mask(L.phiT, L.phiN);
+      blend(L.phiT, L.phiN, lda, out);
+    }
+    T* rp = rec + (size_t)t * 16;
+    for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 4; ++k) rp[4 * i + k] = L.phiN[i][k];
+    for (int k = 0; k < 4; ++k) rp[12 + k] = L.phiT[k];
+  }
+  mask[t] = mk;
+  T* sp = share + (size_t)t * 12;
+  for (int i = 0; i < 3; ++i) st4(sp + 4 * i, out[i]);
+}
+
+template <class T, int SCHEME>
+__global__ void __launch_bounds__(ADJ_TRI_BLOCK) k_stage2_masked(int nt, const int* __restrict__ tri, DevGeo<T> g,
+                                                                 const T* __restrict__ Zs, const T* __restrict__ Wn,
+                                                                 const T* __restrict__ Ws, const T* __restrict__ rec,
+                                                                 Gas<T> gas, T eps, T* __restrict__ share,
+                                                                 DevCtl* ctl, Mask* __restrict__ mask) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  int v[3];
+  T nx[3], ny[3], hl[3], Zc[3][4], wn[3][4], ws[3][4], r[16];
+  load_tri3(t, nt, tri, g, v, nx, ny, hl);
+  for (int c = 0; c < 3; ++c) {
+    load_vec4(Zs, v[c], Zc[c]);
+    load_vec4(Wn, v[c], wn[c]);
+    load_vec4(Ws, v[c], ws[c]);
+  }
+  for (int k = 0; k < 4; ++k) ld4(rec + (size_t)t * 16 + 4 * k, r + 4 * k);
+  const T dt = (T)ctl->dt;
+  TriLin<T> L;
+  int st = linearise(Zc, nx, ny, hl, gas, eps, L);
+  if (st) {
+    mask[t] = 0;
+    atomicOr(&ctl->status, st);
+    return;
+  }
+  Mask mk = node_mask(L, hl, eps);
+  const T a3 = __ldg(g.area + t) * (T(1) / T(3));
+  const T idt = rcp(dt);
+  T PhiN[3][4], PhiT[4] = {T(0), T(0), T(0), T(0)};
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 4; ++k) {
+      T mm = a3 * ((ws[i][k] - wn[i][k]) * idt);
+      PhiN[i][k] = mm + (L.phiN[i][k] + r[4 * i + k]) * T(0.5);
+      PhiT[k] += mm;
+    }
+  for (int k = 0; k < 4; ++k) PhiT[k] += (r[12 + k] + L.phiT[k]) * T(0.5);
+  T lda[3][4], out[3][4];
+  lda_apply(L, PhiT, lda);
+  if (SCHEME == RD_LDA2) {
+    for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 4; ++k) out[i][k] = lda[i][k];
+  } else {
+    mk |= blend_mask(PhiT, PhiN);
+    blend(PhiT, PhiN, lda, out);
+  }
+  mask[t] = mk;
+  T* sp = share + (size_t)t * 12;
+  for (int i = 0; i < 3; ++i) st4(sp + 4 * i, out[i]);
+}
+
 // adjoint of the stage-2 triangle pass: per corner (Z*, W*, W^n) bars, per triangle the record bar
 template <class T, int SCHEME>
 __global__ void __launch_bounds__(ADJ_TRI_BLOCK) k_adj_stage2(int nt, const int* __restrict__ tri, DevGeo<T> g,
@@ -220,9 +324,14 @@ struct rd_adjoint_store {
   std::vector<double> dts;                 // host copy of the recorded dt sequence
   DevBuf dts_dev, ckpt, segW, Zn, spd, Ws, Zs, R1, share, rec, cfl, partial, ctl, mask1, mask2, lam, lams, cb1,
       cb2, recb, stage;
+  // two-stage schemes, when a segment's worth fits in a quarter of the free device
+  // memory: Z^n, W*, Z* and the stage-2 record of every step of the segment, kept
+  // from the forward re-run so that the reverse sweep does not recompute stage 1
+  DevBuf segZn, segWs, segZs, segRec;
+  bool stored = false;
   ~rd_adjoint_store() {
     DevBuf* b[] = {&dts_dev, &ckpt, &segW, &Zn, &spd, &Ws, &Zs, &R1, &share, &rec, &cfl, &partial, &ctl,
-                   &mask1, &mask2, &lam, &lams, &cb1, &cb2, &recb, &stage};
+                   &mask1, &mask2, &lam, &lams, &cb1, &cb2, &recb, &stage, &segZn, &segWs, &segZs, &segRec};
     for (DevBuf* d : b) dev_free(*d);
   }
 };
@@ -259,6 +368,23 @@ int ensure(rd_adjoint_store* A, rd_state* s, cudaStream_t st) {
   CK(dev_alloc(A->cb2, 36 * nt * ts, st));
   CK(dev_alloc(A->recb, 16 * nt * ts, st));
   CK(dev_alloc(A->stage, 4 * nv * sizeof(double), st));
+  A->stored = false;
+  if (s->p.scheme != RD_N1) {
+    size_t free_b = 0, total_b = 0;
+    const size_t need = k * (12 * nv + 16 * nt) * ts;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && need <= free_b / 4) {
+      if (dev_alloc(A->segZn, k * 4 * nv * ts, st) == RD_OK && dev_alloc(A->segWs, k * 4 * nv * ts, st) == RD_OK &&
+          dev_alloc(A->segZs, k * 4 * nv * ts, st) == RD_OK && dev_alloc(A->segRec, k * 16 * nt * ts, st) == RD_OK)
+        A->stored = true;
+    }
+    cudaGetLastError();
+    if (!A->stored) {  // recompute instead
+      dev_free(A->segZn);
+      dev_free(A->segWs);
+      dev_free(A->segZs);
+      dev_free(A->segRec);
+    }
+  }
   return RD_OK;
 }
 
@@ -309,20 +435,30 @@ int backward(rd_state* s, rd_adjoint_store* A, const double* dLdWf, double* dLdW
     const int n0 = seg * k, n1 = std::min(n0 + k, A->n_steps);
     CU(cudaMemcpyAsync(segW, (const T*)A->ckpt.p + (size_t)seg * wsz, wsz * sizeof(T), cudaMemcpyDeviceToDevice, st));
     // forward re-run of the segment: keep W^n of every step and both stages' masks
+    // (each triangle linearised once per stage: the masks come with the shares)
     for (int j = 0; j < n1 - n0; ++j) {
       const double dt = A->dts[n0 + j];
       T* Wn = segW + (size_t)j * wsz;
       T* Wn1 = segW + (size_t)(j + 1) * wsz;
+      T* Znj = A->stored ? (T*)A->segZn.p + (size_t)j * wsz : Zn;
+      T* Wsj = A->stored ? (T*)A->segWs.p + (size_t)j * wsz : Ws;
+      T* Zsj = A->stored ? (T*)A->segZs.p + (size_t)j * wsz : Zs;
+      T* recj = A->stored ? (T*)A->segRec.p + (size_t)j * 16 * nt : rec;
+      k_prepare<T><<<gv, ADJ_VTX_BLOCK, 0, st>>>(nv, Wn, gamma, Znj, spd, ctl);
+      k_stage1_masked<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, Znj, spd, Gas<T>::of(gamma), eps, share,
+                                                          recj, cf, ctl, mask1 + (size_t)j * nt);
+      launch_gather_cfl<T>(VTX_BLOCK, st, nv, ptr, ent, share, cf, V, (T*)A->R1.p, (T*)A->partial.p, cflnum, ctl);
+      k_set_dt<<<1, 1, 0, st>>>(ctl, dt);
       if (two) {
-        stage1_and_wstar(Wn, dt, Ws, Zs);
-        k_mask1<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, Zn, gamma, eps, mask1 + (size_t)j * nt);
-        k_tri_stage2<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, nv, tri, g, Zs, Wn, Ws, rec, Gas<T>::of(gamma), eps, share, ctl);
-        k_mask2<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, Zs, Wn, Ws, rec, (T)dt, gamma, eps,
-                                                    mask2 + (size_t)j * nt);
-        k_update<T><<<gv, ADJ_VTX_BLOCK, 0, st>>>(nv, Ws, nullptr, ptr, ent, share, V, gamma, Wn1, Zs, nullptr, ctl);
+        k_update<T><<<gv, ADJ_VTX_BLOCK, 0, st>>>(nv, Wn, (const T*)A->R1.p, ptr, ent, nullptr, V, gamma, Wsj, Zsj,
+                                                  nullptr, ctl);
+        k_stage2_masked<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, Zsj, Wn, Wsj, recj, Gas<T>::of(gamma), eps,
+                                                            share, ctl, mask2 + (size_t)j * nt);
+        // Z of W^{n+1} is not needed (the next step's k_prepare recomputes it): scratch
+        k_update<T><<<gv, ADJ_VTX_BLOCK, 0, st>>>(nv, Wsj, nullptr, ptr, ent, share, V, gamma, Wn1, Zs, nullptr, ctl);
       } else {
-        stage1_and_wstar(Wn, dt, Wn1, Zs);
-        k_mask1<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, Zn, gamma, eps, mask1 + (size_t)j * nt);
+        k_update<T><<<gv, ADJ_VTX_BLOCK, 0, st>>>(nv, Wn, (const T*)A->R1.p, ptr, ent, nullptr, V, gamma, Wn1, Zs,
+                                                  nullptr, ctl);
       }
     }
     // reverse sweep over the segment
@@ -330,11 +466,19 @@ int backward(rd_state* s, rd_adjoint_store* A, const double* dLdWf, double* dLdW
       const double dt = A->dts[n0 + j];
       T* Wn = segW + (size_t)j * wsz;
       if (two) {
-        stage1_and_wstar(Wn, dt, Ws, Zs);
-        k_adj_stage2<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, V, Zs, Wn, Ws, rec, mask2 + (size_t)j * nt, lam,
-                                                          (T)dt, gamma, eps, (T*)A->cb2.p, (T*)A->recb.p, ctl);
-        k_adj_gather2<T><<<gv, ADJ_VTX_BLOCK, 0, st>>>(nv, ptr, ent, (const T*)A->cb2.p, lam, Ws, gamma, lams);
-        k_adj_stage1<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, V, Zn, mask1 + (size_t)j * nt, lams,
+        T *Znj = Zn, *Wsj = Ws, *Zsj = Zs, *recj = rec;
+        if (A->stored) {  // kept by the forward re-run
+          Znj = (T*)A->segZn.p + (size_t)j * wsz;
+          Wsj = (T*)A->segWs.p + (size_t)j * wsz;
+          Zsj = (T*)A->segZs.p + (size_t)j * wsz;
+          recj = (T*)A->segRec.p + (size_t)j * 16 * nt;
+        } else {
+          stage1_and_wstar(Wn, dt, Ws, Zs);
+        }
+        k_adj_stage2<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, V, Zsj, Wn, Wsj, recj, mask2 + (size_t)j * nt,
+                                                          lam, (T)dt, gamma, eps, (T*)A->cb2.p, (T*)A->recb.p, ctl);
+        k_adj_gather2<T><<<gv, ADJ_VTX_BLOCK, 0, st>>>(nv, ptr, ent, (const T*)A->cb2.p, lam, Wsj, gamma, lams);
+        k_adj_stage1<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, V, Znj, mask1 + (size_t)j * nt, lams,
                                                           (const T*)A->recb.p, (T)dt, gamma, eps, (T*)A->cb1.p, ctl);
         k_adj_gather1<T><<<gv, ADJ_VTX_BLOCK, 0, st>>>(nv, ptr, ent, (const T*)A->cb1.p, (const T*)A->cb2.p, lams,
                                                        Wn, gamma, lam);
