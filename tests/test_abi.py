@@ -92,3 +92,32 @@ def test_flop_count_of_the_triangle_kernels(lib):
     assert n1["sqrt"] == 1 and b1["sqrt"] == 1            # one sqrt per Roe state
     assert 500 < n1["total"] < b1["total"] < b2["total"] < 3000
     assert b1["div"] <= 20 and b2["div"] <= 20
+
+
+def test_boundary_and_meshgen_argument_checks(lib):
+    """Argument checks of the boundary and mesh-generator entry points run before any device work."""
+    assert lib.rd_mesh_set_boundary(None, None, 0, None, 0.75) == binding.RD_EINVAL
+    h = ctypes.c_void_p()
+    good = dict(Lx=1.0, Ly=1.0, max_circumradius=0.05, quality=2 ** 0.5, nx0=4, ny0=4, max_vertices=1000,
+                max_rounds=10, max_flip_rounds=10, reserved=0, seed=1)
+    for key, bad in (("nx0", 2), ("quality", 0.9), ("max_circumradius", 0.0), ("Lx", -1.0),
+                     ("max_vertices", 8), ("max_rounds", 0), ("max_flip_rounds", 0)):
+        p = binding.MeshgenParams(**{**good, key: bad})
+        assert lib.rd_meshgen_run(ctypes.byref(p), None, ctypes.byref(h)) == binding.RD_EINVAL, key
+        assert not h.value
+    assert lib.rd_meshgen_run(None, None, ctypes.byref(h)) == binding.RD_EINVAL
+    assert lib.rd_meshgen_sizes(None, None, None, None, None) == binding.RD_EINVAL
+    lib.rd_meshgen_destroy(None)
+
+
+def test_scheme_and_lumping_parameters(lib):
+    """rd_params: scheme and lumping codes outside their ranges, selective lumping with
+    the one-stage N scheme, and a nonzero reserved field are rejected."""
+    h = ctypes.c_void_p()
+    for args in ((6, 0, 0.8, 1.4, 1e-6, 0, 0), (1, 0, 0.8, 1.4, 1e-6, 2, 0), (0, 0, 0.8, 1.4, 1e-6, 1, 0),
+                 (1, 0, 0.8, 1.4, 1e-6, 0, 7)):
+        p = binding.Params(*args)
+        # a NULL mesh is rejected as well, so this checks the parameter path does not crash
+        assert lib.rd_state_init(None, None, ctypes.byref(p), ctypes.byref(h)) == binding.RD_EINVAL
+    assert binding._params("B2_SL", "fp64", 0.8, 1.4, 1e-6).lumping == 1
+    assert binding._params("BX2", "fp32", 0.8, 1.4, 1e-6).scheme == 5
