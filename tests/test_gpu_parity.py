@@ -211,3 +211,26 @@ def test_full_size_4096_khi_b2_first_step(rd):
     Wo, dto = oracle.run(mesh, W0, "B2", nsteps=1, nthreads=NTH)
     assert dt == pytest.approx(dto[0], rel=1e-14)
     assert rel_max_err(s.get(), Wo) < TOL
+
+
+def test_full_size_4096_in_the_benchmarked_configuration(rd):
+    """The configuration bench.py times: 4096^2 KHI B2 with the autotuned launch shapes,
+    two steps through the captured CUDA graph of rd_run, FP64 against the oracle at
+    1e-12 and FP32 by its L1 density error."""
+    mesh = inputs.periodic_grid(4096)
+    W0 = inputs.khi_state(mesh)
+    m = rd.Mesh(mesh, reorder="morton")
+    s = rd.State(m, W0, scheme="B2")
+    shapes = s.autotune()
+    assert s.run(2) == 2
+    Wo, dto = oracle.run(mesh, W0, "B2", nsteps=2, nthreads=NTH)
+    err = rel_max_err(s.get(), Wo)
+    print(f"4096^2 B2, shapes {shapes}, 2 graph steps: rel max err {err:.2e}")
+    assert err < TOL
+    s.close()
+    s32 = rd.State(m, W0, scheme="B2", precision="fp32")
+    s32.autotune()
+    assert s32.run(2) == 2
+    l1 = exact.l1_error(oracle.geometry(mesh)["V"], s32.get()[0], Wo[0])
+    print(f"4096^2 B2 FP32, 2 graph steps: L1 density error vs the FP64 oracle {l1:.2e}")
+    assert l1 < 1e-6
