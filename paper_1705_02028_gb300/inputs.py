@@ -276,6 +276,21 @@ def bounded_grid(Nx: int, Ny: int | None = None, Lx: float = 1.0, Ly: float | No
     return relabel(mesh, relabel_seed) if relabel_seed is not None else mesh
 
 
+def noh_quadrant(N: int, relabel_seed: int | None = None) -> Mesh:
+    """The quadrant [0, 1]^2 of the Noh problem (Sec. 5.2): reflecting walls on the
+    symmetry lines x = 0 and y = 0, ghost vertices (held at the initial inflow
+    state) on x = 1 and y = 1; N x N cells split along a-c."""
+    m = bounded_grid(N, N, bc_x="wall", bc_y="wall")
+    P = m.xy[m.tri] + m.shift * np.array([m.Lx, m.Ly])
+    keep = [(t, c) for t, c in m.walls
+            if (P[t, (c + 1) % 3, 0] == 0.0 and P[t, (c + 2) % 3, 0] == 0.0)
+            or (P[t, (c + 1) % 3, 1] == 0.0 and P[t, (c + 2) % 3, 1] == 0.0)]
+    m.walls = np.ascontiguousarray(np.array(keep, dtype=np.int32))
+    x, y = m.xy[:, 0], m.xy[:, 1]
+    m.ghost = ((x >= m.Lx * (1 - 1e-12)) | (y >= m.Ly * (1 - 1e-12))).astype(np.uint8)
+    return relabel(m, relabel_seed) if relabel_seed is not None else m
+
+
 # ---------------------------------------------------------------------------
 # conserved state from primitives
 # ---------------------------------------------------------------------------
@@ -317,6 +332,18 @@ def uniform01(seed: int, counters: np.ndarray) -> np.ndarray:
 def uniform_state(mesh: Mesh, rho=1.0, u=0.0, v=0.0, p=1.0, gamma=GAMMA) -> np.ndarray:
     one = np.ones(mesh.nv)
     return conserved(rho * one, u * one, v * one, p * one, gamma)
+
+
+def noh_state(mesh: Mesh, p0: float = 1e-6, gamma: float = 5.0 / 3.0) -> np.ndarray:
+    """Noh's implosion: rho = 1, velocity -r/|r| of unit magnitude towards the origin
+    (zero at the origin), pressure p0; exact solution for gamma = 5/3 in 2-D: a shock
+    at r = t/3 with rho = 16 behind it and rho = 1 + t/r ahead of it."""
+    x, y = mesh.xy[:, 0], mesh.xy[:, 1]
+    r = np.hypot(x, y)
+    rs = np.where(r > 0, r, 1.0)
+    u = np.where(r > 0, -x / rs, 0.0)
+    v = np.where(r > 0, -y / rs, 0.0)
+    return conserved(np.ones(mesh.nv), u, v, np.full(mesh.nv, p0), gamma)
 
 
 def vortex_primitives(x, y, t=0.0, beta=5.0, scale=10.0, u0=1.0, v0=1.0, Lx=1.0, Ly=1.0,

@@ -120,3 +120,20 @@ def test_boundary_changes_and_limits(rd):
     with pytest.raises(binding.RDError) as e:
         s.adjoint_forward(3)
     assert e.value.status == binding.RD_ENOTSUP
+
+
+@pytest.mark.parametrize("scheme,steps", [("N1", 100), ("B2", 100), ("BMAX2", 100)])
+def test_noh_quadrant(rd, scheme, steps):
+    """Noh's implosion (gamma = 5/3, p0 = 1e-6) with walls on the symmetry lines and
+    ghost inflow on the far sides, against the oracle at 1e-12."""
+    _, binding = rd
+    mesh = inputs.noh_quadrant(40, relabel_seed=1)
+    W0 = inputs.noh_state(mesh)
+    m = binding.Mesh(mesh)
+    s = binding.State(m, W0, scheme=scheme, gamma=5.0 / 3.0)
+    assert s.run(steps) == steps
+    Wld, _ = oracle.run(mesh, W0, scheme, nsteps=steps, gamma=5.0 / 3.0, nthreads=NTH, long_double=True)
+    Wd, _ = oracle.run(mesh, W0, scheme, nsteps=steps, gamma=5.0 / 3.0, nthreads=NTH)
+    err, floor = rel_max_err(s.get(), Wld), rel_max_err(Wd, Wld)
+    print(f"Noh {scheme}: {err:.2e} (oracle floor {floor:.2e})")
+    assert err < TOL

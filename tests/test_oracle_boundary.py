@@ -137,3 +137,29 @@ def test_wall_split_conserves_the_correction():
         out[alpha] = (W, oracle.conserved(m, W))
     assert np.allclose(out[0.75][1], out[0.5][1], rtol=1e-14, atol=1e-16)
     assert np.abs(out[0.75][0] - out[0.5][0]).max() > 1e-9        # but the split itself differs
+
+
+def test_noh_implosion_against_its_exact_solution():
+    """Noh's problem (Sec. 5.2, gamma = 5/3) on the quadrant with reflecting walls on the
+    symmetry lines and ghost inflow boundaries: with the first-order N scheme the shock
+    stands at r = t/3, the inflow ahead of it is compressed to 1 + t/r, and the post-shock
+    plateau approaches 16 (first order: within 12 %; wall heating lowers it near the origin)."""
+    T, g = 0.6, 5.0 / 3.0
+    m = inputs.noh_quadrant(60, relabel_seed=3)
+    W0 = inputs.noh_state(m)
+    n = int(np.ceil(T / oracle.time_step(m, W0, gamma=g)))
+    W, _ = oracle.run(m, W0, "N1", nsteps=n, dt_fixed=np.full(n, T / n), gamma=g, nthreads=4)
+    rho = W[0]
+    r = np.hypot(m.xy[:, 0], m.xy[:, 1])
+    rs = T / 3
+    plateau = (r > 0.3 * rs) & (r < 0.8 * rs)
+    assert abs(rho[plateau].mean() - 16.0) < 0.12 * 16.0
+    ahead = (r > 1.3 * rs) & (r < 0.35)
+    assert np.abs(np.mean(rho[ahead] / (1 + T / r[ahead])) - 1.0) < 0.06
+    # shock radius: the mid-density crossing of the radially binned profile
+    bins = np.linspace(0.0, 0.5, 51)
+    idx = np.digitize(r, bins)
+    prof = np.array([rho[idx == k].mean() for k in range(1, len(bins))])
+    mid = 0.5 * (bins[1:] + bins[:-1])
+    k = np.where((prof[:-1] - 8.5) * (prof[1:] - 8.5) <= 0)[0][0]
+    assert abs(mid[k] - rs) < 0.03
