@@ -28,8 +28,8 @@ struct rd_meshgen {
   double unit = 0.0;  // length of one grid unit
   int32_t cap_v = 0, cap_t = 0, nv = 0, nt = 0;
   int32_t rounds = 0, flips = 0, deferred = 0;
-  DevBuf vx, vy, tv, ts, tn, tc;         // mesh
-  DevBuf flag, offs, cand, ctri, cedge, cpt, lock, win, part, total;
+  DevBuf vx, vy, tv, ts, tn, tc, dirty;  // mesh
+  DevBuf flag, offs, cand, ctri, cedge, cpt, lock, win, part, total, nflips;
   double ms[5] = {0, 0, 0, 0, 0};        // quality+locate, cavities, insertion, flips, total
   Mesh dev() const {
     Mesh m;
@@ -39,6 +39,7 @@ struct rd_meshgen {
     m.ts = (int8_t*)ts.p;
     m.tn = (int32_t*)tn.p;
     m.tc = (int8_t*)tc.p;
+    m.dirty = (uint8_t*)dirty.p;
     m.Px = Px;
     m.Py = Py;
     return m;
@@ -183,14 +184,17 @@ __global__ void k_insert(Mesh m, int nc, const int* __restrict__ win, const int*
 // ---------------------------------------------------------------------------
 // Delaunay restoration by parallel flips (Sec. 2.4.6, Sec. 4.1.4)
 // ---------------------------------------------------------------------------
-// flag[t] = 1 + k for the first edge of t (shared with a higher-numbered
-// triangle) that is not locally Delaunay, 0 if none
+// flag[t] = 1 + k for the first edge of a rewritten triangle t that is not
+// locally Delaunay, 0 if none; t stays marked while it has such an edge
 __global__ void k_edge_check(Mesh m, int nt, int* __restrict__ flag) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
   int f = 0;
-  for (int k = 0; k < 3 && !f; ++k)
-    if (edge_bad(m, t, k)) f = 1 + k;
+  if (m.dirty[t]) {
+    for (int k = 0; k < 3 && !f; ++k)
+      if (edge_bad(m, t, k)) f = 1 + k;
+    m.dirty[t] = f ? 1 : 0;
+  }
   flag[t] = f;
 }
 
@@ -235,10 +239,12 @@ __global__ void k_flip_win(Mesh m, int nt, const int* __restrict__ flag, const u
   win[t] = w;
 }
 
-__global__ void k_flip(Mesh m, int nt, const int* __restrict__ flag, const int* __restrict__ win) {
+__global__ void k_flip(Mesh m, int nt, const int* __restrict__ flag, const int* __restrict__ win,
+                       unsigned long long* __restrict__ nflips) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt || !win[t]) return;
   flip(m, t, flag[t] - 1);
+  atomicAdd(nflips, 1ull);
 }
 
 inline unsigned nb(int n) { return (unsigned)((n + BLK - 1) / BLK); }
@@ -250,31 +256,18 @@ int restore_delaunay(rd_meshgen* g, uint32_t& round_id, int max_rounds) {
   for (int r = 0; r < max_rounds; ++r) {
     const int nt = g->nt;
     k_edge_check<<<nb(nt), BLK, 0, st>>>(m, nt, (int*)g->flag.p);
-    // count the bad edges (flags > 0) through the win buffer
+    int nbad = 0;  // sum of the flags: nonzero iff a rewritten triangle has a non-Delaunay edge
+    CK(scan(g, nt, &nbad));
+    if (nbad == 0) return RD_OK;
     CU(cudaMemsetAsync(g->lock.p, 0, (size_t)nt * sizeof(unsigned long long), st));
     k_flip_lock<<<nb(nt), BLK, 0, st>>>(m, nt, (const int*)g->flag.p, (unsigned long long*)g->lock.p, g->p.seed,
                                         round_id);
     k_flip_win<<<nb(nt), BLK, 0, st>>>(m, nt, (const int*)g->flag.p, (const unsigned long long*)g->lock.p, g->p.seed,
                                        round_id, (int*)g->win.p);
-    k_flip<<<nb(nt), BLK, 0, st>>>(m, nt, (const int*)g->flag.p, (const int*)g->win.p);
+    k_flip<<<nb(nt), BLK, 0, st>>>(m, nt, (const int*)g->flag.p, (const int*)g->win.p,
+                                   (unsigned long long*)g->nflips.p);
     CU(cudaGetLastError());
     ++round_id;
-    // number of flips done this round
-    std::swap(g->flag, g->win);
-    int nflip = 0;
-    const int rc = scan(g, nt, &nflip);
-    std::swap(g->flag, g->win);
-    CK(rc);
-    g->flips += nflip;
-    if (nflip == 0) {
-      // no winner: either no bad edge is left, or every bad edge is blocked
-      k_edge_check<<<nb(nt), BLK, 0, st>>>(m, nt, (int*)g->flag.p);
-      int nbad = 0;
-      CK(scan(g, nt, &nbad));
-      if (nbad == 0) return RD_OK;
-      // bad edges whose six triangles are not distinct cannot flip (tiny periodic meshes)
-      return RD_EINVAL;
-    }
   }
   return RD_ETIMEOUT;
 }
@@ -354,6 +347,10 @@ int run(rd_meshgen* g) {
   CK(upload(g->ts, ts, 6 * ct, st));
   CK(upload(g->tn, tn, 3 * ct, st));
   CK(upload(g->tc, tc, 3 * ct, st));
+  CK(dev_alloc(g->dirty, ct, st));
+  CU(cudaMemsetAsync(g->dirty.p, 1, ct, st));  // every initial triangle is checked
+  CK(dev_alloc(g->nflips, sizeof(unsigned long long), st));
+  CU(cudaMemsetAsync(g->nflips.p, 0, sizeof(unsigned long long), st));
   CK(dev_alloc(g->flag, ct * sizeof(int), st));
   CK(dev_alloc(g->offs, ct * sizeof(int), st));
   CK(dev_alloc(g->win, ct * sizeof(int), st));
@@ -433,6 +430,8 @@ int run(rd_meshgen* g) {
   cudaEventRecord(e[4], st);
   cudaEventSynchronize(e[4]);
   g->ms[4] = elapsed(5, 4);
+  unsigned long long nfl = 0;
+  if (cudaMemcpy(&nfl, g->nflips.p, sizeof(nfl), cudaMemcpyDeviceToHost) == cudaSuccess) g->flips = (int32_t)nfl;
   for (auto& x : e) cudaEventDestroy(x);
   dev_free(centre);
   return rc;
@@ -528,8 +527,8 @@ extern "C" int rd_meshgen_domain(const rd_meshgen* g, double* Lx, double* Ly, in
 extern "C" void rd_meshgen_destroy(rd_meshgen* g) {
   if (!g) return;
   if (g->stream) cudaStreamSynchronize(g->stream);
-  DevBuf* bufs[] = {&g->vx, &g->vy, &g->tv, &g->ts, &g->tn, &g->tc, &g->flag, &g->offs, &g->cand,
-                    &g->ctri, &g->cedge, &g->cpt, &g->lock, &g->win, &g->part, &g->total};
+  DevBuf* bufs[] = {&g->vx, &g->vy, &g->tv, &g->ts, &g->tn, &g->tc, &g->dirty, &g->flag, &g->offs, &g->cand,
+                    &g->ctri, &g->cedge, &g->cpt, &g->lock, &g->win, &g->part, &g->total, &g->nflips};
   for (DevBuf* b : bufs) dev_free(*b);
   if (g->own_stream) cudaStreamDestroy(g->stream);
   delete g;

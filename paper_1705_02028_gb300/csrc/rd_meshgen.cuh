@@ -44,6 +44,7 @@ struct Mesh {
   int8_t* ts;       // [cap_t][3][2] image shift of each corner, in {0, 1}
   int32_t* tn;      // [cap_t][3] neighbour across the edge opposite each corner
   int8_t* tc;       // [cap_t][3] that edge's corner index in the neighbour
+  uint8_t* dirty;   // [cap_t] 1: triangle rewritten since its edges were last found Delaunay (nullable)
   int64_t Px, Py;   // periods in units
 };
 
@@ -212,6 +213,7 @@ MG_HD void write_triangle(Mesh& m, int32_t t, const int32_t v[3], const int8_t s
                           const int8_t nc[3]) {
   int8_t sh[6] = {s[0], s[1], s[2], s[3], s[4], s[5]};
   normalise_shifts(sh);
+  if (m.dirty) m.dirty[t] = 1;
   for (int k = 0; k < 3; ++k) {
     m.tv[3 * (size_t)t + k] = v[k];
     m.tn[3 * (size_t)t + k] = nb[k];
@@ -322,11 +324,14 @@ MG_HD void split4(Mesh& m, int32_t t, int k, int32_t pv, P64 p, int32_t t1, int3
   m.tc[3 * (size_t)o_ad + c_ad] = 1;
 }
 
-// Is the edge opposite corner k of t (shared with n = tn[t][k], t < n) not
-// locally Delaunay (Sec. 2.4.6)?  The far vertex of n is tested against t's circumcircle.
+// Is the edge opposite corner k of t (shared with n = tn[t][k]) not locally
+// Delaunay (Sec. 2.4.6)?  The far vertex of n is tested against t's
+// circumcircle.  An edge can only turn non-Delaunay when one of its two
+// triangles is rewritten, so the flip rounds test the edges of rewritten
+// ("dirty") triangles only -- from either side, as Sec. 4.1.1 restricts the
+// checks to edges of the cavities and new edges.
 MG_HD bool edge_bad(const Mesh& m, int32_t t, int k) {
   const int32_t n = m.tn[3 * (size_t)t + k];
-  if (n <= t) return false;
   const int j = m.tc[3 * (size_t)t + k];
   const P64 off = frame_offset(m, t, k);
   P64 d = corner(m, n, j);
