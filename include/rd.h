@@ -39,7 +39,7 @@ extern "C" {
 #define RD_ENONPHYSICAL 4  /* rho<=0, p<=0, Roe c^2<=0, singular N^ or NaN;
                               the state stays at the last good step           */
 #define RD_ETIMEOUT 5      /* a bounded device-side wait expired              */
-#define RD_ENOTSUP 6       /* option not supported by this build              */
+#define RD_ENOTSUP 6       /* combination of options the library does not offer */
 
 /* ---- schemes (Sec. 3.3, Sec. 3.4; labels as in the paper's figures) ------ */
 #define RD_N1 0   /* N scheme, forward Euler (first order in space and time)    */

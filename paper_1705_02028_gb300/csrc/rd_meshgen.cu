@@ -29,7 +29,7 @@ struct rd_meshgen {
   int32_t cap_v = 0, cap_t = 0, nv = 0, nt = 0;
   int32_t rounds = 0, flips = 0, deferred = 0;
   DevBuf vx, vy, tv, ts, tn, tc, dirty;  // mesh
-  DevBuf flag, offs, cand, ctri, cedge, cpt, lock, win, part, total, nflips;
+  DevBuf flag, offs, ctri, cedge, cpt, lock, win, part, total, nflips;
   double ms[5] = {0, 0, 0, 0, 0};        // quality+locate, cavities, insertion, flips, total
   Mesh dev() const {
     Mesh m;
@@ -123,16 +123,16 @@ __global__ void k_quality(Mesh m, int nt, double R_units, double B, int* __restr
   if (bad) centre[t] = c;
 }
 
-// compacted candidates: cand[i] = bad triangle, its circumcentre located
+// compacted candidates: the circumcentre of the i-th bad triangle, located
+// (containing triangle ctri[i], edge cedge[i] if on one, point cpt[i] in its frame)
 __global__ void k_locate(Mesh m, int nt, const int* __restrict__ flag, const int* __restrict__ offs,
-                         const P64* __restrict__ centre, int* __restrict__ cand, int* __restrict__ ctri,
-                         int* __restrict__ cedge, P64* __restrict__ cpt) {
+                         const P64* __restrict__ centre, int* __restrict__ ctri, int* __restrict__ cedge,
+                         P64* __restrict__ cpt) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt || !flag[t]) return;
   const int i = offs[t];
   P64 p = centre[t];
   int edge = -1;
-  cand[i] = t;
   ctri[i] = locate(m, t, p, edge);
   cedge[i] = edge;
   cpt[i] = p;
@@ -354,7 +354,6 @@ int run(rd_meshgen* g) {
   CK(dev_alloc(g->flag, ct * sizeof(int), st));
   CK(dev_alloc(g->offs, ct * sizeof(int), st));
   CK(dev_alloc(g->win, ct * sizeof(int), st));
-  CK(dev_alloc(g->cand, ct * sizeof(int), st));
   CK(dev_alloc(g->ctri, ct * sizeof(int), st));
   CK(dev_alloc(g->cedge, ct * sizeof(int), st));
   CK(dev_alloc(g->cpt, ct * sizeof(P64), st));
@@ -388,7 +387,7 @@ int run(rd_meshgen* g) {
       break;
     }
     k_locate<<<nb(nt), BLK, 0, st>>>(m, nt, (const int*)g->flag.p, (const int*)g->offs.p, (const P64*)centre.p,
-                                     (int*)g->cand.p, (int*)g->ctri.p, (int*)g->cedge.p, (P64*)g->cpt.p);
+                                     (int*)g->ctri.p, (int*)g->cedge.p, (P64*)g->cpt.p);
     cudaEventRecord(e[1], st);
     CU(cudaMemsetAsync(g->lock.p, 0, (size_t)nt * sizeof(unsigned long long), st));
     k_cavity_lock<<<nb(nc), BLK, 0, st>>>(m, nc, (const int*)g->ctri.p, (const int*)g->cedge.p,
@@ -527,7 +526,7 @@ extern "C" int rd_meshgen_domain(const rd_meshgen* g, double* Lx, double* Ly, in
 extern "C" void rd_meshgen_destroy(rd_meshgen* g) {
   if (!g) return;
   if (g->stream) cudaStreamSynchronize(g->stream);
-  DevBuf* bufs[] = {&g->vx, &g->vy, &g->tv, &g->ts, &g->tn, &g->tc, &g->dirty, &g->flag, &g->offs, &g->cand,
+  DevBuf* bufs[] = {&g->vx, &g->vy, &g->tv, &g->ts, &g->tn, &g->tc, &g->dirty, &g->flag, &g->offs,
                     &g->ctri, &g->cedge, &g->cpt, &g->lock, &g->win, &g->part, &g->total, &g->nflips};
   for (DevBuf* b : bufs) dev_free(*b);
   if (g->own_stream) cudaStreamDestroy(g->stream);
