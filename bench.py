@@ -491,6 +491,22 @@ def adjoint_measure(args, ws, n_steps=200, ckpt_every=20):
             "cost_vs_plain_step": (t_fwd + t_bwd) / t_plain, "grad_norm": float(np.linalg.norm(g))}
 
 
+def host_cpu():
+    """CPU model and logical core count of the host the oracle runs on."""
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"model": model, "machine": platform.machine(), "logical_cpus": os.cpu_count()}
+
+
 def sample_mesh(workload):
     """1024^2 periodic mesh of the workload's kind (1/16 of a 4096^2 workload's triangles)."""
     from paper_1705_02028_gb300 import inputs
@@ -523,7 +539,7 @@ def cpu_baseline(args):
     if secs < 8.0:  # aim for ~10-30 s of CPU work
         extra = max(1, int(10.0 / max(secs / 2, 1e-3)))
         rate, secs, nts = oracle_sample_rate(args.workload, scheme, min(extra, 40), nth)
-    return {"value": rate, "unit": UNIT, "cores": nth, "kind": "oracle", "seconds": secs,
+    return {"value": rate, "unit": UNIT, "cores": nth, "kind": "oracle", "seconds": secs, "host": host_cpu(),
             "sample": f"{scheme} steps of the KHI state on a 1024x1024 periodic mesh ({nts} triangles, "
                       f"1/16 of the workload, {WORKLOADS[args.workload][3]} mesh), FP64 C++ oracle, OpenMP over {nth} host threads"}
 
@@ -552,7 +568,8 @@ def reference(args, ws, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "triangles_per_sample_step": mesh.nt, "scheme": scheme},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nth, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nth, "kind": "oracle", "sample": sample,
+                             "host": host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
