@@ -336,9 +336,36 @@ int rd_probe_fma_peak(int32_t precision, double *flops_per_s);
 /* Launch-shape autotuner of one state: times one uncommitted step (the
  * committed state is not changed) for triangle-kernel blocks of 64, 128, 192,
  * 256 threads and vertex-kernel blocks of 128, 256, 512 and keeps the
- * fastest; returns the choice (either pointer may be NULL).  Results do not
+ * fastest; then, on meshes of at least 4096 triangles created with a
+ * reordering, times the tiled step (rd_state_set_tiling) for a few tile sizes
+ * and keeps it if it is faster.  Returns the block choice (either pointer may
+ * be NULL; the tiling is read with rd_state_get_tiling).  Results do not
  * depend on the launch shape (every sum has a fixed order). */
 int rd_state_autotune(rd_state *s, int32_t *tri_block, int32_t *vtx_block);
+
+/* Tiled step (Sec. 3.3-3.4 and Eqs. eqRK1/eqRK2 computed as in rd_step; the
+ * distribution of Sec. 4.2.1 done on chip).  The triangles, in the mesh
+ * store's order (sorted by smallest internal vertex id), are cut into tiles of
+ * tile_triangles consecutive triangles, each processed by one thread block of
+ * `threads` threads.  The block keeps its triangles' corner shares in shared
+ * memory and sums them for every vertex whose triangles all lie in the tile;
+ * only the shares of the other (boundary) vertices go through device memory.
+ * Stage 2 and the final update are fused the same way for the two-stage
+ * schemes except RD_BX2 and on meshes without walls or ghost vertices (those
+ * keep the per-triangle stage 2).  Every sum keeps the CSR order, so states
+ * are bitwise identical to the untiled step's.
+ *   tile_triangles: 0 (untiled, the default) or a multiple of 32 in
+ *                   [32, 4096]; threads: a multiple of 32 in [32, 256].
+ * Errors: RD_EINVAL for values out of range; RD_ENOTSUP when the mesh was
+ * created with RD_ORDER_NONE (its triangles are not sorted), a tile would
+ * touch more than 65535 vertices, or its shared memory exceeds the device's
+ * per-block limit.  The host builds the tile plan (O(n_tri log) work) and
+ * uploads it; the state's captured graph is rebuilt on the next rd_run. */
+int rd_state_set_tiling(rd_state *s, int32_t tile_triangles, int32_t threads);
+/* Current tiling (0, 0, 0 when untiled) and the number of boundary vertices;
+ * any pointer may be NULL. */
+int rd_state_get_tiling(const rd_state *s, int32_t *tile_triangles, int32_t *threads,
+                        int32_t *n_boundary_vertices);
 
 /* ---- batched form: many independent meshes, one graph launch -------------
  * rd_batch_create: n_mesh (1..65535) meshes created on the same stream, with

@@ -95,6 +95,8 @@ _SIGS = {
     "rd_batch_get_dt": (ctypes.c_int, [_vp, _dp]),
     "rd_batch_destroy": (None, [_vp]),
     "rd_state_autotune": (ctypes.c_int, [_vp, _i32p, _i32p]),
+    "rd_state_set_tiling": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
+    "rd_state_get_tiling": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p]),
     "rd_adjoint_forward": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _dp]),
     "rd_adjoint_backward": (ctypes.c_int, [_vp, _dp, _dp]),
     "rd_run_fixed_dt": (ctypes.c_int, [_vp, ctypes.c_int32, _dp]),
@@ -367,6 +369,17 @@ class State:
         tb, vb = ctypes.c_int32(), ctypes.c_int32()
         _check(_lib.rd_state_autotune(self.handle, ctypes.byref(tb), ctypes.byref(vb)), "rd_state_autotune")
         return tb.value, vb.value
+
+    def set_tiling(self, tile_triangles: int, threads: int = 128):
+        """Tiled step with tiles of `tile_triangles` triangles (0: untiled); rd_state_set_tiling."""
+        _check(_lib.rd_state_set_tiling(self.handle, int(tile_triangles), int(threads)), "rd_state_set_tiling")
+
+    def tiling(self):
+        """(tile_triangles, threads, boundary vertices) of the current tiling; zeros when untiled."""
+        tt, bt, nb = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.rd_state_get_tiling(self.handle, ctypes.byref(tt), ctypes.byref(bt), ctypes.byref(nb)),
+               "rd_state_get_tiling")
+        return tt.value, bt.value, nb.value
 
     def close(self):
         if getattr(self, "handle", None):

@@ -16,6 +16,7 @@
 #include "rd_device.h"
 #include "rd_internal.h"
 #include "rd_kernels.cuh"
+#include "rd_tiled.h"
 
 using namespace rd;
 
@@ -226,16 +227,9 @@ __global__ void k_fix_dt(DevCtl* ctl, double dt) {
   if (!ctl->stop) ctl->dt = dt;
 }
 
-// Blend configuration of a state's two-stage triangle kernels (Sec. 3.3.3, Sec. 3.4).
 template <class T>
 BlendArgs<T> blend_args(const rd_state* s) {
-  BlendArgs<T> ba;
-  ba.mode = s->p.scheme == RD_BMAX2 ? BLEND_MAX : s->p.scheme == RD_BMIN2 ? BLEND_MIN
-            : s->p.scheme == RD_BX2 ? BLEND_X : BLEND_B;
-  ba.sl = s->p.lumping == RD_LUMP_SELECTIVE;
-  double L = s->m->h.Lx > s->m->h.Ly ? s->m->h.Lx : s->m->h.Ly;
-  ba.L = (T)(L > 0.0 ? L : 1.0);
-  return ba;
+  return tile_blend_args<T>(s);
 }
 
 template <class T>
@@ -280,6 +274,10 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
   ba1.vr = vr0;
   ba2.vr = vr1;
   mark(0);
+  const bool tiled = s->tiles != nullptr;
+  if (tiled) {
+    CK(tiled_stage1<T>(s, a, ev));
+  } else {
   switch (s->p.scheme) {
     case RD_N1:
       k_tri_stage1<T, RD_N1><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, nullptr, cf, ctl);
@@ -298,6 +296,7 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
   }
   mark(1);
   launch_gather_cfl<T>(VB, st, nv, ptr, ent, share, cf, V, (T*)s->R1.p, (T*)s->partial.p, cfl, ctl);
+  }
   if (fixed_dt > 0.0) k_fix_dt<<<1, 1, 0, st>>>(ctl, fixed_dt);
   mark(2);
   if (s->p.scheme == RD_N1) {
@@ -306,6 +305,10 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
                                           nullptr, wa1, ga);
     mark(3);
     mark(4);
+    mark(5);
+  } else if (tiled && tiled_stage2_applies(s)) {
+    mark(3);
+    CK(tiled_stage2<T>(s, a, ev));
     mark(5);
   } else {
     if (vr1) k_vr_reset<<<1, 1, 0, st>>>(vr1, ctl, 0);
@@ -632,9 +635,28 @@ extern "C" int rd_state_autotune(rd_state* s, int32_t* tri_block, int32_t* vtx_b
     if (rc != RD_OK || (rc = time_step(best_t, vb, ms)) != RD_OK) break;
     if (ms < best) { best = ms; best_v = vb; }
   }
-  for (auto& e : ev) cudaEventDestroy(e);
   s->tri_block = best_t;
   s->vtx_block = best_v;
+  // tiled step: a few tile sizes against the untiled step with the shapes above
+  if (rc == RD_OK && s->m->h.nt >= 4096) {
+    float untiled = 1e30f;
+    rc = rd_state_set_tiling(s, 0, 0);
+    if (rc == RD_OK) rc = time_step(best_t, best_v, untiled);
+    const int c32[][2] = {{256, 128}, {512, 128}, {512, 256}, {1024, 256}};
+    const int c64[][2] = {{128, 64}, {256, 64}, {256, 128}};
+    const int nc = s->pi == 0 ? 3 : 4;
+    int best_tt = 0, best_bt = 0;
+    float best_tiled = untiled;
+    for (int k = 0; k < nc && rc == RD_OK; ++k) {
+      const int tt = s->pi == 0 ? c64[k][0] : c32[k][0], bt = s->pi == 0 ? c64[k][1] : c32[k][1];
+      int r = rd_state_set_tiling(s, tt, bt);
+      if (r == RD_ENOTSUP) break;  // this mesh has no tile plan
+      if ((rc = r) != RD_OK || (rc = time_step(best_t, best_v, ms)) != RD_OK) break;
+      if (ms < best_tiled) { best_tiled = ms; best_tt = tt; best_bt = bt; }
+    }
+    if (rc == RD_OK) rc = rd_state_set_tiling(s, best_tt, best_bt);
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
   if (s->g2) {  // the captured graph holds the old launch shapes
     cudaGraphExecDestroy(s->g2);
     s->g2 = nullptr;
@@ -748,6 +770,7 @@ extern "C" void rd_state_destroy(rd_state* s) {
                     &s->cons_partial, &s->cons_out, &s->stage, &s->vr, &s->ghostW};
   for (DevBuf* b : bufs) dev_free(*b);
   adjoint_free(s->adj);
+  tile_plan_free(s->tiles);
   delete s;
 }
 

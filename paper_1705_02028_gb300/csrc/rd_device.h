@@ -47,6 +47,24 @@ template <class T>
 void launch_gather_cfl(int vblock, cudaStream_t st, int nv, const int* ptr, const int* ent, const T* share,
                        const T* cfl, const T* V, T* R1, T* partial, T cflnum, DevCtl* ctl);
 
+// Tiled step (rd_state_set_tiling).  Triangles, sorted by their smallest
+// vertex id, are cut into tiles of tt consecutive triangles; tile p owns the
+// vertex range [vs[p], vs[p+1]) (vs[p] = smallest vertex of triangle p tt).
+// A vertex all of whose triangles lie in its own tile is interior and is
+// gathered on chip; the others (boundary vertices) through global memory.
+struct TilePlan {
+  int tt = 0, bt = 0;     // triangles per tile, threads per block
+  int n_tiles = 0, n_bvert = 0;
+  int slots = 0;          // max over tiles of owned + halo vertices
+  DevBuf vs;              // [n_tiles + 1] int32 vertex range of each tile
+  DevBuf hptr, hlist;     // [n_tiles + 1], halo vertex ids (ascending per tile)
+  DevBuf lslot;           // [3][nt] uint16: slot of each corner in its tile
+  DevBuf bmask;           // [nt] uint8: bit c = corner c is a boundary vertex
+  DevBuf bvert;           // [n_bvert] int32 boundary vertices, ascending
+  DevBuf partial;         // dt block minima: tiles, then boundary blocks (8 B each)
+};
+void tile_plan_free(TilePlan* tp);
+
 }  // namespace rd
 
 struct rd_adjoint_store;
@@ -100,6 +118,7 @@ struct rd_state {
   bool bc_init = false;
   long long launched = 0;  // host view of the committed step count (parity of the buffers)
   int tri_block = rd::TRI_BLOCK, vtx_block = rd::VTX_BLOCK;  // launch shapes (autotuned)
+  rd::TilePlan* tiles = nullptr;  // tiled step (nullptr: per-triangle share arrays)
   cudaGraphExec_t g2 = nullptr;  // two steps (even -> odd -> even)
   bool graph_failed = false;
   rd_adjoint_store* adj = nullptr;  // checkpoints and buffers of the adjoint rollout

@@ -792,13 +792,65 @@ __device__ __forceinline__ void gather_corners(int e0, int e1, const int* __rest
   }
 }
 
+// Block minimum of v (every thread of the block calls it; blockDim.x a
+// multiple of 32, at most 1024); the result is valid in thread 0.
+template <class T>
+__device__ __forceinline__ T block_min(T v) {
+  __shared__ T red_min[32];
+  v = warp_min(v);
+  if ((threadIdx.x & 31) == 0) red_min[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T x = T(INFINITY);
+  if (threadIdx.x < 32) {
+    x = threadIdx.x < (blockDim.x >> 5) ? red_min[threadIdx.x] : T(INFINITY);
+    x = warp_min(x);
+  }
+  return x;
+}
+
+// Second level of the dt reduction: each block stores its minimum of
+// 2 V_i / sigma_i in partial[slot]; the last of the gridDim.x blocks to finish
+// (ticket in the control block) takes the minimum over partial[0, count) and
+// sets dt = CFL * min, clipped to t_end.  Every thread of the block calls it.
+template <class T>
+__device__ __forceinline__ void dt_finish(T ratio, T* __restrict__ partial, int slot, int count, T cflnum,
+                                          DevCtl* ctl) {
+  __shared__ bool last;
+  T x = block_min(ratio);
+  if (threadIdx.x == 0) {
+    partial[slot] = x;
+    __threadfence();
+    unsigned int tk = atomicAdd(&ctl->ticket, 1u);
+    last = (tk == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  // last block: min over all block minima
+  __threadfence();
+  T m = T(INFINITY);
+  for (int b = threadIdx.x; b < count; b += blockDim.x) {
+    T y = ((volatile T*)partial)[b];
+    m = y < m ? y : m;
+  }
+  __syncthreads();  // red_min of the first block_min is read before it is reused
+  m = block_min(m);
+  if (threadIdx.x == 0) {
+    double dt = (double)(cflnum * m);
+    if (ctl->t_end > 0.0) {
+      double rem = ctl->t_end - ctl->t;
+      if (dt > rem) dt = rem;
+      if (!(rem > 0.0)) ctl->stop = 1;  // t_end reached: the rest of this step is a no-op
+    }
+    ctl->dt = (double)(T)dt;
+    ctl->ticket = 0u;
+  }
+}
+
 template <class T, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_gather_cfl(int nv, const int* __restrict__ ptr, const int* __restrict__ ent,
                                                       const T* __restrict__ share, const T* __restrict__ cfl,
                                                       const T* __restrict__ V, T* __restrict__ R1,
                                                       T* __restrict__ partial, T cflnum, DevCtl* ctl) {
-  __shared__ T red[BLOCK / 32];
-  __shared__ bool last;
   if (ctl->stop) return;
   int i = blockIdx.x * BLOCK + threadIdx.x;
   T ratio = T(INFINITY);
@@ -809,45 +861,7 @@ __global__ void __launch_bounds__(BLOCK) k_gather_cfl(int nv, const int* __restr
     st4(R1 + 4 * (size_t)i, r);
     ratio = T(2) * __ldg(V + i) / sig;
   }
-  ratio = warp_min(ratio);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ratio;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    T x = threadIdx.x < BLOCK / 32 ? red[threadIdx.x] : T(INFINITY);
-    x = warp_min(x);
-    if (threadIdx.x == 0) {
-      partial[blockIdx.x] = x;
-      __threadfence();
-      unsigned int tk = atomicAdd(&ctl->ticket, 1u);
-      last = (tk == gridDim.x - 1);
-    }
-  }
-  __syncthreads();
-  if (!last) return;
-  // last block: min over all block minima
-  __threadfence();
-  T m = T(INFINITY);
-  for (int b = threadIdx.x; b < gridDim.x; b += BLOCK) {
-    T x = ((volatile T*)partial)[b];
-    m = x < m ? x : m;
-  }
-  m = warp_min(m);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    T x = threadIdx.x < BLOCK / 32 ? red[threadIdx.x] : T(INFINITY);
-    x = warp_min(x);
-    if (threadIdx.x == 0) {
-      double dt = (double)(cflnum * x);
-      if (ctl->t_end > 0.0) {
-        double rem = ctl->t_end - ctl->t;
-        if (dt > rem) dt = rem;
-        if (!(rem > 0.0)) ctl->stop = 1;  // t_end reached: the rest of this step is a no-op
-      }
-      ctl->dt = (double)(T)dt;
-      ctl->ticket = 0u;
-    }
-  }
+  dt_finish(ratio, partial, blockIdx.x, gridDim.x, cflnum, ctl);
 }
 
 // Vertex state -> parameter vector Z and |v| + c; returns false if non-physical.
