@@ -367,9 +367,13 @@ DevGeo<T> geo_view(const rd_mesh* m) {
 }
 
 // Opt every instantiation of a precision into the dynamic shared memory it
-// needs (above the 48 KB default).
+// needs (above the 48 KB default).  The limits only grow, so that the plans of
+// other states stay launchable.
 template <class T>
 int tile_smem_attrs(size_t b1, size_t b2) {
+  static size_t lim1 = 0, lim2 = 0;
+  b1 = std::max(b1, lim1);
+  b2 = std::max(b2, lim2);
   CU(cudaFuncSetAttribute(k_tile_stage1<T, RD_N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1));
   CU(cudaFuncSetAttribute(k_tile_stage1<T, RD_LDA2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1));
   CU(cudaFuncSetAttribute(k_tile_stage1<T, RD_B2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1));
@@ -377,6 +381,8 @@ int tile_smem_attrs(size_t b1, size_t b2) {
   CU(cudaFuncSetAttribute(k_tile_stage2<T, RD_LDA2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b2));
   CU(cudaFuncSetAttribute(k_tile_stage2<T, RD_B2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b2));
   CU(cudaFuncSetAttribute(k_tile_stage2<T, RD_BMAX2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b2));
+  lim1 = b1;
+  lim2 = b2;
   return RD_OK;
 }
 
