@@ -75,6 +75,12 @@ def kernel_alg_bytes(kernel: str, scheme: str, s: int) -> float:
         return geo + 0.5 * 5 * s + 12 * s + rec + s      # Z, |v|+c in; shares, rec, cfl out
     if kernel == "tri_stage2":
         return geo + 0.5 * 12 * s + 16 * s + 12 * s      # Z*, W^n, W* in; rec in; shares out
+    # tiled step: corner slots (3 x uint16) instead of ids, the CSR read once, no share arrays
+    tgeo, csr = 11 * s + 6, 0.5 * 4 + 12
+    if kernel == "tile_stage1":
+        return tgeo + 0.5 * 5 * s + 16 * s + 0.5 * 5 * s + csr   # Z, |v|+c in; rec out; R1 out, V in
+    if kernel == "tile_stage2":
+        return tgeo + 0.5 * 9 * s + 16 * s + 0.5 * 9 * s + csr   # W^n, R1, V in; rec in; W, Z, |v|+c out
     raise KeyError(kernel)
 
 
@@ -205,6 +211,13 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def tiling_info(t):
+    """Tiled-step choice of the autotuner (rd_state_get_tiling), None when untiled."""
+    if not t or not t[0]:
+        return None
+    return {"tile_triangles": t[0], "threads": t[1], "boundary_vertices": t[2]}
+
+
 def ncu_traffic(workload, precision, kernel, nt):
     """DRAM bytes per launch of a kernel from the committed ncu summary, scaled to nt
     triangles; None when missing or taken on a different kernel source."""
@@ -223,6 +236,7 @@ def run_state_timing(binding, mesh_dev, W0, scheme, precision, steps, warmup, ws
     import torch
     s = binding.State(mesh_dev, W0, scheme=scheme, precision=precision)
     s.shapes = s.autotune() if autotune else None
+    s.tiles = s.tiling()
     s.run(warmup)
     st = mesh_dev.stream
     torch.cuda.synchronize()
@@ -295,8 +309,8 @@ def ours(args, ws, rank, local):
     # roofline of the dominant kernel
     dom = max(per_kernel, key=per_kernel.get)
     dom_ms = per_kernel[dom]
-    stage = 1 if dom == "tri_stage1" else 2
-    if args.precision == "fp64" and dom in ("tri_stage1", "tri_stage2"):
+    stage = 1 if dom in ("tri_stage1", "tile_stage1") else 2
+    if args.precision == "fp64" and dom in ("tri_stage1", "tri_stage2", "tile_stage1", "tile_stage2"):
         fl = binding.count_flops(flop_scheme(scheme), stage)["total"]
         peak = binding.probe_fma_peak("fp64")
         achieved = fl * nt / (dom_ms * 1e-3)
@@ -308,7 +322,7 @@ def ours(args, ws, rank, local):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
         hbm = float(peaks.get("hbm_gbs", 6800.0))
-        bpt = kernel_alg_bytes(dom, scheme, s_bytes) if dom.startswith("tri_") else None
+        bpt = kernel_alg_bytes(dom, scheme, s_bytes) if dom.startswith(("tri_", "tile_stage")) else None
         achieved = bpt * nt / (dom_ms * 1e-3) / 1e9 if bpt else None
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm if achieved else None, "bytes_per_triangle": bpt,
@@ -355,6 +369,7 @@ def ours(args, ws, rank, local):
             "ms_per_step_graph": ms_graph, "per_kernel_ms": per_kernel,
             "launch_shapes": {"tri_block": shapes[0], "vtx_block": shapes[1], "source": "rd_state_autotune"}
             if shapes else None,
+            "tiling": tiling_info(s.tiles),
             "roofline": roof, "step_hbm": step_hbm, "e2e": e2e,
             "gpu_launches": launches * args.steps + 1,
             "clocks": clk}
@@ -366,10 +381,11 @@ def ours(args, ws, rank, local):
         ms32 = max_over_ranks(ms32 / max(args.steps, 20), ws)
         d32 = max(pk32, key=pk32.get)
         hbm = hbm_peak
-        b32 = kernel_alg_bytes(d32, scheme, 4) if d32.startswith("tri_") else None
+        b32 = kernel_alg_bytes(d32, scheme, 4) if d32.startswith(("tri_", "tile_stage")) else None
         a32 = b32 * nt / (pk32[d32] * 1e-3) / 1e9 if b32 else None
         sb32 = ALG_BYTES_STEP.get((alg_scheme(scheme), 4))
         line["fp32"] = {"value": ws * nt / (ms32 * 1e-3), "ms_per_step": ms32, "per_kernel_ms": pk32,
+                        "tiling": tiling_info(s32.tiles),
                         "roofline": {"bound": "hbm", "kernel": d32, "achieved": a32, "peak": hbm, "unit": "GB/s",
                                      "frac": a32 / hbm if a32 else None, "bytes_per_triangle": b32,
                                      "traffic": ncu_traffic(args.workload, "fp32", d32, nt)},

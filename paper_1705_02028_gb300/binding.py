@@ -234,6 +234,7 @@ class Mesh:
         _check(rc, "rd_mesh_create")
         self.handle = h
         self.states = []
+        self.has_boundary = False
         ghost, walls = getattr(mesh, "ghost", None), getattr(mesh, "walls", None)
         if ghost is not None or walls is not None:
             self.set_boundary(ghost, walls, getattr(mesh, "alpha", 0.75))
@@ -244,6 +245,7 @@ class Mesh:
         w = np.zeros((0, 2), np.int32) if walls is None else np.ascontiguousarray(walls, dtype=np.int32)
         _check(_lib.rd_mesh_set_boundary(self.handle, _ptr(g, ctypes.c_uint8), len(w), _ptr(w, ctypes.c_int32),
                                          float(alpha)), "rd_mesh_set_boundary")
+        self.has_boundary = bool(len(w)) or (g is not None and bool(g.any()))
 
     @property
     def stream(self):
@@ -277,6 +279,7 @@ class State:
                  lumping="global"):
         load()
         self.mesh = mesh
+        self.scheme = scheme
         self.params = _params(scheme, precision, cfl, gamma, eps_fix, lumping)
         Wc = np.ascontiguousarray(W, dtype=np.float64)
         if Wc.shape != (4, mesh.nv):
@@ -334,7 +337,11 @@ class State:
         ms = np.zeros(6)
         n = ctypes.c_int32(0)
         _check(_lib.rd_state_profile(self.handle, int(n_steps), _ptr(ms), ctypes.byref(n)), "rd_state_profile")
-        names = ("tri_stage1", "gather_cfl", "update1", "tri_stage2", "update2", "commit")
+        names = ["tri_stage1", "gather_cfl", "update1", "tri_stage2", "update2", "commit"]
+        if self.tiling()[0] > 0:
+            names[0:2] = ["tile_stage1", "tile_bnd1"]
+            if str(self.scheme).split("_")[0] not in ("N1", "BX2") and not self.mesh.has_boundary:
+                names[3:5] = ["tile_stage2", "tile_bnd2"]
         return dict(zip(names, ms.tolist())), n.value
 
     def run_fixed_dt(self, dts):

@@ -339,6 +339,15 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
   return RD_OK;
 }
 
+// Kernel launches of one committed step as launch_step issues them.
+int step_launches(const rd_state* s) {
+  const bool bx = s->p.scheme == RD_BX2;
+  int n = 2 + 1;  // stage 1 + gather (tiled: tile kernel + boundary gather), commit
+  if (s->p.scheme == RD_N1) return n + 1;
+  if (s->tiles && tiled_stage2_applies(s)) return n + 1 + (s->tiles->n_bvert > 0 ? 1 : 0);
+  return n + 3 + (bx ? 2 : 0);  // update1, stage 2, update2 (+ the two |v| range resets of Bx)
+}
+
 int launch_step_any(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = true, double fixed_dt = 0.0) {
   if (s->bc_version != s->m->bc_version) return RD_EINVAL;  // boundary changed: rd_state_set first
   return s->pi == 0 ? launch_step<double>(s, a, ev, commit, fixed_dt) : launch_step<float>(s, a, ev, commit, fixed_dt);
@@ -595,7 +604,7 @@ extern "C" int rd_state_profile(rd_state* s, int32_t n_steps, double* ms_per_lau
   for (auto& e : ev)
     if (e) cudaEventDestroy(e);
   cudaGetLastError();
-  if (launches_per_step) *launches_per_step = s->p.scheme == RD_N1 ? 4 : 6;
+  if (launches_per_step) *launches_per_step = step_launches(s);
   if (rc != RD_OK) return rc;
   DevCtl c;
   CK(read_ctl(s, c));
@@ -653,6 +662,10 @@ extern "C" int rd_state_autotune(rd_state* s, int32_t* tri_block, int32_t* vtx_b
       if (r == RD_ENOTSUP) break;  // this mesh has no tile plan
       if ((rc = r) != RD_OK || (rc = time_step(best_t, best_v, ms)) != RD_OK) break;
       if (ms < best_tiled) { best_tiled = ms; best_tt = tt; best_bt = bt; }
+    }
+    if (best_tt && !(best_tiled < 0.98f * untiled)) {  // keep the untiled step unless tiling wins clearly
+      best_tt = 0;
+      best_bt = 0;
     }
     if (rc == RD_OK) rc = rd_state_set_tiling(s, best_tt, best_bt);
   }
