@@ -30,6 +30,27 @@ struct HostMesh {
 int build_host_mesh(int32_t nv, const double* xy, int32_t nt, const int32_t* tri,
                     const int8_t* shift, double Lx, double Ly, int32_t reorder, HostMesh& out);
 
+// Tile plan of the tiled step (host form; the device copy is rd::TilePlan).
+// Triangles, sorted by their smallest vertex id, form tiles of tt consecutive
+// triangles; tile p owns the vertices [vs[p], vs[p+1]); its halo vertices are
+// hlist[hptr[p] .. hptr[p+1]); lslot[c][t] is corner c's slot in its tile
+// (owned vertex v -> v - vs[p], halo vertex -> owned count + halo index);
+// a vertex is a boundary vertex when one of its triangles precedes its tile,
+// and bmask[t] bit c flags corner c of t at such a vertex.
+constexpr int MAX_TILE_TRIANGLES = 4096;
+struct TilePlanHost {
+  int tt = 0, n_tiles = 0, n_bvert = 0, slots = 0;
+  std::vector<int32_t> vs, hptr, hlist, bvert;
+  std::vector<uint16_t> lslot;
+  std::vector<uint8_t> bmask;
+};
+
+// Plan for tiles of tt triangles (a multiple of 32, at most
+// MAX_TILE_TRIANGLES).  RD_ENOTSUP if the triangles are not sorted by their
+// smallest vertex id (a mesh created without reordering) or a tile would
+// touch more than 65535 vertices.
+int build_tile_plan(const HostMesh& h, int tt, TilePlanHost& out);
+
 // Device control block of one state (one per mesh in batched mode).
 struct DevCtl {
   double dt;              // dt of the current step

@@ -11,21 +11,6 @@
 
 namespace rd {
 
-constexpr int MAX_TILE_TRIANGLES = 4096;
-
-// Host form of a tile plan (see TilePlan).
-struct TilePlanHost {
-  int tt = 0, n_tiles = 0, n_bvert = 0, slots = 0;
-  std::vector<int32_t> vs, hptr, hlist, bvert;
-  std::vector<uint16_t> lslot;
-  std::vector<uint8_t> bmask;
-};
-
-// Plan for tiles of tt triangles (a multiple of 32, at most
-// MAX_TILE_TRIANGLES).  RD_ENOTSUP if the triangles are not sorted by their
-// smallest vertex id (a mesh created without reordering) or a tile would
-// touch more than 65535 vertices.
-int build_tile_plan(const HostMesh& h, int tt, TilePlanHost& out);
 // Device copy of a plan for state s with bt threads per block.
 int tile_plan_upload(rd_state* s, const TilePlanHost& hp, int bt, TilePlan** out);
 // Dynamic shared memory of the stage-1 / stage-2 tile kernels.
