@@ -510,17 +510,28 @@ def adjoint_measure(args, ws, n_steps=200, ckpt_every=20):
 def host_cpu():
     """CPU model and logical core count of the host the oracle runs on."""
     import platform
-    model = platform.processor() or platform.machine()
-    try:
-        with open("/proc/cpuinfo") as f:
-            for line in f:
-                key = line.split(":")[0].strip().lower()
-                if key in ("model name", "cpu part", "hardware"):
-                    model = line.split(":", 1)[1].strip()
-                    break
-    except OSError:
+    import subprocess
+    model = None
+    try:  # lscpu names Arm cores (/proc/cpuinfo on Arm gives only part numbers)
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip().lower() == "model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
         pass
-    return {"model": model, "machine": platform.machine(), "logical_cpus": os.cpu_count()}
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    key = line.split(":")[0].strip().lower()
+                    if key in ("model name", "cpu part", "hardware"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"model": model or platform.processor() or platform.machine(), "machine": platform.machine(),
+            "logical_cpus": os.cpu_count()}
 
 
 def sample_mesh(workload):
