@@ -156,16 +156,9 @@ __global__ void __launch_bounds__(ADJ_TRI_BLOCK) k_stage2_masked(int nt, const i
     return;
   }
   Mask mk = node_mask(L, hl, eps);
-  const T a3 = __ldg(g.area + t) * (T(1) / T(3));
   const T idt = rcp(dt);
-  T PhiN[3][4], PhiT[4] = {T(0), T(0), T(0), T(0)};
-  for (int i = 0; i < 3; ++i)
-    for (int k = 0; k < 4; ++k) {
-      T mm = a3 * ((ws[i][k] - wn[i][k]) * idt);
-      PhiN[i][k] = mm + (L.phiN[i][k] + r[4 * i + k]) * T(0.5);
-      PhiT[k] += mm;
-    }
-  for (int k = 0; k < 4; ++k) PhiT[k] += (r[12 + k] + L.phiT[k]) * T(0.5);
+  T PhiN[3][4], PhiT[4];
+  stage2_totals(L, wn, ws, r, __ldg(g.area + t), idt, PhiN, PhiT);
   T lda[3][4], out[3][4];
   lda_apply(L, PhiT, lda);
   if (SCHEME == RD_LDA2) {

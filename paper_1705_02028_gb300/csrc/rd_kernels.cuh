@@ -177,10 +177,15 @@ RD_HD T abs_reg(T lam, T delta, T i2d) {
 //   mu1 = l1 - l3, mu2 = l2 - l3, s1 = (mu1 + mu2) / (2 c^2),
 //   s2 = (mu1 - mu2) / (2 c), hp = (mu1 + mu2) / 2.
 // PLUS selects Lambda^+ or Lambda^-; o = K^{+-} v.
+// Pressure-row product a . v, the node-independent part of K^{+-} v.
+template <class T>
+RD_HD T pressure_row(const RoeState<T>& r, const T v[4]) {
+  return r.alpha * v[0] - r.g1u * v[1] - r.g1v * v[2] + r.g1 * v[3];
+}
+// o = K^{+-} v given A = a . v (shared when one v meets all three nodes).
 template <class T, bool PLUS>
-RD_HD void Kpm_apply(const RoeState<T>& r, const NodeSys<T>& n, const T v[4], T o[4]) {
+RD_HD void Kpm_apply_a(const RoeState<T>& r, const NodeSys<T>& n, const T v[4], T A, T o[4]) {
   const int j = PLUS ? 0 : 1;
-  T A = r.alpha * v[0] - r.g1u * v[1] - r.g1v * v[2] + r.g1 * v[3];
   T B = n.nx * v[1] + n.ny * v[2] - n.w * v[0];
   T P = n.s1[j] * A + n.s2[j] * B;
   T Q = n.s2[j] * A + n.hp[j] * B;
@@ -189,6 +194,10 @@ RD_HD void Kpm_apply(const RoeState<T>& r, const NodeSys<T>& n, const T v[4], T 
   o[1] = l3 * v[1] + r.u * P + n.nx * Q;
   o[2] = l3 * v[2] + r.v * P + n.ny * Q;
   o[3] = l3 * v[3] + r.h * P + n.w * Q;
+}
+template <class T, bool PLUS>
+RD_HD void Kpm_apply(const RoeState<T>& r, const NodeSys<T>& n, const T v[4], T o[4]) {
+  Kpm_apply_a<T, PLUS>(r, n, v, pressure_row(r, v), o);
 }
 
 // LU factorisation with partial pivoting of a 4x4 matrix held in registers.
@@ -454,16 +463,18 @@ template <class T>
 RD_HD void lda_apply(const TriLin<T>& L, const T x[4], T out[3][4]) {
   T y[4];
   L.lu.solve(x, y);
+  const T A = pressure_row(L.r, y);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     T o[4];
-    Kpm_apply<T, true>(L.r, L.nd[i], y, o);
+    Kpm_apply_a<T, true>(L.r, L.nd[i], y, A, o);
 #pragma unroll
     for (int k = 0; k < 4; ++k) out[i][k] = -o[k];
   }
 }
 
-// Theta_kk = |tot_k| / max(sum_i |N_ik|, |tot_k|) (0/0 -> 0); out = Theta N + (1-Theta) LDA.
+// Theta_kk = |tot_k| / max(sum_i |N_ik|, |tot_k|) (0/0 -> 0); out = Theta N + (1-Theta) LDA,
+// evaluated as LDA + Theta (N - LDA).
 template <class T>
 RD_HD void blend(const T tot[4], const T N[3][4], const T lda[3][4], T out[3][4], int mode = BLEND_B,
                  T theta_x = T(0)) {
@@ -494,7 +505,7 @@ RD_HD void blend(const T tot[4], const T N[3][4], const T lda[3][4], T out[3][4]
 #pragma unroll
   for (int k = 0; k < 4; ++k)
 #pragma unroll
-    for (int i = 0; i < 3; ++i) out[i][k] = th[k] * N[i][k] + (T(1) - th[k]) * lda[i][k];
+    for (int i = 0; i < 3; ++i) out[i][k] = lda[i][k] + th[k] * (N[i][k] - lda[i][k]);
 }
 
 // Shock sensor of the Bx blend (Sec. 3.3.3): theta = min(1, s^2 h_T / L),
@@ -609,6 +620,26 @@ RD_HD int stage1_body(const T Z[3][4], const T nx[3], const T ny[3], const T hl[
 //   Phi^T     = sum_j |T|/3 (W*_j - W^n_j)/dt + (phi^T(W^n) + phi^T(W*)) / 2
 //   Phi^LDA_i = beta_i(W*) Phi^T     (m^LDA_ij = |T|/3 beta_i, global lumping)
 //   Phi_i     = Theta Phi^N_i + (I - Theta) Phi^LDA_i, Theta from (Phi^T, Phi^N)
+// Total residuals of stage 2 from the W* linearisation L, the stage-1 record
+// and the mass term (m = |T|/3 (W* - W^n) / dt).
+template <class T>
+RD_HD void stage2_totals(const TriLin<T>& L, const T Wn[3][4], const T Ws[3][4], const T rec[16], T area, T idt,
+                         T PhiN[3][4], T PhiT[4]) {
+  const T q = area * (T(1) / T(3)) * idt;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) PhiT[k] = T(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      T m = (Ws[i][k] - Wn[i][k]) * q;
+      PhiN[i][k] = m + (L.phiN[i][k] + rec[4 * i + k]) * T(0.5);
+      PhiT[k] += m;
+    }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) PhiT[k] += (rec[12 + k] + L.phiT[k]) * T(0.5);
+}
+
 template <class T, int SCHEME>
 RD_HD int stage2_body(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], const T rec[16], const T nx[3],
                       const T ny[3], const T hl[3], T area, T dt, const Gas<T>& gas, T eps, T out[3][4],
@@ -616,21 +647,9 @@ RD_HD int stage2_body(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], cons
   TriLin<T> L;
   int st = linearise(Zs, nx, ny, hl, gas, eps, L);
   if (st) return st;
-  T a3 = area * (T(1) / T(3));
   T idt = rcp(dt);
   T PhiN[3][4], PhiT[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) PhiT[k] = T(0);
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      T m = a3 * ((Ws[i][k] - Wn[i][k]) * idt);
-      PhiN[i][k] = m + (L.phiN[i][k] + rec[4 * i + k]) * T(0.5);
-      PhiT[k] += m;
-    }
-#pragma unroll
-  for (int k = 0; k < 4; ++k) PhiT[k] += (rec[12 + k] + L.phiT[k]) * T(0.5);
+  stage2_totals(L, Wn, Ws, rec, area, idt, PhiN, PhiT);
   T lda[3][4];
   lda_apply(L, PhiT, lda);
   if (SCHEME == RD_LDA2) {
@@ -865,21 +884,23 @@ __global__ void __launch_bounds__(BLOCK) k_gather_cfl(int nv, const int* __restr
 }
 
 // Vertex state -> parameter vector Z and |v| + c; returns false if non-physical.
+// One reciprocal of rho serves the four quotients (u, v, h and p / rho).
 template <class T>
 RD_HD bool vertex_Z(const T W[4], T gamma, T Z[4], T& spd, T* vmag = nullptr) {
   T rho = W[0];
-  if (!(rho > T(0))) return false;
-  T u = W[1] / rho, v = W[2] / rho;
+  if (!positive(rho)) return false;
+  const T ir = rcp(rho);
+  T u = W[1] * ir, v = W[2] * ir;
   T p = (gamma - T(1)) * (W[3] - T(0.5) * rho * (u * u + v * v));
-  if (!(p > T(0))) return false;
-  T h = (W[3] + p) / rho;
+  if (!positive(p)) return false;
+  T h = (W[3] + p) * ir;
   T sr = sqrt(rho);
   Z[0] = sr;
   Z[1] = sr * u;
   Z[2] = sr * v;
   Z[3] = sr * h;
   T q = sqrt(u * u + v * v);
-  spd = q + sqrt(gamma * p / rho);
+  spd = q + sqrt(gamma * p * ir);
   if (vmag) *vmag = q;
   return true;
 }
