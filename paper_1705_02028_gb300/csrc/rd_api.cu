@@ -132,12 +132,6 @@ extern "C" int rd_mesh_create(int32_t n_vertex, const double* xy, int32_t n_tri,
   };
   st = up_int(m->tri, m->h.tri);
   if (st == RD_OK) st = up_int(m->ptr, m->h.csr_ptr);
-  for (int k = 0; k < 3; ++k) {  // largest entry count of a vertex block (staged gathers)
-    const int B = 128 << k, nv = m->h.nv;
-    int mx = 0;
-    for (int v0 = 0; v0 < nv; v0 += B) mx = std::max(mx, m->h.csr_ptr[std::min(nv, v0 + B)] - m->h.csr_ptr[v0]);
-    m->max_block_entries[k] = mx;
-  }
   if (st == RD_OK) st = up_int(m->ent, m->h.csr_ent);
   if (st == RD_OK) st = up_int(m->vperm, m->h.vperm);
   if (st == RD_OK && cudaStreamSynchronize(m->stream) != cudaSuccess) {
@@ -233,28 +227,6 @@ __global__ void k_fix_dt(DevCtl* ctl, double dt) {
   if (!ctl->stop) ctl->dt = dt;
 }
 
-// Shared memory of a staged gather for a vertex block of vb threads (0 when it
-// would exceed STAGED_GATHER_MAX_BYTES: the per-vertex gather is used).
-template <class T>
-size_t staged_bytes(const rd_mesh* m, int vb, bool cfl) {
-  const int k = vb == 128 ? 0 : vb == 256 ? 1 : vb == 512 ? 2 : -1;
-  if (k < 0) return 0;
-  const size_t b = (size_t)m->max_block_entries[k] * staged_entry_bytes<T>(cfl);
-  return b <= STAGED_GATHER_MAX_BYTES ? b : 0;
-}
-
-int staged_smem_attrs() {
-  static bool done = false;
-  if (done) return RD_OK;
-  const int b = (int)STAGED_GATHER_MAX_BYTES;
-  CU(cudaFuncSetAttribute(k_gather_cfl_staged<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-  CU(cudaFuncSetAttribute(k_gather_cfl_staged<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-  CU(cudaFuncSetAttribute(k_update_staged<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-  CU(cudaFuncSetAttribute(k_update_staged<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-  done = true;
-  return RD_OK;
-}
-
 template <class T>
 BlendArgs<T> blend_args(const rd_state* s) {
   return tile_blend_args<T>(s);
@@ -323,11 +295,7 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
       break;
   }
   mark(1);
-  if (const size_t sb = staged_bytes<T>(m, VB, true))
-    k_gather_cfl_staged<T><<<gv, VB, sb, st>>>(nv, ptr, ent, share, cf, V, (T*)s->R1.p, (T*)s->partial.p, cfl,
-                                              (int)(sb / staged_entry_bytes<T>(true)), ctl);
-  else
-    launch_gather_cfl<T>(VB, st, nv, ptr, ent, share, cf, V, (T*)s->R1.p, (T*)s->partial.p, cfl, ctl);
+  launch_gather_cfl<T>(VB, st, nv, ptr, ent, share, cf, V, (T*)s->R1.p, (T*)s->partial.p, cfl, ctl);
   }
   if (fixed_dt > 0.0) k_fix_dt<<<1, 1, 0, st>>>(ctl, fixed_dt);
   mark(2);
@@ -360,14 +328,9 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
                                                    nullptr, nullptr, ba2);
     mark(4);
     if (vr0) k_vr_reset<<<1, 1, 0, st>>>(vr0, ctl, 0);
-    if (staged_bytes<T>(m, VB, false))
-      k_update_staged<T><<<gv, VB, staged_bytes<T>(m, VB, false), st>>>(
-          nv, (const T*)s->Ws.p, ptr, ent, share, V, gamma, (T*)s->W[b].p, (T*)s->Z[b].p, (T*)s->spd[b].p, ctl,
-          vr0, wa2, ga);
-    else
-      k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)s->Ws.p, nullptr, ptr, ent, share, V, gamma,
-                                            (T*)s->W[b].p, (T*)s->Z[b].p, (T*)s->spd[b].p, ctl, nullptr, nullptr,
-                                            vr0, wa2, ga);
+    k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)s->Ws.p, nullptr, ptr, ent, share, V, gamma,
+                                          (T*)s->W[b].p, (T*)s->Z[b].p, (T*)s->spd[b].p, ctl, nullptr, nullptr, vr0,
+                                          wa2, ga);
     mark(5);
   }
   if (commit) k_commit<<<1, 1, 0, st>>>(ctl);
@@ -449,7 +412,6 @@ int download_state(const rd_state* s, int buf, double* W_out) {
 
 int alloc_state(rd_state* s) {
   rd_mesh* m = s->m;
-  CK(staged_smem_attrs());
   const size_t nv = m->h.nv, nt = m->h.nt, ts = s->ts;
   cudaStream_t st = m->stream;
   for (int b = 0; b < 2; ++b) {

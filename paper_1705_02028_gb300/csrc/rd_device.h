@@ -42,10 +42,6 @@ constexpr int TRI_BLOCK = 128;
 constexpr int VTX_BLOCK = 256;
 constexpr int VTX_BLOCK_MIN = 128;
 
-// Staged gathers (corner records through shared memory) are used while their
-// shared memory stays within this bound.
-constexpr size_t STAGED_GATHER_MAX_BYTES = 96 * 1024;
-
 // Launch the dt gather with a runtime block size of 128, 256 or 512.
 template <class T>
 void launch_gather_cfl(int vblock, cudaStream_t st, int nv, const int* ptr, const int* ent, const T* share,
@@ -90,9 +86,6 @@ struct rd_mesh {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   rd::DevBuf tri, ptr, ent, vperm;
-  // largest CSR entry count of one vertex block of 128, 256, 512 vertices
-  // (shared-memory size of the staged gathers)
-  int max_block_entries[3] = {0, 0, 0};
   // geometry per precision (0: double, 1: float): nx, ny, hl, area, lmax, V
   rd::DevBuf geo[2][6];
   bool geo_ready[2] = {false, false};

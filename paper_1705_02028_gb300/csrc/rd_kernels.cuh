@@ -883,68 +883,6 @@ __global__ void __launch_bounds__(BLOCK) k_gather_cfl(int nv, const int* __restr
   dt_finish(ratio, partial, blockIdx.x, gridDim.x, cflnum, ctl);
 }
 
-// Corner records of one block's vertices staged in shared memory.  The block's
-// vertices [v0, v0 + blockDim.x) own the CSR entries [ptr[v0], ptr[v1]); the
-// entry ids are read coalesced and every record is fetched with its load
-// independent of the others (the per-vertex gather chains three dependent
-// loads), into srec[e - eb][4] (and the triangle's CFL term into scfl).  Each
-// vertex then sums its records in CSR order: the additions and their order are
-// those of gather_corners.  Returns eb; every thread of the block calls it.
-template <class T, bool CFL>
-__device__ __forceinline__ int stage_block_corners(int nv, const int* __restrict__ ptr, const int* __restrict__ ent,
-                                                   const T* __restrict__ share, const T* __restrict__ cfl, T* srec,
-                                                   T* scfl) {
-  const int v0 = blockIdx.x * blockDim.x;
-  const int v1 = min(nv, v0 + (int)blockDim.x);
-  const int eb = __ldg(ptr + v0), ee = __ldg(ptr + v1);
-  for (int e = eb + threadIdx.x; e < ee; e += blockDim.x) {
-    const int te = __ldg(ent + e);
-    T q[4];
-    ld4(share + (size_t)te * 4, q);
-    st4(srec + 4 * (e - eb), q);
-    if (CFL) scfl[e - eb] = __ldg(cfl + te / 3);
-  }
-  __syncthreads();
-  return eb;
-}
-
-// Shared-memory bytes per staged corner entry.
-template <class T>
-constexpr size_t staged_entry_bytes(bool cfl) {
-  return (cfl ? 5 : 4) * sizeof(T);
-}
-
-// k_gather_cfl with the block's corner records staged in shared memory
-// (dynamic: the mesh's largest entry count of a block x staged_entry_bytes).
-template <class T>
-__global__ void __launch_bounds__(512) k_gather_cfl_staged(int nv, const int* __restrict__ ptr,
-                                                          const int* __restrict__ ent, const T* __restrict__ share,
-                                                          const T* __restrict__ cfl, const T* __restrict__ V,
-                                                          T* __restrict__ R1, T* __restrict__ partial, T cflnum,
-                                                          int max_entries, DevCtl* ctl) {
-  extern __shared__ __align__(16) unsigned char gsm[];
-  if (ctl->stop) return;
-  T* srec = reinterpret_cast<T*>(gsm);
-  T* scfl = srec + 4 * (size_t)max_entries;
-  const int eb = stage_block_corners<T, true>(nv, ptr, ent, share, cfl, srec, scfl);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  T ratio = T(INFINITY);
-  if (i < nv) {
-    T r[4] = {T(0), T(0), T(0), T(0)};
-    T sig = T(0);
-    const int e1 = __ldg(ptr + i + 1);
-    for (int e = __ldg(ptr + i); e < e1; ++e) {
-      const T* q = srec + 4 * (e - eb);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) r[k] += q[k];
-      sig += scfl[e - eb];
-    }
-    st4(R1 + 4 * (size_t)i, r);
-    ratio = T(2) * __ldg(V + i) / sig;
-  }
-  dt_finish(ratio, partial, blockIdx.x, gridDim.x, cflnum, ctl);
-}
-
 // Vertex state -> parameter vector Z and |v| + c; returns false if non-physical.
 // One reciprocal of rho serves the four quotients (u, v, h and p / rho).
 template <class T>
@@ -1093,15 +1031,31 @@ __device__ __forceinline__ void wall_add(const WallArgs<T>& wa, const T* __restr
   }
 }
 
-// The update of one vertex given its residual r: walls, W_out = W_in - dt/V R,
-// ghost reset, Z_out = Z(W_out), spd_out (nullable) = |v| + c, status.
-// Returns whether the state is physical (q = |v|).
+// W_out = W_in - dt/V R; Z_out = Z(W_out); spd_out (nullable) = |v| + c.
+// If R2 != nullptr, W_in is W* and R = R2 gathered here from share (stage 2).
 template <class T>
-__device__ __forceinline__ bool update_vertex(int i, T r[4], const T* __restrict__ Win, const T* __restrict__ V,
-                                              T gamma, T* __restrict__ Wout, T* __restrict__ Zout,
-                                              T* __restrict__ spdout, DevCtl* ctl, const double* __restrict__ dtm,
-                                              const uint16_t* __restrict__ vmesh, const WallArgs<T>& wa,
-                                              const GhostArgs<T>& ga, T& q) {
+__global__ void __launch_bounds__(512) k_update(int nv, const T* __restrict__ Win, const T* __restrict__ R,
+                                                const int* __restrict__ ptr, const int* __restrict__ ent,
+                                                const T* __restrict__ share, const T* __restrict__ V, T gamma,
+                                                T* __restrict__ Wout, T* __restrict__ Zout, T* __restrict__ spdout,
+                                                DevCtl* ctl, const double* __restrict__ dtm = nullptr,
+                                                const uint16_t* __restrict__ vmesh = nullptr,
+                                                unsigned long long* __restrict__ vr_out = nullptr,
+                                                WallArgs<T> wa = WallArgs<T>(), GhostArgs<T> ga = GhostArgs<T>()) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act = i < nv && !ctl->stop;
+  if (!act && !vr_out) return;
+  bool has = false;
+  T q = T(0);
+  if (act) {
+  T r[4];
+  if (share) {
+    r[0] = r[1] = r[2] = r[3] = T(0);
+    T unused = T(0);
+    gather_corners<T, false>(__ldg(ptr + i), __ldg(ptr + i + 1), ent, share, nullptr, r, unused);
+  } else {
+    load_vec4(R, i, r);
+  }
   if (wa.ptr) {
     if (wa.Wn) {
       wall_add(wa, Win, i, gamma, T(0.5), r);
@@ -1128,67 +1082,7 @@ __device__ __forceinline__ bool update_vertex(int i, T r[4], const T* __restrict
     atomicOr(&ctl->status, ST_NONPHYS_VERTEX);
     ctl->stop = 1;
   }
-  return ok;
-}
-
-// W_out = W_in - dt/V R; Z_out = Z(W_out); spd_out (nullable) = |v| + c.
-// If R2 != nullptr, W_in is W* and R = R2 gathered here from share (stage 2).
-template <class T>
-__global__ void __launch_bounds__(512) k_update(int nv, const T* __restrict__ Win, const T* __restrict__ R,
-                                                const int* __restrict__ ptr, const int* __restrict__ ent,
-                                                const T* __restrict__ share, const T* __restrict__ V, T gamma,
-                                                T* __restrict__ Wout, T* __restrict__ Zout, T* __restrict__ spdout,
-                                                DevCtl* ctl, const double* __restrict__ dtm = nullptr,
-                                                const uint16_t* __restrict__ vmesh = nullptr,
-                                                unsigned long long* __restrict__ vr_out = nullptr,
-                                                WallArgs<T> wa = WallArgs<T>(), GhostArgs<T> ga = GhostArgs<T>()) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool act = i < nv && !ctl->stop;
-  if (!act && !vr_out) return;
-  bool has = false;
-  T q = T(0);
-  if (act) {
-    T r[4];
-    if (share) {
-      r[0] = r[1] = r[2] = r[3] = T(0);
-      T unused = T(0);
-      gather_corners<T, false>(__ldg(ptr + i), __ldg(ptr + i + 1), ent, share, nullptr, r, unused);
-    } else {
-      load_vec4(R, i, r);
-    }
-    has = update_vertex(i, r, Win, V, gamma, Wout, Zout, spdout, ctl, dtm, vmesh, wa, ga, q);
-  }
-  if (vr_out) vrange_fold(has, q, vr_out);
-}
-
-// The stage-2 form of k_update (R gathered from share) with the block's corner
-// records staged in shared memory (dynamic: max_entries x 4 words).
-template <class T>
-__global__ void __launch_bounds__(512) k_update_staged(int nv, const T* __restrict__ Win, const int* __restrict__ ptr,
-                                                       const int* __restrict__ ent, const T* __restrict__ share,
-                                                       const T* __restrict__ V, T gamma, T* __restrict__ Wout,
-                                                       T* __restrict__ Zout, T* __restrict__ spdout, DevCtl* ctl,
-                                                       unsigned long long* __restrict__ vr_out, WallArgs<T> wa,
-                                                       GhostArgs<T> ga) {
-  extern __shared__ __align__(16) unsigned char gsm[];
-  __shared__ int stop;
-  if (threadIdx.x == 0) stop = ctl->stop;
-  __syncthreads();
-  if (stop) return;  // the whole block: a stopped run leaves the |v| range as it was
-  T* srec = reinterpret_cast<T*>(gsm);
-  const int eb = stage_block_corners<T, false>(nv, ptr, ent, share, nullptr, srec, nullptr);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  bool has = false;
-  T q = T(0);
-  if (i < nv) {
-    T r[4] = {T(0), T(0), T(0), T(0)};
-    const int e1 = __ldg(ptr + i + 1);
-    for (int e = __ldg(ptr + i); e < e1; ++e) {
-      const T* qq = srec + 4 * (e - eb);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) r[k] += qq[k];
-    }
-    has = update_vertex(i, r, Win, V, gamma, Wout, Zout, spdout, ctl, nullptr, nullptr, wa, ga, q);
+  has = ok;
   }
   if (vr_out) vrange_fold(has, q, vr_out);
 }
