@@ -80,6 +80,11 @@ template <class T>
 RD_HD T rcp(T x) {
   return T(1) / x;
 }
+#if defined(__CUDACC__)
+// The IEEE division of the rare out-of-range arguments, out of line: inlined,
+// the compiler may evaluate it beside the fast path and select.
+static __device__ __noinline__ double rcp_ieee(double x) { return 1.0 / x; }
+#endif
 RD_HD double rcp(double x) {
 #if defined(__CUDA_ARCH__) && RD_FAST_RCP
   const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
@@ -91,8 +96,10 @@ RD_HD double rcp(double x) {
     t = fma(-x, r, 1.0);
     return fma(r, t, r);
   }
-#endif
+  return rcp_ieee(x);
+#else
   return 1.0 / x;
+#endif
 }
 
 // Blends of N and LDA (Sec. 3.3.3): diagonal Theta (B), every diagonal entry
@@ -167,6 +174,20 @@ template <class T>
 RD_HD T abs_reg(T lam, T delta, T i2d) {
   return mag_less(lam, delta) ? (lam * lam + delta * delta) * i2d : fabs(lam);
 }
+// The three regularised |lambda| of a node that has one below delta (rare).
+template <class T>
+RD_HD void abs_reg3(const T la[3], T delta, T ab[3]) {
+  const T i2d = T(0.5) / delta;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) ab[k] = abs_reg(la[k], delta, i2d);
+}
+#if defined(__CUDACC__)
+// Out of line on the device, so that the common path carries none of its work.
+template <class T>
+__device__ __noinline__ void abs_reg3_dev(const T* la, T delta, T* ab) {
+  abs_reg3(la, delta, ab);
+}
+#endif
 
 // K^{+-} in closed form (App. A).  With the right eigenvectors of App. A,
 // e = (1, u, v, h), d = (0, nx, ny, w), the pressure row a = (alpha, -g1 u,
@@ -367,32 +388,45 @@ RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3]
     n.w = r.u * n.nx + r.v * n.ny;
     T delta = eps * r.c * hl[i];
     T la[3] = {(n.w + r.c) * hl[i], (n.w - r.c) * hl[i], n.w * hl[i]};
-    T i2d = T(0);
-    if (mag_less(la[0], delta) || mag_less(la[1], delta) || mag_less(la[2], delta)) i2d = T(0.5) / delta;
     T ab[3];
+    if (mag_less(la[0], delta) || mag_less(la[1], delta) || mag_less(la[2], delta)) {
+#ifdef __CUDA_ARCH__
+      abs_reg3_dev(la, delta, ab);
+#else
+      abs_reg3(la, delta, ab);
+#endif
+    } else {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) ab[k] = abs_reg(la[k], delta, i2d);
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      // j = 0: Lambda^+ = (la + |la|)/2, j = 1: Lambda^- = (la - |la|)/2
-      T sg = j == 0 ? T(0.5) : T(-0.5);
-      T l1 = la[0] * T(0.5) + sg * ab[0];
-      T l2 = la[1] * T(0.5) + sg * ab[1];
-      T l3 = la[2] * T(0.5) + sg * ab[2];
-      T mu1 = l1 - l3, mu2 = l2 - l3;
-      T sp = mu1 + mu2, sm = mu1 - mu2;
-      n.l3[j] = l3;
-      n.s1[j] = sp * r.ic2h;
-      n.s2[j] = sm * r.i2c;
-      n.hp[j] = sp * T(0.5);
+      for (int k = 0; k < 3; ++k) ab[k] = fabs(la[k]);
     }
+    // Lambda^{+-} = (la +- |la|) / 2, mu_k = l_k - l_3.  Since la_1 + la_2 = 2 la_3
+    // and la_1 - la_2 = 2 c hl:  mu_1 + mu_2 = +-X,  mu_1 - mu_2 = c hl +- Y with
+    // X = (|la_1| + |la_2|) / 2 - |la_3|, Y = (|la_1| - |la_2|) / 2, and
+    // (c hl) i2c = hl / 2 (i2c = 1 / 2c).
+    const T X = T(0.5) * (ab[0] + ab[1]) - ab[2];
+    const T Yi = (T(0.5) * (ab[0] - ab[1])) * r.i2c;
+    const T s1 = X * r.ic2h, hp = X * T(0.5), q2 = T(0.5) * hl[i];
+    const T l3m = T(0.5) * la[2], l3a = T(0.5) * ab[2];
+    n.l3[0] = l3m + l3a;
+    n.l3[1] = l3m - l3a;
+    n.s1[0] = s1;
+    n.s1[1] = -s1;
+    n.hp[0] = hp;
+    n.hp[1] = -hp;
+    n.s2[0] = q2 + Yi;
+    n.s2[1] = q2 - Yi;
   }
 
   // sum_j K_j^- = (sum l3) I + e P^T + sum_j d_j q_j^T,
-  //   P = (sum s1) a + sum_j s2_j b_j,  q_j = s2_j a + hp_j b_j
+  //   P = (sum s1) a + sum_j s2_j b_j,  q_j = s2_j a + hp_j b_j.
+  // With d_j = (0, nx, ny, w)_j and b_j = (-w, nx, ny, 0)_j the rows
+  // M_x = sum_j nx_j q_j (and M_y, M_w) need only the moments
+  // P_x = sum s2 nx, ..., S_xy = sum hp nx ny, ...:
+  //   M_x = P_x a + (-S_xw, S_xx, S_xy, 0), M_y = P_y a + (-S_yw, S_xy, S_yy, 0),
+  //   M_w = P_w a + (-S_ww, S_xw, S_yw, 0).
   {
     T L3 = T(0), S1 = T(0), Pw = T(0), Px = T(0), Py = T(0);
-    T M1[4] = {T(0), T(0), T(0), T(0)}, M2[4] = {T(0), T(0), T(0), T(0)}, M3[4] = {T(0), T(0), T(0), T(0)};
+    T Sxx = T(0), Sxy = T(0), Syy = T(0), Sxw = T(0), Syw = T(0), Sww = T(0);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const NodeSys<T>& n = L.nd[j];
@@ -401,15 +435,17 @@ RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3]
       Pw += n.s2[1] * n.w;
       Px += n.s2[1] * n.nx;
       Py += n.s2[1] * n.ny;
-      T q[4] = {n.s2[1] * r.alpha - n.hp[1] * n.w, n.hp[1] * n.nx - n.s2[1] * r.g1u,
-                n.hp[1] * n.ny - n.s2[1] * r.g1v, n.s2[1] * r.g1};
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        M1[c] += n.nx * q[c];
-        M2[c] += n.ny * q[c];
-        M3[c] += n.w * q[c];
-      }
+      const T hx = n.hp[1] * n.nx, hy = n.hp[1] * n.ny, hw = n.hp[1] * n.w;
+      Sxx += hx * n.nx;
+      Sxy += hx * n.ny;
+      Syy += hy * n.ny;
+      Sxw += hx * n.w;
+      Syw += hy * n.w;
+      Sww += hw * n.w;
     }
+    const T M1[4] = {Px * r.alpha - Sxw, Sxx - Px * r.g1u, Sxy - Px * r.g1v, Px * r.g1};
+    const T M2[4] = {Py * r.alpha - Syw, Sxy - Py * r.g1u, Syy - Py * r.g1v, Py * r.g1};
+    const T M3[4] = {Pw * r.alpha - Sww, Sxw - Pw * r.g1u, Syw - Pw * r.g1v, Pw * r.g1};
     T P[4] = {S1 * r.alpha - Pw, Px - S1 * r.g1u, Py - S1 * r.g1v, S1 * r.g1};
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -423,22 +459,36 @@ RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3]
   }
   if (!L.lu.factor()) return ST_SINGULAR;
 
-  // conservative linearised states W^_i = dW/dZ(Zbar) Z_i and sum_j K_j^- W^_j
+  // conservative linearised states W^_i = dW/dZ(Zbar) Z_i and
+  // S = sum_j K_j^- W^_j = sum_j l3_j W^_j + e sum_j P_j + sum_j d_j Q_j
+  // (P_j = s1 A + s2 B, Q_j = s2 A + hp B, A = a . W^_j, B = b_j . W^_j)
   T (*Wh)[4] = L.Wh;
   T S[4] = {T(0), T(0), T(0), T(0)};
   {
     const T g = gas.g, ig = gas.ig;
+    T SP = T(0), SQx = T(0), SQy = T(0), SQw = T(0);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       Wh[i][0] = T(2) * Zb[0] * Z[i][0];
       Wh[i][1] = Zb[1] * Z[i][0] + Zb[0] * Z[i][1];
       Wh[i][2] = Zb[2] * Z[i][0] + Zb[0] * Z[i][2];
       Wh[i][3] = (Zb[3] * Z[i][0] + Zb[0] * Z[i][3]) * ig + g * (Zb[1] * Z[i][1] + Zb[2] * Z[i][2]);
-      T o[4];
-      Kpm_apply<T, false>(r, L.nd[i], Wh[i], o);
+      const NodeSys<T>& n = L.nd[i];
+      const T A = pressure_row(r, Wh[i]);
+      const T B = n.nx * Wh[i][1] + n.ny * Wh[i][2] - n.w * Wh[i][0];
+      const T Pj = n.s1[1] * A + n.s2[1] * B;
+      const T Qj = n.s2[1] * A + n.hp[1] * B;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) S[k] += o[k];
+      for (int k = 0; k < 4; ++k) S[k] += n.l3[1] * Wh[i][k];
+      SP += Pj;
+      SQx += n.nx * Qj;
+      SQy += n.ny * Qj;
+      SQw += n.w * Qj;
     }
+    S[0] += SP;
+    S[1] += r.u * SP + SQx;
+    S[2] += r.v * SP + SQy;
+    S[3] += r.h * SP + SQw;
   }
   // N scheme: phi_i^N = K_i^+ (W^_i - N^ sum_j K_j^- W^_j)
   T* win = L.win;
