@@ -102,6 +102,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form companion measurement")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tiling", default="auto",
+                    help="tiled step: 'auto' (the autotuner's choice), 'none', or TRIANGLESxTHREADS, e.g. 512x128")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-rollout companion measurement")
     ap.add_argument("--no-meshgen", action="store_true", help="skip the mesh-generation companion measurement")
     return ap.parse_args()
@@ -232,10 +234,16 @@ def ncu_traffic(workload, precision, kernel, nt):
     return float(e["dram_bytes_per_triangle"]) * nt
 
 
-def run_state_timing(binding, mesh_dev, W0, scheme, precision, steps, warmup, ws, clocks=None, autotune=True):
+def run_state_timing(binding, mesh_dev, W0, scheme, precision, steps, warmup, ws, clocks=None, autotune=True,
+                     tiling="auto"):
     import torch
     s = binding.State(mesh_dev, W0, scheme=scheme, precision=precision)
     s.shapes = s.autotune() if autotune else None
+    if tiling == "none":
+        s.set_tiling(0)
+    elif tiling != "auto":
+        tt, bt = (int(x) for x in tiling.lower().split("x"))
+        s.set_tiling(tt, bt)
     s.tiles = s.tiling()
     s.run(warmup)
     st = mesh_dev.stream
@@ -290,7 +298,7 @@ def ours(args, ws, rank, local):
     clocks = ClockSampler(local)
     s, ms_total, per_kernel, launches = run_state_timing(binding, m, W0, scheme, args.precision,
                                                          args.steps, args.warmup, ws, clocks,
-                                                         autotune=not args.no_autotune)
+                                                         autotune=not args.no_autotune, tiling=args.tiling)
     clk = clocks.result
     shapes = s.shapes
     ms_step = max_over_ranks(ms_total / args.steps, ws)
@@ -377,7 +385,7 @@ def ours(args, ws, rank, local):
     # FP32 companion measurement on the same mesh
     if not args.no_fp32 and args.precision == "fp64":
         s32, ms32, pk32, _ = run_state_timing(binding, m, W0, scheme, "fp32", max(args.steps, 20),
-                                              args.warmup, ws, autotune=not args.no_autotune)
+                                              args.warmup, ws, autotune=not args.no_autotune, tiling=args.tiling)
         ms32 = max_over_ranks(ms32 / max(args.steps, 20), ws)
         d32 = max(pk32, key=pk32.get)
         hbm = hbm_peak
