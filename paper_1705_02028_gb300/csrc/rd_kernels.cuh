@@ -182,10 +182,16 @@ RD_HD void abs_reg3(const T la[3], T delta, T ab[3]) {
   for (int k = 0; k < 3; ++k) ab[k] = abs_reg(la[k], delta, i2d);
 }
 #if defined(__CUDACC__)
-// Out of line on the device, so that the common path carries none of its work.
+// Out of line on the device, so that the common path carries none of its work;
+// scalar arguments and result, so that no array of the caller needs an address.
 template <class T>
-__device__ __noinline__ void abs_reg3_dev(const T* la, T delta, T* ab) {
-  abs_reg3(la, delta, ab);
+struct Abs3 {
+  T a0, a1, a2;
+};
+template <class T>
+__device__ __noinline__ Abs3<T> abs_reg3_dev(T la0, T la1, T la2, T delta) {
+  const T i2d = T(0.5) / delta;
+  return Abs3<T>{abs_reg(la0, delta, i2d), abs_reg(la1, delta, i2d), abs_reg(la2, delta, i2d)};
 }
 #endif
 
@@ -391,7 +397,10 @@ RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3]
     T ab[3];
     if (mag_less(la[0], delta) || mag_less(la[1], delta) || mag_less(la[2], delta)) {
 #ifdef __CUDA_ARCH__
-      abs_reg3_dev(la, delta, ab);
+      const Abs3<T> a = abs_reg3_dev(la[0], la[1], la[2], delta);
+      ab[0] = a.a0;
+      ab[1] = a.a1;
+      ab[2] = a.a2;
 #else
       abs_reg3(la, delta, ab);
 #endif
