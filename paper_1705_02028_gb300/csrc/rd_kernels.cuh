@@ -189,9 +189,13 @@ struct Abs3 {
   T a0, a1, a2;
 };
 template <class T>
-__device__ __noinline__ Abs3<T> abs_reg3_dev(T la0, T la1, T la2, T delta) {
+RD_HD Abs3<T> abs_reg3_val(T la0, T la1, T la2, T delta) {
   const T i2d = T(0.5) / delta;
   return Abs3<T>{abs_reg(la0, delta, i2d), abs_reg(la1, delta, i2d), abs_reg(la2, delta, i2d)};
+}
+template <class T>
+__device__ __noinline__ Abs3<T> abs_reg3_dev(T la0, T la1, T la2, T delta) {
+  return abs_reg3_val(la0, la1, la2, delta);
 }
 #endif
 
