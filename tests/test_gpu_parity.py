@@ -214,9 +214,9 @@ def test_full_size_4096_khi_b2_first_step(rd):
 
 
 def test_full_size_4096_in_the_benchmarked_configuration(rd):
-    """The configuration bench.py times: 4096^2 KHI B2 with the autotuned launch shapes,
-    two steps through the captured CUDA graph of rd_run, FP64 against the oracle at
-    1e-12 and FP32 by its L1 density error."""
+    """The configuration bench.py times: 4096^2 KHI B2 with the autotuned launch shapes
+    (and tiling), two steps through the captured CUDA graph of rd_run, FP64 against the
+    oracle at 1e-12 and FP32 by its L1 density error."""
     mesh = inputs.periodic_grid(4096)
     W0 = inputs.khi_state(mesh)
     m = rd.Mesh(mesh, reorder="morton")
@@ -229,8 +229,8 @@ def test_full_size_4096_in_the_benchmarked_configuration(rd):
     assert err < TOL
     s.close()
     s32 = rd.State(m, W0, scheme="B2", precision="fp32")
-    s32.autotune()
+    s32.autotune()  # may keep the tiled step (rd_state_set_tiling)
     assert s32.run(2) == 2
     l1 = exact.l1_error(oracle.geometry(mesh)["V"], s32.get()[0], Wo[0])
-    print(f"4096^2 B2 FP32, 2 graph steps: L1 density error vs the FP64 oracle {l1:.2e}")
+    print(f"4096^2 B2 FP32 (tiling {s32.tiling()}), 2 graph steps: L1 density error vs the FP64 oracle {l1:.2e}")
     assert l1 < 1e-6
