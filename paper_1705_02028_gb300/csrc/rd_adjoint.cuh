@@ -131,7 +131,8 @@ RD_HD void blend_rev(const T tot[4], const T N[3][4], const T lda[3][4], const T
     T num = fabs(tot[k]);
     T D = fabs(N[0][k]) + fabs(N[1][k]) + fabs(N[2][k]);
     T den = D > num ? D : num;
-    T th = mbit(m, 30 + k) ? num / den : T(0);
+    const T iden = rcp(den);
+    T th = mbit(m, 30 + k) ? num * iden : T(0);
     T thb = T(0);
     for (int i = 0; i < 3; ++i) {
       thb += ob[i][k] * (N[i][k] - lda[i][k]);
@@ -139,8 +140,8 @@ RD_HD void blend_rev(const T tot[4], const T N[3][4], const T lda[3][4], const T
       ldab[i][k] += (T(1) - th) * ob[i][k];
     }
     if (!mbit(m, 30 + k)) continue;
-    T numb = thb / den;
-    T denb = -thb * num / (den * den);
+    T numb = thb * iden;
+    T denb = -(thb * th) * iden;  // -thb num / den^2
     T Db = T(0);
     if (mbit(m, 26 + k)) Db = denb;
     else numb += denb;
@@ -252,9 +253,11 @@ RD_HD void linearise_rev(const T Z[3][4], const T nx[3], const T ny[3], const T 
     const NodeSys<T>& n = L.nd[i];
     T delta = eps * r.c * hl[i];
     T la[3] = {(n.w + r.c) * hl[i], (n.w - r.c) * hl[i], n.w * hl[i]};
+    const bool reg = mbit(mask, 3 * i) || mbit(mask, 3 * i + 1) || mbit(mask, 3 * i + 2);
+    const T idelta = reg ? rcp(delta) : T(0);
     T ab[3];
     for (int k = 0; k < 3; ++k)
-      ab[k] = mbit(mask, 3 * i + k) ? (la[k] * la[k] + delta * delta) * (T(0.5) / delta) : fabs(la[k]);
+      ab[k] = mbit(mask, 3 * i + k) ? (la[k] * la[k] + delta * delta) * (T(0.5) * idelta) : fabs(la[k]);
     T lab[3] = {T(0), T(0), T(0)}, abb[3] = {T(0), T(0), T(0)};
     for (int j = 0; j < 2; ++j) {
       T sg = j == 0 ? T(0.5) : T(-0.5);
@@ -277,8 +280,8 @@ RD_HD void linearise_rev(const T Z[3][4], const T nx[3], const T ny[3], const T 
     T deltab = T(0);
     for (int k = 0; k < 3; ++k) {
       if (mbit(mask, 3 * i + k)) {
-        lab[k] += abb[k] * la[k] / delta;
-        deltab += abb[k] * (delta * delta - la[k] * la[k]) / (T(2) * delta * delta);
+        lab[k] += abb[k] * la[k] * idelta;
+        deltab += abb[k] * (delta * delta - la[k] * la[k]) * (T(0.5) * idelta * idelta);
       } else {
         lab[k] += abb[k] * (mbit(mask, 9 + 3 * i + k) ? T(-1) : T(1));
       }
@@ -308,12 +311,12 @@ RD_HD void linearise_rev(const T Z[3][4], const T nx[3], const T ny[3], const T 
   }
   // Roe state from Zbar
   {
-    T iz = T(1) / Zb[0];
+    T iz = rcp(Zb[0]);
     T c2 = r.c * r.c;
     T cb = rb.c + rb.i2c * r.ic2h;
     T ic2hb = rb.ic2h + rb.i2c * r.c;
     T ic2b = T(0.5) * ic2hb;
-    T c2b = -r.ic2 * r.ic2 * ic2b + cb / (T(2) * r.c);
+    T c2b = -r.ic2 * r.ic2 * ic2b + cb * r.i2c;  // i2c = 1 / (2 c)
     T q2hb = r.g1 * rb.alpha - r.g1 * c2b;
     T hb = rb.h + r.g1 * c2b;
     T ub = rb.u + r.g1 * rb.g1u + r.u * q2hb;
@@ -386,16 +389,9 @@ RD_HD int stage2_rev(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], const
   TriLin<T> L;
   int st = linearise(Zs, nx, ny, hl, gamma, eps, L);
   if (st) return st;
-  T a3 = area * (T(1) / T(3));
-  T idt = T(1) / dt;
-  T PhiN[3][4], PhiT[4] = {T(0), T(0), T(0), T(0)};
-  for (int i = 0; i < 3; ++i)
-    for (int k = 0; k < 4; ++k) {
-      T m = a3 * ((Ws[i][k] - Wn[i][k]) * idt);
-      PhiN[i][k] = m + (L.phiN[i][k] + rec[4 * i + k]) * T(0.5);
-      PhiT[k] += m;
-    }
-  for (int k = 0; k < 4; ++k) PhiT[k] += (rec[12 + k] + L.phiT[k]) * T(0.5);
+  const T q = area * (T(1) / T(3)) * rcp(dt);  // |T| / (3 dt), as in stage2_totals
+  T PhiN[3][4], PhiT[4];
+  stage2_totals(L, Wn, Ws, rec, area, rcp(dt), PhiN, PhiT);
   T y[4], lda[3][4], ldab[3][4];
   L.lu.solve(PhiT, y);
   for (int i = 0; i < 3; ++i) {
@@ -432,8 +428,8 @@ RD_HD int stage2_rev(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], const
       T mb = PhiNb[i][k] + PhiTb[k];
       phiNb[i][k] = T(0.5) * PhiNb[i][k];
       recb[4 * i + k] = T(0.5) * PhiNb[i][k];
-      Wsb[i][k] = a3 * idt * mb;
-      Wnb[i][k] = -(a3 * idt * mb);
+      Wsb[i][k] = q * mb;
+      Wnb[i][k] = -(q * mb);
       Zsb[i][k] = T(0);
     }
   linearise_rev(Zs, nx, ny, hl, gamma, eps, L, mask, phiNb, phiTb, Mb, rb, nb, Zsb);
@@ -457,16 +453,8 @@ RD_HD Mask stage2_mask(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], con
   if (linearise(Zs, nx, ny, hl, gamma, eps, L)) return 0;
   Mask m = node_mask(L, hl, eps);
   if (SCHEME != RD_B2) return m;
-  T a3 = area * (T(1) / T(3));
-  T idt = T(1) / dt;
-  T PhiN[3][4], PhiT[4] = {T(0), T(0), T(0), T(0)};
-  for (int i = 0; i < 3; ++i)
-    for (int k = 0; k < 4; ++k) {
-      T mm = a3 * ((Ws[i][k] - Wn[i][k]) * idt);
-      PhiN[i][k] = mm + (L.phiN[i][k] + rec[4 * i + k]) * T(0.5);
-      PhiT[k] += mm;
-    }
-  for (int k = 0; k < 4; ++k) PhiT[k] += (rec[12 + k] + L.phiT[k]) * T(0.5);
+  T PhiN[3][4], PhiT[4];
+  stage2_totals(L, Wn, Ws, rec, area, rcp(dt), PhiN, PhiT);  // as the masked forward kernel
   return m | blend_mask(PhiT, PhiN);
 }
 
@@ -474,13 +462,14 @@ RD_HD Mask stage2_mask(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], con
 template <class T>
 RD_HD void vertex_Z_rev(const T W[4], T gamma, const T Zb[4], T Wb[4]) {
   T rho = W[0];
-  T u = W[1] / rho, v = W[2] / rho;
+  const T ir = rcp(rho);
+  T u = W[1] * ir, v = W[2] * ir;
   T g1 = gamma - T(1);
   T p = g1 * (W[3] - T(0.5) * rho * (u * u + v * v));
-  T h = (W[3] + p) / rho;
-  T s = sqrt(rho), is = T(1) / s;
+  T h = (W[3] + p) * ir;
+  T s = sqrt(rho), is = rcp(s);
   T Z1 = s * u, Z2 = s * v;
-  Wb[0] += T(0.5) * is * Zb[0] - (Zb[1] * Z1 + Zb[2] * Z2) / (T(2) * rho) +
+  Wb[0] += T(0.5) * is * Zb[0] - (Zb[1] * Z1 + Zb[2] * Z2) * (T(0.5) * ir) +
            Zb[3] * (T(0.5) * g1 * (u * u + v * v) - T(0.5) * h) * is;
   Wb[1] += (Zb[1] - Zb[3] * g1 * u) * is;
   Wb[2] += (Zb[2] - Zb[3] * g1 * v) * is;
