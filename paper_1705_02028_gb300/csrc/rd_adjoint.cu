@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(ADJ_TRI_BLOCK) k_stage1_masked(int nt, const i
                                                                  const T* __restrict__ Z, const T* __restrict__ spd,
                                                                  Gas<T> gas, T eps, T* __restrict__ share,
                                                                  T* __restrict__ rec, T* __restrict__ cfl,
-                                                                 DevCtl* ctl, Mask* __restrict__ mask) {
+                                                                 DevCtl* ctl, Mask* __restrict__ mask,
+                                                                 T* __restrict__ lin = nullptr) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
   int v[3];
@@ -106,6 +107,7 @@ __global__ void __launch_bounds__(ADJ_TRI_BLOCK) k_stage1_masked(int nt, const i
     return;
   }
   Mask mk = node_mask(L, hl, eps);
+  if (lin) store_lin(L, lin, t, nt);
   T out[3][4];
   if (SCHEME == RD_N1) {
     for (int i = 0; i < 3; ++i)
@@ -135,7 +137,8 @@ __global__ void __launch_bounds__(ADJ_TRI_BLOCK) k_stage2_masked(int nt, const i
                                                                  const T* __restrict__ Zs, const T* __restrict__ Wn,
                                                                  const T* __restrict__ Ws, const T* __restrict__ rec,
                                                                  Gas<T> gas, T eps, T* __restrict__ share,
-                                                                 DevCtl* ctl, Mask* __restrict__ mask) {
+                                                                 DevCtl* ctl, Mask* __restrict__ mask,
+                                                                 T* __restrict__ lin = nullptr) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
   int v[3];
@@ -156,6 +159,7 @@ __global__ void __launch_bounds__(ADJ_TRI_BLOCK) k_stage2_masked(int nt, const i
     return;
   }
   Mask mk = node_mask(L, hl, eps);
+  if (lin) store_lin(L, lin, t, nt);
   const T idt = rcp(dt);
   T PhiN[3][4], PhiT[4];
   stage2_totals(L, wn, ws, r, __ldg(g.area + t), idt, PhiN, PhiT);
@@ -174,7 +178,7 @@ __global__ void __launch_bounds__(ADJ_TRI_BLOCK) k_stage2_masked(int nt, const i
 }
 
 // adjoint of the stage-2 triangle pass: per corner (Z*, W*, W^n) bars, per triangle the record bar
-template <class T, int SCHEME>
+template <class T, int SCHEME, bool LIN>
 __global__ void __launch_bounds__(ADJ_TRI_BLOCK) k_adj_stage2(int nt, const int* __restrict__ tri, DevGeo<T> g,
                                                               const T* __restrict__ V, const T* __restrict__ Zs,
                                                               const T* __restrict__ Wn, const T* __restrict__ Ws,
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(ADJ_TRI_BLOCK) k_adj_stage2(int nt, const int*
                                                               const Mask* __restrict__ mask,
                                                               const T* __restrict__ lam_next, T dt, T gamma, T eps,
                                                               T* __restrict__ cb2, T* __restrict__ recb,
-                                                              DevCtl* ctl) {
+                                                              DevCtl* ctl, const T* __restrict__ lin = nullptr) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
   int v[3];
@@ -199,8 +203,16 @@ __global__ void __launch_bounds__(ADJ_TRI_BLOCK) k_adj_stage2(int nt, const int*
   }
   for (int k = 0; k < 4; ++k) ld4(rec + (size_t)t * 16 + 4 * k, r + 4 * k);
   T Zsb[3][4], Wnb[3][4], Wsb[3][4], rb[16];
-  int st = stage2_rev<T, SCHEME>(Zc, wn, ws, r, nx, ny, hl, __ldg(g.area + t), dt, gamma, eps, __ldg(mask + t), ob,
-                                 Zsb, Wnb, Wsb, rb);
+  int st;
+  if (LIN) {  // the forward re-run's linearisation of this triangle
+    TriLin<T> L;
+    load_lin(L, lin, t, nt);
+    st = stage2_rev_lin<T, SCHEME>(L, Zc, wn, ws, r, nx, ny, hl, __ldg(g.area + t), dt, gamma, eps, __ldg(mask + t),
+                                   ob, Zsb, Wnb, Wsb, rb);
+  } else {
+    st = stage2_rev<T, SCHEME>(Zc, wn, ws, r, nx, ny, hl, __ldg(g.area + t), dt, gamma, eps, __ldg(mask + t), ob,
+                               Zsb, Wnb, Wsb, rb);
+  }
   if (st) {
     atomicOr(&ctl->status, st);
     return;
@@ -244,13 +256,14 @@ __global__ void __launch_bounds__(ADJ_VTX_BLOCK) k_adj_gather2(int nv, const int
 }
 
 // adjoint of the stage-1 (or forward-Euler) triangle pass: per corner Z^n bar
-template <class T, int SCHEME>
+template <class T, int SCHEME, bool LIN>
 __global__ void __launch_bounds__(ADJ_TRI_BLOCK) k_adj_stage1(int nt, const int* __restrict__ tri, DevGeo<T> g,
                                                               const T* __restrict__ V, const T* __restrict__ Z,
                                                               const Mask* __restrict__ mask,
                                                               const T* __restrict__ lams,
                                                               const T* __restrict__ recb, T dt, T gamma, T eps,
-                                                              T* __restrict__ cb1, DevCtl* ctl) {
+                                                              T* __restrict__ cb1, DevCtl* ctl,
+                                                              const T* __restrict__ lin = nullptr) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
   int v[3];
@@ -269,7 +282,14 @@ __global__ void __launch_bounds__(ADJ_TRI_BLOCK) k_adj_stage1(int nt, const int*
     for (int k = 0; k < 16; ++k) rb[k] = T(0);
   }
   T Zb[3][4];
-  int st = stage1_rev<T, SCHEME>(Zc, nx, ny, hl, gamma, eps, __ldg(mask + t), ob, rb, Zb);
+  int st;
+  if (LIN) {  // the forward re-run's linearisation of this triangle
+    TriLin<T> L;
+    load_lin(L, lin, t, nt);
+    st = stage1_rev_lin<T, SCHEME>(L, Zc, nx, ny, hl, gamma, eps, __ldg(mask + t), ob, rb, Zb);
+  } else {
+    st = stage1_rev<T, SCHEME>(Zc, nx, ny, hl, gamma, eps, __ldg(mask + t), ob, rb, Zb);
+  }
   if (st) {
     atomicOr(&ctl->status, st);
     return;
@@ -322,9 +342,15 @@ struct rd_adjoint_store {
   // from the forward re-run so that the reverse sweep does not recompute stage 1
   DevBuf segZn, segWs, segZs, segRec;
   bool stored = false;
+  // and, when that leaves room, both stages' linearisations of every triangle
+  // and step (LIN_WORDS words each, field-major), so that the reverse kernels
+  // do not linearise again
+  DevBuf segL1, segL2;
+  bool storedL = false;
   ~rd_adjoint_store() {
     DevBuf* b[] = {&dts_dev, &ckpt, &segW, &Zn, &spd, &Ws, &Zs, &R1, &share, &rec, &cfl, &partial, &ctl,
-                   &mask1, &mask2, &lam, &lams, &cb1, &cb2, &recb, &stage, &segZn, &segWs, &segZs, &segRec};
+                   &mask1, &mask2, &lam, &lams, &cb1, &cb2, &recb, &stage, &segZn, &segWs, &segZs, &segRec,
+                   &segL1, &segL2};
     for (DevBuf* d : b) dev_free(*d);
   }
 };
@@ -376,6 +402,21 @@ int ensure(rd_adjoint_store* A, rd_state* s, cudaStream_t st) {
       dev_free(A->segWs);
       dev_free(A->segZs);
       dev_free(A->segRec);
+    }
+  }
+  A->storedL = false;
+  if (A->stored || s->p.scheme == RD_N1) {
+    size_t free_b = 0, total_b = 0;
+    const size_t lin = k * LIN_WORDS * nt * ts;
+    const int nl = s->p.scheme == RD_N1 ? 1 : 2;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && nl * lin <= free_b / 4) {
+      if (dev_alloc(A->segL1, lin, st) == RD_OK && (nl == 1 || dev_alloc(A->segL2, lin, st) == RD_OK))
+        A->storedL = true;
+    }
+    cudaGetLastError();
+    if (!A->storedL) {
+      dev_free(A->segL1);
+      dev_free(A->segL2);
     }
   }
   return RD_OK;
@@ -437,16 +478,18 @@ int backward(rd_state* s, rd_adjoint_store* A, const double* dLdWf, double* dLdW
       T* Wsj = A->stored ? (T*)A->segWs.p + (size_t)j * wsz : Ws;
       T* Zsj = A->stored ? (T*)A->segZs.p + (size_t)j * wsz : Zs;
       T* recj = A->stored ? (T*)A->segRec.p + (size_t)j * 16 * nt : rec;
+      T* lin1 = A->storedL ? (T*)A->segL1.p + (size_t)j * LIN_WORDS * nt : nullptr;
+      T* lin2 = A->storedL && two ? (T*)A->segL2.p + (size_t)j * LIN_WORDS * nt : nullptr;
       k_prepare<T><<<gv, ADJ_VTX_BLOCK, 0, st>>>(nv, Wn, gamma, Znj, spd, ctl);
       k_stage1_masked<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, Znj, spd, Gas<T>::of(gamma), eps, share,
-                                                          recj, cf, ctl, mask1 + (size_t)j * nt);
+                                                          recj, cf, ctl, mask1 + (size_t)j * nt, lin1);
       launch_gather_cfl<T>(VTX_BLOCK, st, nv, ptr, ent, share, cf, V, (T*)A->R1.p, (T*)A->partial.p, cflnum, ctl);
       k_set_dt<<<1, 1, 0, st>>>(ctl, dt);
       if (two) {
         k_update<T><<<gv, ADJ_VTX_BLOCK, 0, st>>>(nv, Wn, (const T*)A->R1.p, ptr, ent, nullptr, V, gamma, Wsj, Zsj,
                                                   nullptr, ctl);
         k_stage2_masked<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, Zsj, Wn, Wsj, recj, Gas<T>::of(gamma), eps,
-                                                            share, ctl, mask2 + (size_t)j * nt);
+                                                            share, ctl, mask2 + (size_t)j * nt, lin2);
         // Z of W^{n+1} is not needed (the next step's k_prepare recomputes it): scratch
         k_update<T><<<gv, ADJ_VTX_BLOCK, 0, st>>>(nv, Wsj, nullptr, ptr, ent, share, V, gamma, Wn1, Zs, nullptr, ctl);
       } else {
@@ -458,6 +501,8 @@ int backward(rd_state* s, rd_adjoint_store* A, const double* dLdWf, double* dLdW
     for (int j = n1 - n0 - 1; j >= 0; --j) {
       const double dt = A->dts[n0 + j];
       T* Wn = segW + (size_t)j * wsz;
+      const T* lin1 = A->storedL ? (const T*)A->segL1.p + (size_t)j * LIN_WORDS * nt : nullptr;
+      const T* lin2 = A->storedL && two ? (const T*)A->segL2.p + (size_t)j * LIN_WORDS * nt : nullptr;
       if (two) {
         T *Znj = Zn, *Wsj = Ws, *Zsj = Zs, *recj = rec;
         if (A->stored) {  // kept by the forward re-run
@@ -468,17 +513,34 @@ int backward(rd_state* s, rd_adjoint_store* A, const double* dLdWf, double* dLdW
         } else {
           stage1_and_wstar(Wn, dt, Ws, Zs);
         }
-        k_adj_stage2<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, V, Zsj, Wn, Wsj, recj, mask2 + (size_t)j * nt,
-                                                          lam, (T)dt, gamma, eps, (T*)A->cb2.p, (T*)A->recb.p, ctl);
+        if (lin2)
+          k_adj_stage2<T, S, true><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, V, Zsj, Wn, Wsj, recj,
+                                                                 mask2 + (size_t)j * nt, lam, (T)dt, gamma, eps,
+                                                                 (T*)A->cb2.p, (T*)A->recb.p, ctl, lin2);
+        else
+          k_adj_stage2<T, S, false><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, V, Zsj, Wn, Wsj, recj,
+                                                                  mask2 + (size_t)j * nt, lam, (T)dt, gamma, eps,
+                                                                  (T*)A->cb2.p, (T*)A->recb.p, ctl, nullptr);
         k_adj_gather2<T><<<gv, ADJ_VTX_BLOCK, 0, st>>>(nv, ptr, ent, (const T*)A->cb2.p, lam, Wsj, gamma, lams);
-        k_adj_stage1<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, V, Znj, mask1 + (size_t)j * nt, lams,
-                                                          (const T*)A->recb.p, (T)dt, gamma, eps, (T*)A->cb1.p, ctl);
+        if (lin1)
+          k_adj_stage1<T, S, true><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, V, Znj, mask1 + (size_t)j * nt, lams,
+                                                                 (const T*)A->recb.p, (T)dt, gamma, eps,
+                                                                 (T*)A->cb1.p, ctl, lin1);
+        else
+          k_adj_stage1<T, S, false><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, V, Znj, mask1 + (size_t)j * nt, lams,
+                                                                  (const T*)A->recb.p, (T)dt, gamma, eps,
+                                                                  (T*)A->cb1.p, ctl, nullptr);
         k_adj_gather1<T><<<gv, ADJ_VTX_BLOCK, 0, st>>>(nv, ptr, ent, (const T*)A->cb1.p, (const T*)A->cb2.p, lams,
                                                        Wn, gamma, lam);
       } else {
         k_prepare<T><<<gv, ADJ_VTX_BLOCK, 0, st>>>(nv, Wn, gamma, Zn, spd, ctl);
-        k_adj_stage1<T, S><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, V, Zn, mask1 + (size_t)j * nt, lam, nullptr,
-                                                          (T)dt, gamma, eps, (T*)A->cb1.p, ctl);
+        if (lin1)
+          k_adj_stage1<T, S, true><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, V, Zn, mask1 + (size_t)j * nt, lam,
+                                                                 nullptr, (T)dt, gamma, eps, (T*)A->cb1.p, ctl, lin1);
+        else
+          k_adj_stage1<T, S, false><<<gt, ADJ_TRI_BLOCK, 0, st>>>(nt, tri, g, V, Zn, mask1 + (size_t)j * nt, lam,
+                                                                  nullptr, (T)dt, gamma, eps, (T*)A->cb1.p, ctl,
+                                                                  nullptr);
         k_adj_gather1<T><<<gv, ADJ_VTX_BLOCK, 0, st>>>(nv, ptr, ent, (const T*)A->cb1.p, nullptr, lam, Wn, gamma,
                                                        lam);
       }

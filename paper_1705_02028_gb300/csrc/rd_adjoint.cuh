@@ -334,12 +334,11 @@ RD_HD void linearise_rev(const T Z[3][4], const T nx[3], const T ny[3], const T 
 
 // Reverse of the stage-1 body (SCHEME RD_B2 / RD_LDA2 / RD_N1).  outb: adjoint of
 // the three shares; recb (two-stage schemes): adjoint of (phi^N_0..2, phi^T).
+// stage1_rev_lin takes the triangle's linearisation L (as linearise computes it
+// from Z) instead of recomputing it.
 template <class T, int SCHEME>
-RD_HD int stage1_rev(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3], T gamma, T eps, Mask mask,
-                     const T outb[3][4], const T recb[16], T Zbar[3][4]) {
-  TriLin<T> L;
-  int st = linearise(Z, nx, ny, hl, gamma, eps, L);
-  if (st) return st;
+RD_HD int stage1_rev_lin(const TriLin<T>& L, const T Z[3][4], const T nx[3], const T ny[3], const T hl[3], T gamma,
+                         T eps, Mask mask, const T outb[3][4], const T recb[16], T Zbar[3][4]) {
   T phiNb[3][4], phiTb[4] = {T(0), T(0), T(0), T(0)}, Mb[4][4];
   RoeBar<T> rb;
   rb.zero();
@@ -379,16 +378,21 @@ RD_HD int stage1_rev(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3
   linearise_rev(Z, nx, ny, hl, gamma, eps, L, mask, phiNb, phiTb, Mb, rb, nb, Zbar);
   return 0;
 }
+template <class T, int SCHEME>
+RD_HD int stage1_rev(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3], T gamma, T eps, Mask mask,
+                     const T outb[3][4], const T recb[16], T Zbar[3][4]) {
+  TriLin<T> L;
+  int st = linearise(Z, nx, ny, hl, gamma, eps, L);
+  if (st) return st;
+  return stage1_rev_lin<T, SCHEME>(L, Z, nx, ny, hl, gamma, eps, mask, outb, recb, Zbar);
+}
 
 // Reverse of the stage-2 body: outputs the adjoints of Z*, W^n, W* (3x4 each)
 // and of the stage-1 record (16).
 template <class T, int SCHEME>
-RD_HD int stage2_rev(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], const T rec[16], const T nx[3],
-                     const T ny[3], const T hl[3], T area, T dt, T gamma, T eps, Mask mask, const T outb[3][4],
-                     T Zsb[3][4], T Wnb[3][4], T Wsb[3][4], T recb[16]) {
-  TriLin<T> L;
-  int st = linearise(Zs, nx, ny, hl, gamma, eps, L);
-  if (st) return st;
+RD_HD int stage2_rev_lin(const TriLin<T>& L, const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], const T rec[16],
+                         const T nx[3], const T ny[3], const T hl[3], T area, T dt, T gamma, T eps, Mask mask,
+                         const T outb[3][4], T Zsb[3][4], T Wnb[3][4], T Wsb[3][4], T recb[16]) {
   const T q = area * (T(1) / T(3)) * rcp(dt);  // |T| / (3 dt), as in stage2_totals
   T PhiN[3][4], PhiT[4];
   stage2_totals(L, Wn, Ws, rec, area, rcp(dt), PhiN, PhiT);
@@ -435,6 +439,16 @@ RD_HD int stage2_rev(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], const
   linearise_rev(Zs, nx, ny, hl, gamma, eps, L, mask, phiNb, phiTb, Mb, rb, nb, Zsb);
   return 0;
 }
+template <class T, int SCHEME>
+RD_HD int stage2_rev(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], const T rec[16], const T nx[3],
+                     const T ny[3], const T hl[3], T area, T dt, T gamma, T eps, Mask mask, const T outb[3][4],
+                     T Zsb[3][4], T Wnb[3][4], T Wsb[3][4], T recb[16]) {
+  TriLin<T> L;
+  int st = linearise(Zs, nx, ny, hl, gamma, eps, L);
+  if (st) return st;
+  return stage2_rev_lin<T, SCHEME>(L, Zs, Wn, Ws, rec, nx, ny, hl, area, dt, gamma, eps, mask, outb, Zsb, Wnb, Wsb,
+                                   recb);
+}
 
 // Mask of a stage-1 / stage-2 evaluation (recomputes the primal of the triangle).
 template <class T, int SCHEME>
@@ -456,6 +470,60 @@ RD_HD Mask stage2_mask(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], con
   T PhiN[3][4], PhiT[4];
   stage2_totals(L, Wn, Ws, rec, area, rcp(dt), PhiN, PhiT);  // as the masked forward kernel
   return m | blend_mask(PhiT, PhiN);
+}
+
+// A triangle's linearisation as LIN_WORDS scalars (the LU pivots packed into
+// the last one), stored field-major (word w of triangle t at w * nt + t) by the
+// forward re-run for the reverse kernels.
+constexpr int LIN_WORDS = 12 + 3 * 11 + 16 + 4 + 4 + 12 + 4 + 4 + 4 + 12 + 4 + 1;
+template <class T, class F>
+__device__ __forceinline__ void lin_fields(TriLin<T>& L, F&& f) {
+  int w = 0;
+  RoeState<T>& r = L.r;
+  f(w++, r.u); f(w++, r.v); f(w++, r.h); f(w++, r.c); f(w++, r.q2h); f(w++, r.ic2);
+  f(w++, r.ic2h); f(w++, r.i2c); f(w++, r.g1); f(w++, r.alpha); f(w++, r.g1u); f(w++, r.g1v);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    NodeSys<T>& n = L.nd[i];
+    f(w++, n.nx); f(w++, n.ny); f(w++, n.w);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      f(w++, n.l3[j]); f(w++, n.s1[j]); f(w++, n.s2[j]); f(w++, n.hp[j]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) f(w++, L.lu.a[a][b]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) f(w++, L.lu.rdiag[k]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) f(w++, L.phiT[k]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) f(w++, L.phiN[i][k]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    f(w++, L.Zb[k]); f(w++, L.gx[k]); f(w++, L.gy[k]); f(w++, L.win[k]);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) f(w++, L.Wh[i][k]);
+}
+template <class T>
+__device__ __forceinline__ void store_lin(TriLin<T>& L, T* __restrict__ out, int t, int nt) {
+  lin_fields(L, [&](int w, T& x) { out[(size_t)w * nt + t] = x; });
+  out[(size_t)(LIN_WORDS - 1) * nt + t] = T(L.lu.piv[0] + 4 * L.lu.piv[1] + 16 * L.lu.piv[2]);
+}
+template <class T>
+__device__ __forceinline__ void load_lin(TriLin<T>& L, const T* __restrict__ in, int t, int nt) {
+  lin_fields(L, [&](int w, T& x) { x = __ldg(in + (size_t)w * nt + t); });
+  const int pk = (int)__ldg(in + (size_t)(LIN_WORDS - 1) * nt + t);
+  L.lu.piv[0] = pk & 3;
+  L.lu.piv[1] = (pk >> 2) & 3;
+  L.lu.piv[2] = (pk >> 4) & 3;
 }
 
 // reverse of vertex_Z: Zb -> Wb += (dZ/dW)^T Zb
