@@ -338,7 +338,8 @@ int rd_probe_fma_peak(int32_t precision, double *flops_per_s);
  * 256 threads and vertex-kernel blocks of 128, 256, 512 and keeps the
  * fastest; then, on meshes of at least 4096 triangles created with a
  * reordering, times the tiled step (rd_state_set_tiling) for a few tile sizes
- * and keeps it if it is faster.  Returns the block choice (either pointer may
+ * and keeps the fastest if it beats the untiled step by 2 % (otherwise the
+ * state is left untiled).  Returns the block choice (either pointer may
  * be NULL; the tiling is read with rd_state_get_tiling).  Results do not
  * depend on the launch shape (every sum has a fixed order). */
 int rd_state_autotune(rd_state *s, int32_t *tri_block, int32_t *vtx_block);
