@@ -85,8 +85,9 @@ def lib():
         _lib.ora_geometry.argtypes = mesh_args + [dp, dp, dp, dp]
         _lib.ora_triangle_terms.argtypes = mesh_args + [dp, ctypes.c_double, ctypes.c_double] + [dp] * 8
         _lib.ora_triangle_terms_ld.argtypes = mesh_args + [dp, ctypes.c_double, ctypes.c_double] + [dp] * 4
-        _lib.ora_stage2_terms.argtypes = mesh_args + [dp, dp, ctypes.c_double, ctypes.c_double,
-                                                      ctypes.c_double, ctypes.c_int] + [dp] * 5
+        for f in (_lib.ora_stage2_terms, _lib.ora_stage2_terms_ld):
+            f.argtypes = mesh_args + [dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int] + [dp] * 5
         _lib.ora_run_bc.argtypes = mesh_args + [dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                 ctypes.c_double, ctypes.c_int32, dp, dp, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_uint8), ctypes.c_int32,
@@ -229,14 +230,15 @@ def stage1_shares(mesh, W, scheme="B2", gamma=1.4, eps=1e-6, nthreads=1, long_do
     return out
 
 
-def stage2_terms(mesh, Wn, Ws, dt, gamma=1.4, eps=1e-6, scheme="B2"):
+def stage2_terms(mesh, Wn, Ws, dt, gamma=1.4, eps=1e-6, scheme="B2", long_double=False):
     keep, margs = _mesh_args(mesh)
     nt = mesh.nt
     a = np.ascontiguousarray(Wn, dtype=np.float64)
     b = np.ascontiguousarray(Ws, dtype=np.float64)
     out = dict(PhiT=np.zeros((nt, 4)), PhiN=np.zeros((nt, 3, 4)), PhiLDA=np.zeros((nt, 3, 4)),
                Phi=np.zeros((nt, 3, 4)), theta=np.zeros((nt, 4)))
-    rc = lib().ora_stage2_terms(*margs, _p(a), _p(b), dt, gamma, eps, scheme_code(scheme),
+    f = lib().ora_stage2_terms_ld if long_double else lib().ora_stage2_terms
+    rc = f(*margs, _p(a), _p(b), dt, gamma, eps, scheme_code(scheme),
                                 _p(out["PhiT"]), _p(out["PhiN"]), _p(out["PhiLDA"]), _p(out["Phi"]),
                                 _p(out["theta"]))
     _check(rc, "ora_stage2_terms")

@@ -1052,24 +1052,36 @@ int ora_triangle_terms(int32_t nv, const double* xy, int32_t nt, const int32_t* 
 int ora_stage2_terms(int32_t nv, const double* xy, int32_t nt, const int32_t* tri,
                      const int8_t* shift, double Lx, double Ly, const double* Wn,
                      const double* Ws, double dt, double gamma, double eps, int scheme,
-                     double* PhiT, double* PhiN, double* PhiLDA, double* Phi, double* theta) {
-  ora::Mesh<double> m;
+                     double* PhiT, double* PhiN, double* PhiLDA, double* Phi, double* theta);
+int ora_stage2_terms_ld(int32_t nv, const double* xy, int32_t nt, const int32_t* tri,
+                        const int8_t* shift, double Lx, double Ly, const double* Wn,
+                        const double* Ws, double dt, double gamma, double eps, int scheme,
+                        double* PhiT, double* PhiN, double* PhiLDA, double* Phi, double* theta);
+
+}  // extern "C"
+
+template <class S>
+int stage2_terms_impl(int32_t nv, const double* xy, int32_t nt, const int32_t* tri, const int8_t* shift, double Lx,
+                      double Ly, const double* Wn, const double* Ws, double dt_d, double gamma_d, double eps_d,
+                      int scheme, double* PhiT, double* PhiN, double* PhiLDA, double* Phi, double* theta) {
+  ora::Mesh<S> m;
   int e = ora::build_mesh(nv, xy, nt, tri, shift, Lx, Ly, m);
   if (e) return e;
-  std::vector<double> Wnv, Wsv, Zn, Zs;
+  const S dt = S(dt_d), gamma = S(gamma_d), eps = S(eps_d);
+  std::vector<S> Wnv, Wsv, Zn, Zs;
   ora::soa_to_aos(Wn, nv, Wnv);
   ora::soa_to_aos(Ws, nv, Wsv);
   e = ora::all_Z(m, Wnv, gamma, Zn);
   if (e) return e;
   e = ora::all_Z(m, Wsv, gamma, Zs);
   if (e) return e;
-  double vrange = 0.0;
+  S vrange = S(0);
   if ((scheme & 0xff) == ora::BX2) {
     e = ora::speed_range(Wsv, gamma, vrange);
     if (e) return e;
   }
   for (int32_t t = 0; t < nt; ++t) {
-    double zn[3][4], zs[3][4], wn[3][4], ws[3][4], n[3][2];
+    S zn[3][4], zs[3][4], wn[3][4], ws[3][4], n[3][2];
     ora::tri_Z(m, Zn, t, zn, n);
     ora::tri_Z(m, Zs, t, zs, n);
     for (int c = 0; c < 3; ++c) {
@@ -1079,25 +1091,39 @@ int ora_stage2_terms(int32_t nv, const double* xy, int32_t nt, const int32_t* tr
         ws[c][k] = Wsv[4 * (size_t)v + k];
       }
     }
-    ora::TriStage2<double> o;
-    double thx = (scheme & 0xff) == ora::BX2 ? ora::bx_theta(m, t, ws, vrange) : 0.0;
+    ora::TriStage2<S> o;
+    S thx = (scheme & 0xff) == ora::BX2 ? ora::bx_theta(m, t, ws, vrange) : S(0);
     e = ora::stage2_triangle(zn, zs, wn, ws, n, m.area[t], dt, gamma, eps, scheme, o, thx);
     if (e) return e;
     for (int k = 0; k < 4; ++k) {
-      if (PhiT) PhiT[4 * (size_t)t + k] = o.PhiT[k];
-      if (theta) theta[4 * (size_t)t + k] = o.theta[k];
+      if (PhiT) PhiT[4 * (size_t)t + k] = ora::val(o.PhiT[k]);
+      if (theta) theta[4 * (size_t)t + k] = ora::val(o.theta[k]);
     }
     for (int c = 0; c < 3; ++c)
       for (int k = 0; k < 4; ++k) {
         size_t ix = 12 * (size_t)t + 4 * c + k;
-        if (PhiN) PhiN[ix] = o.PhiN[c][k];
-        if (PhiLDA) PhiLDA[ix] = o.PhiLDA[c][k];
-        if (Phi) Phi[ix] = o.Phi[c][k];
+        if (PhiN) PhiN[ix] = ora::val(o.PhiN[c][k]);
+        if (PhiLDA) PhiLDA[ix] = ora::val(o.PhiLDA[c][k]);
+        if (Phi) Phi[ix] = ora::val(o.Phi[c][k]);
       }
   }
   return ora::OK;
 }
 
+extern "C" {
+int ora_stage2_terms(int32_t nv, const double* xy, int32_t nt, const int32_t* tri, const int8_t* shift, double Lx,
+                     double Ly, const double* Wn, const double* Ws, double dt, double gamma, double eps, int scheme,
+                     double* PhiT, double* PhiN, double* PhiLDA, double* Phi, double* theta) {
+  return stage2_terms_impl<double>(nv, xy, nt, tri, shift, Lx, Ly, Wn, Ws, dt, gamma, eps, scheme, PhiT, PhiN,
+                                   PhiLDA, Phi, theta);
+}
+int ora_stage2_terms_ld(int32_t nv, const double* xy, int32_t nt, const int32_t* tri, const int8_t* shift,
+                        double Lx, double Ly, const double* Wn, const double* Ws, double dt, double gamma,
+                        double eps, int scheme, double* PhiT, double* PhiN, double* PhiLDA, double* Phi,
+                        double* theta) {
+  return stage2_terms_impl<long double>(nv, xy, nt, tri, shift, Lx, Ly, Wn, Ws, dt, gamma, eps, scheme, PhiT,
+                                        PhiN, PhiLDA, Phi, theta);
+}
 }  // extern "C"
 
 template <class S>

@@ -1,0 +1,96 @@
+"""The CUDA kernels' per-triangle code, compiled for the host, against the oracle
+(no GPU).  `kernel_host_check.cu` runs the very functions the triangle kernels
+call (vertex Z, linearisation, N / LDA / B distribution, stage-2 totals and
+blend) on the CPU in double precision over every triangle of a mesh, with the
+geometry of the library's mesh store; the oracle computes the same stage-1
+shares and stage-2 shares from its own implementation (Sec. 3.2-3.4), in
+double and in long double.  Against the long-double result the kernels'
+double arithmetic must be as accurate as the oracle's own double arithmetic
+(within a factor of 8, and 1e-13 relative in the max norm per component at
+least): triangles where the blend weight divides a small residual by a sum of
+larger ones carry round-off of 1e-11 relative in either implementation.  The
+GPU tests hold the device build of the same code to the oracle; this one
+keeps the algebra pinned in the CPU suite."""
+import os
+import shutil
+import struct
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1705_02028_gb300 import binding, build, inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SCHEME_CODE = {"N1": 0, "B2": 1, "LDA2": 2}
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    binding.load()
+    nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
+    if not nvcc:
+        pytest.skip("nvcc not available")
+    out = str(tmp_path_factory.mktemp("kh") / "kernel_host_check")
+    lib_dir = os.path.dirname(build.LIB)
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-gencode", "arch=compute_103a,code=sm_103a", "-I", build.CSRC,
+                    "-I", os.path.join(ROOT, "include"), os.path.join(HERE, "kernel_host_check.cu"), "-o", out,
+                    "-L", lib_dir, "-lrd", "-Xlinker", "-rpath=" + lib_dir], check=True)
+    return out
+
+
+def _run(harness, mesh, Wn, Ws, dt, scheme, tmp_path, gamma=1.4, eps=1e-6):
+    src, dst = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
+    with open(src, "wb") as f:
+        sh = mesh.shift
+        f.write(struct.pack("<iiddi", mesh.nv, mesh.nt, float(mesh.Lx), float(mesh.Ly), 0 if sh is None else 1))
+        f.write(np.ascontiguousarray(mesh.xy, dtype=np.float64).tobytes())
+        f.write(np.ascontiguousarray(mesh.tri, dtype=np.int32).tobytes())
+        if sh is not None:
+            f.write(np.ascontiguousarray(sh, dtype=np.int8).tobytes())
+        f.write(struct.pack("<dddi", gamma, eps, dt, SCHEME_CODE[scheme]))
+        f.write(np.ascontiguousarray(Wn, dtype=np.float64).tobytes())
+        f.write(np.ascontiguousarray(Ws, dtype=np.float64).tobytes())
+    subprocess.run([harness, src, dst], check=True)
+    a = np.fromfile(dst, dtype=np.float64).reshape(-1, mesh.nt, 3, 4)
+    return a[0], (a[1] if len(a) > 1 else None)
+
+
+def _rel(a, b):
+    scale = np.abs(b).reshape(-1, 4).max(axis=0)
+    return float((np.abs(a - b).reshape(-1, 4).max(axis=0) / scale).max())
+
+
+MESHES = {
+    "grid": lambda: inputs.periodic_grid(20, relabel_seed=6),
+    "jittered": lambda: inputs.jittered_grid(22, 18, 1.0, 0.8, seed=6, diagonal="random", relabel_seed=6),
+}
+STATES = {"khi": inputs.khi_state, "vortex": inputs.vortex_state, "sod": inputs.sod_like_state,
+          "khis": inputs.khi_smooth_state}
+
+
+@pytest.mark.parametrize("scheme", ["N1", "B2", "LDA2"])
+@pytest.mark.parametrize("state", sorted(STATES))
+@pytest.mark.parametrize("kind", sorted(MESHES))
+def test_kernel_bodies_match_the_oracle(harness, kind, state, scheme, tmp_path):
+    mesh = MESHES[kind]()
+    Wn = STATES[state](mesh)
+    # a W* near W^n: density and energy scaled by seeded factors (stays physical)
+    rng = np.random.default_rng(11)
+    Ws = Wn * (1.0 + 1e-3 * rng.standard_normal(Wn.shape[1]))[None, :]
+    dt = 1e-3
+    h1, h2 = _run(harness, mesh, Wn, Ws, dt, scheme, tmp_path)
+    o1 = oracle.stage1_shares(mesh, Wn, scheme)
+    x1 = oracle.stage1_shares(mesh, Wn, scheme, long_double=True)
+    e1, f1 = _rel(h1, x1), _rel(o1, x1)
+    print(f"{kind} {state} {scheme}: stage 1 {e1:.2e} (oracle in double {f1:.2e})", end="")
+    assert e1 <= max(8.0 * f1, 1e-13)
+    if scheme != "N1":
+        o2 = oracle.stage2_terms(mesh, Wn, Ws, dt, scheme=scheme)["Phi"]
+        x2 = oracle.stage2_terms(mesh, Wn, Ws, dt, scheme=scheme, long_double=True)["Phi"]
+        e2, f2 = _rel(h2, x2), _rel(o2, x2)
+        print(f", stage 2 {e2:.2e} (oracle in double {f2:.2e})", end="")
+        assert e2 <= max(8.0 * f2, 1e-13)
+    print()
