@@ -53,3 +53,25 @@ def test_reference_arm_other_ranks_exit_without_work():
         steps = 1
         warmup = 0
     assert bench.reference(A(), 2, 1) is None
+
+
+def test_reference_arm_json_line():
+    """bench.py --impl reference (the oracle on the host cores) prints one JSON line
+    with the contract's keys; it needs no GPU."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.strip().splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    for k in ("metric", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "config", "dtype"):
+        assert k in d, k
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
