@@ -12,7 +12,10 @@ closed-form solutions used by the physics pins.
 
 Parity status of each function (what pins it is listed in the tests):
   run / run_ld / triangle_terms / stage2_terms / time_step / geometry /
-  eigensystem / conserved / run_tangent: pinned (see tests/test_oracle_*.py).
+  eigensystem / conserved: pinned (tests/test_oracle_*.py);
+  run_tangent / dual_eval: pinned by the closed-form derivative rules of each
+  dual-number operation and by central differences of run() with the same
+  frozen dt sequence (tests/test_oracle_tangent.py).
 """
 from __future__ import annotations
 
@@ -98,6 +101,7 @@ def lib():
                                                          dp, ctypes.c_int]
         _lib.ora_eigensystem.argtypes = [ctypes.c_double] * 6 + [dp] * 4
         _lib.ora_conserved.argtypes = mesh_args + [dp, dp]
+        _lib.ora_dual_eval.argtypes = [ctypes.c_int] + [ctypes.c_double] * 4 + [dp]
         _lib.ora_num_threads.restype = ctypes.c_int
     return _lib
 
@@ -168,6 +172,17 @@ def run_tangent(mesh, W0, dW0, dts, scheme="B2", gamma=1.4, eps=1e-6, nthreads=1
     _check(rc, "ora_run_tangent")
     del keep
     return W, dW
+
+
+_DUAL_OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3, "sqrt": 4, "fabs": 5, "neg": 6}
+
+
+def dual_eval(op, a, da, b=0.0, db=0.0):
+    """One operation of the oracle's dual-number type: returns (value, derivative)."""
+    out = np.zeros(2)
+    _check(lib().ora_dual_eval(_DUAL_OPS[op], float(a), float(da), float(b), float(db), _p(out)),
+           "ora_dual_eval")
+    return float(out[0]), float(out[1])
 
 
 def time_step(mesh, W, cfl=0.8, gamma=1.4):

@@ -936,6 +936,27 @@ int ora_run_tangent(int32_t nv, const double* xy, int32_t nt, const int32_t* tri
   return ora::OK;
 }
 
+// One operation of the dual-number type on scalars, for the closed-form unit
+// checks of its derivative rules: op 0 a+b, 1 a-b, 2 a*b, 3 a/b, 4 sqrt(a),
+// 5 |a|, 6 -a.  out = (value, derivative).
+int ora_dual_eval(int op, double av, double ad, double bv, double bd, double* out) {
+  const ora::Dual a(av, ad), b(bv, bd);
+  ora::Dual r;
+  switch (op) {
+    case 0: r = a + b; break;
+    case 1: r = a - b; break;
+    case 2: r = a * b; break;
+    case 3: r = a / b; break;
+    case 4: r = ora::sqrt(a); break;
+    case 5: r = ora::fabs(a); break;
+    case 6: r = -a; break;
+    default: return ora::EINVAL;
+  }
+  out[0] = r.v;
+  out[1] = r.d;
+  return ora::OK;
+}
+
 // CFL time step of state W.
 int ora_time_step(int32_t nv, const double* xy, int32_t nt, const int32_t* tri,
                   const int8_t* shift, double Lx, double Ly, const double* W, double cfl,
