@@ -271,9 +271,18 @@ int rd_cfl_dt(int32_t n_vertex, int32_t n_tri, int32_t precision, const void *W,
  *   - Limit: n_vertex <= 16,777,216 (65536 blocks of 256 vertices); larger
  *     meshes are rejected with RD_EINVAL before any device work.
  *   - The first call on a device, with that device current, looks up the
- *     device address of the array (cudaGetSymbolAddress) and caches it; make
- *     that first call before any stream capture.  Call it with the device
- *     that holds the arrays current.
+ *     device address of the array (cudaGetSymbolAddress) and caches it.  With
+ *     CUDA's lazy module loading (the default since CUDA 12.2) that lookup is
+ *     also what loads the library's device code on that device, which
+ *     allocates the array and may synchronise the device; it can fail with
+ *     RD_ECUDA when another allocator has already reserved the free memory.
+ *     So make one warm-up call per device at set-up, before any stream
+ *     capture and before a caching allocator fills the device; "allocates
+ *     nothing" and "no implicit synchronisation" hold from then on.  Call it
+ *     with the device that holds the arrays current.
+ *   - The cached address belongs to the device's primary context.  After a
+ *     cudaDeviceReset in the calling process the address is stale: do not
+ *     call this entry point on that device again in that process.
  *   - Every call shares the array, which keeps the last call's contents; the
  *     control word is cleared at the start of each call.  Calls whose device
  *     work overlaps (other streams, other host threads) race on the array and
@@ -332,6 +341,16 @@ int rd_count_flops(int32_t scheme, int32_t stage, double out[4]);
 /* FMA throughput of the current device (flop/s, 2 per FMA) measured with a
  * dependent-chain-free FMA kernel; precision RD_FP64 or RD_FP32. */
 int rd_probe_fma_peak(int32_t precision, double *flops_per_s);
+
+/* Element-wise evaluation of an arithmetic helper of the triangle kernels on
+ * device arrays, for tests that hold it against CUDA's IEEE operations:
+ *   RD_MATH_RCP  the double reciprocal the FP64 triangle kernels divide with
+ *                (hardware approximation refined by two Newton-Raphson steps
+ *                for |x| in [2^-1000, 2^1000); IEEE 1/x elsewhere).
+ * x, out: n doubles in device memory (caller-owned); synchronises the stream.
+ * Errors: RD_EINVAL (unknown fn, n < 0, NULL arrays), RD_ECUDA. */
+#define RD_MATH_RCP 0
+int rd_math_eval(int32_t fn, int64_t n, const double *x, double *out, void *cuda_stream);
 
 /* Launch-shape autotuner of one state: times one uncommitted step (the
  * committed state is not changed) for triangle-kernel blocks of 64, 128, 192,

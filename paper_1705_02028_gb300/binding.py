@@ -88,6 +88,7 @@ _SIGS = {
     "rd_state_profile": (ctypes.c_int, [_vp, ctypes.c_int32, _dp, _i32p]),
     "rd_count_flops": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _dp]),
     "rd_probe_fma_peak": (ctypes.c_int, [ctypes.c_int32, _dp]),
+    "rd_math_eval": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp]),
     "rd_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(_vp), ctypes.POINTER(_dp),
                                        ctypes.POINTER(Params), ctypes.POINTER(_vp)]),
     "rd_batch_run": (ctypes.c_int, [_vp, ctypes.c_int32]),
@@ -184,6 +185,22 @@ def probe_fma_peak(precision: str = "fp64") -> float:
     out = ctypes.c_double()
     _check(lib.rd_probe_fma_peak(PRECISIONS[precision], ctypes.byref(out)), "rd_probe_fma_peak")
     return out.value
+
+
+MATH_FNS = {"rcp": 0}
+
+
+def math_eval(fn: str, x):
+    """The triangle kernels' arithmetic helper `fn` applied element-wise to a float64
+    CUDA tensor x (rd_math_eval); returns a new tensor."""
+    torch = _require_gpu()
+    lib = load()
+    x = x.contiguous()
+    out = torch.empty_like(x)
+    st = torch.cuda.current_stream(x.device)
+    _check(lib.rd_math_eval(MATH_FNS[fn], x.numel(), _vp(x.data_ptr()), _vp(out.data_ptr()),
+                            _vp(st.cuda_stream)), "rd_math_eval")
+    return out
 
 
 def cfl_dt(W, tri, lmax, V, csr_ptr, csr_ent, precision="fp64", gamma=1.4, cfl=0.8, stream=None,

@@ -155,3 +155,34 @@ extern "C" int rd_probe_fma_peak(int32_t precision, double* flops_per_s) {
   if (precision == RD_FP32) return probe<float>(400000, flops_per_s);
   return RD_EINVAL;
 }
+
+namespace {
+// Element-wise evaluation of the triangle kernels' own device arithmetic
+// helpers, so that tests can hold them against CUDA's IEEE operations.
+__global__ void k_math_eval(int fn, long long n, const double* __restrict__ x, double* __restrict__ out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a = x[i];
+  double r = 0.0;
+  switch (fn) {
+    case RD_MATH_RCP: r = rd::rcp(a); break;
+    default: break;
+  }
+  out[i] = r;
+}
+}  // namespace
+
+extern "C" int rd_math_eval(int32_t fn, int64_t n, const double* x, double* out, void* cuda_stream) {
+  if (fn != RD_MATH_RCP || n < 0 || (n > 0 && (!x || !out))) return RD_EINVAL;
+  if (n == 0) return RD_OK;
+  const int threads = 256;
+  const long long blocks = (n + threads - 1) / threads;
+  if (blocks > 0x7fffffffLL) return RD_EINVAL;
+  k_math_eval<<<(unsigned)blocks, threads, 0, (cudaStream_t)cuda_stream>>>(fn, n, x, out);
+  if (cudaGetLastError() != cudaSuccess) return RD_ECUDA;
+  if (cudaStreamSynchronize((cudaStream_t)cuda_stream) != cudaSuccess) {
+    cudaGetLastError();
+    return RD_ECUDA;
+  }
+  return RD_OK;
+}

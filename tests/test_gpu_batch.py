@@ -84,3 +84,58 @@ def test_batch_fp32_runs_close_to_fp64(rd):
     b32.run(10)
     for k in range(len(cases)):
         assert rel_max_err(b32.get(k), b64.get(k)) < 1e-4
+
+
+def test_batch_at_benchmark_like_sides_against_the_oracle(rd):
+    """Seven meshes of sides 96..256 (vortex, shear, Sod-like, smooth states; labels
+    scrambled), autotuned launch shapes, B2 FP64 over 20 steps, each mesh against the
+    long-double oracle at 1e-12 (the Sod-like mesh included: 20 steps is within the
+    range where B2's round-off amplification stays below the bar)."""
+    torch, binding = rd
+    import os
+    nth = max(1, min(16, os.cpu_count() or 1))
+    stream = torch.cuda.Stream()
+    big = [(256, "vortex"), (200, "khi"), (144, "sod"), (97, "smooth"), (233, "khi"), (128, "vortex"), (181, "sod")]
+    cases = [make_case(N, kind, 40 + k) for k, (N, kind) in enumerate(big)]
+    meshes = [binding.Mesh(m, stream=stream) for m, _ in cases]
+    b = binding.Batch(meshes, [W for _, W in cases], scheme="B2")
+    b.autotune()
+    steps = 20
+    b.run(steps)
+    t, n = b.time()
+    assert np.all(n == steps)
+    for k, (mesh, W0) in enumerate(cases):
+        Wo, dto = oracle.run(mesh, W0, "B2", nsteps=steps, nthreads=nth, long_double=True)
+        err = rel_max_err(b.get(k), Wo)
+        print(f"batch mesh {k} side {big[k][0]} {big[k][1]}: rel max err vs oracle(ld) {err:.2e}")
+        assert err < 1e-12, k
+        assert t[k] == pytest.approx(dto.sum(), rel=1e-13)
+    b.close()
+
+
+def test_benchmark_batch_sampled_meshes(rd):
+    """The benchmarked batch itself (64 meshes, sides U{128..1024}, seed 2, 55M
+    triangles): after 2 graph-launched steps, the first and last meshes and the
+    meshes on either side of the middle of the concatenated ranges match the
+    oracle at 1e-12 and the plain single-mesh path bitwise."""
+    torch, binding = rd
+    import os
+    nth = max(1, min(16, os.cpu_count() or 1))
+    work = inputs.batch_workload(n_mesh=64, seed=2)
+    stream = torch.cuda.Stream()
+    meshes = [binding.Mesh(m, stream=stream) for m, _, _ in work]
+    b = binding.Batch(meshes, [W for _, W, _ in work], scheme="B2")
+    b.autotune()
+    b.run(2)
+    for k in (0, 31, 32, 63):
+        mesh, W0, _ = work[k]
+        Wb = b.get(k)
+        Wo, _ = oracle.run(mesh, W0, "B2", nsteps=2, nthreads=nth)
+        assert rel_max_err(Wb, Wo) < 1e-12, k
+        s = binding.State(meshes[k], W0, scheme="B2")
+        s.run(2)
+        assert np.array_equal(s.get(), Wb), k
+        s.close()
+    b.close()
+    for m in meshes:
+        m.close()

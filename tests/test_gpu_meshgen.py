@@ -71,3 +71,20 @@ def test_generated_mesh_runs_the_solver(rd):
     assert s.run(60) == 60
     Wld, _ = oracle.run(mesh, W0, "B2", nsteps=60, nthreads=max(1, min(16, os.cpu_count() or 1)), long_double=True)
     assert rel_max_err(s.get(), Wld) < 1e-12
+
+
+def test_benchmark_size_mesh_is_delaunay_and_meets_bounds(rd):
+    """The mesh the benchmark generates (circumradius <= 7.3e-4, beta <= sqrt 2: about
+    1.29 million vertices and 2.58 million triangles, the size of the paper's mesh
+    generation test) passes every check of the exact checker."""
+    R = 7.3e-4
+    mesh, info = rd.meshgen(R)
+    assert info["status"] == 0
+    r = _check(mesh, info, R)
+    print(f"R={R}: {mesh.nv} vertices, {mesh.nt} triangles, {info['rounds']} rounds, {info['flips']} flips; "
+          f"max beta {r['max_beta']:.4f}, min angle {r['min_angle_deg']:.2f} deg, "
+          f"cocircular edges {r['cocircular_edges']}")
+    assert mesh.nv > 1_200_000
+    for key in ("coords_in_box", "all_ccw", "area_tiles_box", "every_edge_has_twin", "euler_torus",
+                "delaunay", "size_bound", "quality_bound"):
+        assert r[key], key

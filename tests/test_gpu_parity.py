@@ -202,15 +202,40 @@ def test_full_size_1024_sod_like_b2(rd):
     assert rel_max_err(s.get(), Wo) < TOL
 
 
-def test_full_size_4096_khi_b2_first_step(rd):
-    """4096x4096 (33.5M triangles) KHI B2: first full step and its dt against the oracle."""
+def test_full_size_4096_khi_b2_first_five_steps(rd):
+    """4096x4096 (33.5M triangles) KHI B2: the first five full steps and each step's dt
+    against the oracle (about 7 s per oracle step on 16 host threads)."""
     mesh = inputs.periodic_grid(4096)
     W0 = inputs.khi_state(mesh)
     m, s = make_state(rd, mesh, W0, "B2")
-    dt = s.step(return_dt=True)
-    Wo, dto = oracle.run(mesh, W0, "B2", nsteps=1, nthreads=NTH)
-    assert dt == pytest.approx(dto[0], rel=1e-14)
-    assert rel_max_err(s.get(), Wo) < TOL
+    dts = [s.step(return_dt=True) for _ in range(5)]
+    Wo, dto = oracle.run(mesh, W0, "B2", nsteps=5, nthreads=NTH)
+    assert np.allclose(dts, dto, rtol=1e-14, atol=0)
+    err = rel_max_err(s.get(), Wo)
+    print(f"4096^2 KHI B2, 5 steps: rel max err vs oracle {err:.2e}")
+    assert err < TOL
+
+
+def test_full_size_1024_sod_like_fp32_l1_over_500_steps(rd):
+    """1024x1024 Sod-like B2 over the full 500 steps: the FP32 path's L1 density error
+    against the FP64 oracle, printed beside the FP64 path's own L1 distance to the
+    oracle (B2 amplifies round-off on this state, so even FP64 parts from the oracle
+    over 500 steps; the L1 norm, not the max norm, is the stated measure here)."""
+    mesh = inputs.periodic_grid(1024, relabel_seed=6)
+    W0 = inputs.sod_like_state(mesh)
+    Wo, _ = oracle.run(mesh, W0, "B2", nsteps=500, nthreads=NTH)
+    V = oracle.geometry(mesh)["V"]
+    out = {}
+    for prec in ("fp32", "fp64"):
+        m, s = make_state(rd, mesh, W0, "B2", precision=prec)
+        assert s.run(500) == 500
+        out[prec] = exact.l1_error(V, s.get()[0], Wo[0])
+        s.close()
+        m.close()
+    print(f"1024^2 Sod-like B2, 500 steps: L1 density error vs FP64 oracle: FP32 {out['fp32']:.3e}, "
+          f"FP64 {out['fp64']:.3e}")
+    assert out["fp32"] < 5e-3
+    assert out["fp64"] < out["fp32"]
 
 
 def test_full_size_4096_in_the_benchmarked_configuration(rd):

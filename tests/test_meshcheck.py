@@ -64,3 +64,48 @@ def test_quality_measures():
     # right isosceles triangles with legs h: circumradius h / sqrt 2, beta = 1 / sqrt 2, min angle 45 deg
     assert r["size_bound"] and r["quality_bound"]
     assert abs(r["min_angle_deg"] - 45.0) < 1e-6
+
+
+def test_filtered_predicates_equal_the_integer_definitions():
+    """The vectorised Orient2D / InCircle2D (int64, and a double-precision filter with
+    an error bound) give the signs of the plain Python-integer determinants: on random
+    points at the generator's coordinate scale (2^30 per period), on exactly
+    cocircular quadruples (integer points on x^2 + y^2 = 5^2 13^2 17^2 scaled up) and
+    on quadruples one unit off a circle, where the double evaluation alone is unsure."""
+    rng = np.random.default_rng(3)
+    n = 20000
+    pts = rng.integers(-(1 << 30), 1 << 30, size=(4, n, 2), dtype=np.int64)
+    assert np.array_equal(meshcheck.orient_sign(*pts[:3]), meshcheck._orient_sign_exact(*pts[:3]))
+    assert np.array_equal(meshcheck.incircle_sign(*pts), meshcheck._incircle_sign_exact(*pts))
+    # integer points on one circle of radius 1105 (many Pythagorean representations)
+    r = 1105
+    circ = [(x, y) for x in range(-r, r + 1) for y in (int(round((r * r - x * x) ** 0.5)),)
+            if x * x + y * y == r * r]
+    circ = np.array(circ + [(x, -y) for x, y in circ], dtype=np.int64)
+    idx = rng.integers(0, len(circ), size=(4, 4000))
+    scale = 1 << 17                                    # coordinates up to ~2^27, lifts up to ~2^55
+    off = rng.integers(-(1 << 28), 1 << 28, size=(1, 4000, 2), dtype=np.int64)
+    q = circ[idx] * scale + off
+    # order a, b, c counter-clockwise where they are not collinear
+    o = meshcheck._orient_sign_exact(q[0], q[1], q[2])
+    q[1, o < 0], q[2, o < 0] = q[2, o < 0].copy(), q[1, o < 0].copy()
+    exact = meshcheck._incircle_sign_exact(*q)
+    assert np.array_equal(meshcheck.incircle_sign(*q), exact)
+    assert np.sum(exact == 0) > 100                    # cocircular cases were exercised
+    q2 = q.copy()
+    q2[3, :, 0] += 1                                   # one unit off the circle
+    assert np.array_equal(meshcheck.incircle_sign(*q2), meshcheck._incircle_sign_exact(*q2))
+
+
+def test_edge_map_finds_twins_and_flags_duplicates():
+    m = inputs.jittered_grid(7, jitter=0.1, diagonal="delaunay", relabel_seed=4)
+    nbr, nc = meshcheck.edge_map(m.tri, m.shift)
+    assert np.all(nbr >= 0)
+    t = np.arange(m.nt)[:, None].repeat(3, 1)
+    k = np.arange(3)[None, :].repeat(m.nt, 0)
+    assert np.array_equal(nbr[nbr, nc], t) and np.array_equal(nc[nbr, nc], k)   # twin of twin
+    # a triangle listed twice: its edges no longer have a unique twin
+    tri = np.concatenate([m.tri, m.tri[:1]])
+    sh = np.concatenate([m.shift, m.shift[:1]])
+    nbr2, _ = meshcheck.edge_map(tri, sh)
+    assert np.all(nbr2[0] < 0) and np.all(nbr2[-1] < 0)

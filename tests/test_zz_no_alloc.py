@@ -31,7 +31,50 @@ def test_noalloc_matches_allocating_entry_point_twice(N, state):
         second = binding.cfl_dt(*args, precision=prec, entry="rd_cfl_dt_noalloc")
         assert first == pytest.approx(ref, rel=tol, abs=0)
         assert second == pytest.approx(ref, rel=tol, abs=0)
+        if prec == "fp64":
+            # the FP64 variant against the oracle's CFL step directly
+            assert first == pytest.approx(oracle.time_step(mesh, W), rel=1e-14, abs=0)
     assert ref == pytest.approx(oracle.time_step(mesh, W), rel=1e-6)
+
+
+def test_noalloc_asks_the_installed_allocator_for_nothing():
+    """With a counting allocator installed, rd_cfl_dt_noalloc makes no allocation or
+    release while rd_cfl_dt (which takes its scratch from the allocator) makes some;
+    both return the same dt.  The binding's allocator is put back afterwards."""
+    torch = require_gpu()
+    from paper_1705_02028_gb300 import binding
+    lib = binding.load()
+    binding.use_torch_allocator()
+    counts = {"alloc": 0, "free": 0}
+
+    def _alloc(nbytes, stream, ctx):
+        counts["alloc"] += 1
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, ctx):
+        counts["free"] += 1
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    refs = (binding.ALLOC_FN(_alloc), binding.FREE_FN(_free))
+    mesh = inputs.periodic_grid(96, relabel_seed=5)
+    W = inputs.khi_state(mesh)
+    a = mesh_device_arrays(mesh, torch, torch.float64)
+    Wd = torch.tensor(W, dtype=torch.float64, device="cuda")
+    args = (Wd, a["tri"], a["lmax"], a["V"], a["csr_ptr"], a["csr_ent"])
+    binding.cfl_dt(*args, entry="rd_cfl_dt_noalloc")  # set-up call on this device
+    assert lib.rd_set_allocator(refs[0], refs[1], None) == binding.RD_OK
+    try:
+        dt_free = [binding.cfl_dt(*args, entry="rd_cfl_dt_noalloc") for _ in range(2)]
+        assert counts == {"alloc": 0, "free": 0}
+        dt_ref = binding.cfl_dt(*args)
+        assert counts["alloc"] >= 1 and counts["free"] == counts["alloc"]
+    finally:
+        prev = binding._alloc_refs
+        assert lib.rd_set_allocator(prev[0], prev[1], None) == binding.RD_OK
+    assert dt_free[0] == dt_ref and dt_free[1] == dt_ref
 
 
 def test_noalloc_rejects_meshes_beyond_its_limit():
