@@ -99,6 +99,10 @@ def parse():
     ap.add_argument("--reorder", choices=["none", "morton", "rcm"], default="morton",
                     help="vertex/triangle reordering of the mesh store")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 companion measurement")
+    ap.add_argument("--no-df64", action="store_true",
+                    help="skip the RD_DF64 companion measurement (FP64 state, double-float triangle algebra)")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the accuracy leg (FP32 L1 density error and DF64 difference against FP64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form companion measurement")
     ap.add_argument("--no-autotune", action="store_true")
@@ -399,6 +403,31 @@ def ours(args, ws, rank, local):
                                      "traffic": ncu_traffic(args.workload, "fp32", d32, nt)},
                         "step_hbm_frac_of_measured": sb32 * nt / (ms32 * 1e-3) / 1e9 / hbm}
         s32.close()
+    # RD_DF64 companion: the same step with the triangle algebra in double-float
+    if not args.no_df64 and args.precision == "fp64":
+        sdf, msdf, pkdf, _ = run_state_timing(binding, m, W0, scheme, "df64", args.steps, args.warmup, ws,
+                                              autotune=not args.no_autotune, tiling="none")
+        msdf = max_over_ranks(msdf / args.steps, ws)
+        ddf = max(pkdf, key=pkdf.get)
+        stage_df = 1 if ddf in ("tri_stage1", "tile_stage1") else 2
+        fl_df = binding.count_flops(flop_scheme(scheme), stage_df)["total"] if ddf.startswith("tri_") else None
+        fp64_peak = binding.probe_fma_peak("fp64")
+        fp32_peak = binding.probe_fma_peak("fp32")
+        eq = fl_df * nt / (pkdf[ddf] * 1e-3) if fl_df else None
+        line["df64"] = {"value": ws * nt / (msdf * 1e-3), "ms_per_step": msdf, "per_kernel_ms": pkdf,
+                        "vs_fp64_step": ms_step / msdf,
+                        "launch_shapes": {"tri_block": sdf.shapes[0], "vtx_block": sdf.shapes[1]}
+                        if sdf.shapes else None,
+                        "dominant_kernel": ddf,
+                        "counted_fp64_equivalent_tflops": eq / 1e12 if eq else None,
+                        "vs_measured_fp64_fma_peak": eq / fp64_peak if eq else None,
+                        "measured_fp32_fma_peak_tflops": fp32_peak / 1e12,
+                        "note": "FP64 state and vertex kernels; per-triangle algebra in double-float (FP32 pairs) "
+                                "on the nodal differences; parity-tested against the oracle at the FP64 bar (1e-12)"}
+        sdf.close()
+
+    if not args.no_accuracy and args.precision == "fp64":
+        line["accuracy"] = accuracy_leg(binding, m, W0, scheme, nt, mesh)
     m.close()
 
     if not args.no_batched and args.workload != "batch64_B2":
@@ -413,6 +442,35 @@ def ours(args, ws, rank, local):
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     return line
+
+
+def accuracy_leg(binding, m, W0, scheme, nt, mesh, steps=20):
+    """FP32 L1 density error and the RD_DF64 max-norm difference, both against the
+    FP64 path (itself held to the oracle at 1e-12 by the parity tests), after
+    `steps` steps from the workload's initial state."""
+    import numpy as np
+    out = {"steps": steps, "reference": "FP64 GPU path, same steps (parity-tested against the oracle at 1e-12)"}
+    ref = binding.State(m, W0, scheme=scheme, precision="fp64")
+    ref.run(steps)
+    W64 = ref.get()
+    ref.close()
+    # nodal volumes V_i = sum |T| / 3 for the L1 norm of Sec. 5.1.1
+    P = mesh.xy[mesh.tri] + (mesh.shift * np.array([mesh.Lx, mesh.Ly]) if mesh.shift is not None else 0.0)
+    area = 0.5 * ((P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1]) -
+                  (P[:, 2, 0] - P[:, 0, 0]) * (P[:, 1, 1] - P[:, 0, 1]))
+    V = np.zeros(mesh.nv)
+    np.add.at(V, mesh.tri.ravel(), np.repeat(area / 3.0, 3))
+    for prec in ("fp32", "df64"):
+        s = binding.State(m, W0, scheme=scheme, precision=prec)
+        s.run(steps)
+        W = s.get()
+        s.close()
+        if prec == "fp32":
+            out["fp32_l1_density_error"] = float(np.sum(V * np.abs(W[0] - W64[0])) / np.sum(V))
+        else:
+            scale = np.maximum(np.abs(W64).max(axis=1), np.abs(W64[3]).max())
+            out["df64_max_rel_difference"] = float((np.abs(W - W64).max(axis=1) / scale).max())
+    return out
 
 
 def batched(args, ws, steps):

@@ -68,6 +68,16 @@ extern "C" {
 /* ---- arithmetic precision of the device path --------------------------- */
 #define RD_FP64 0
 #define RD_FP32 1
+/* RD_DF64: FP64 state and FP64 vertex kernels (gathers, updates, dt), with
+ * the per-triangle algebra run in double-float arithmetic (pairs of FP32
+ * numbers, about 48 significant bits) on the FP32 pipe.  Per triangle the
+ * nodal mean Zbar, the differences Z_i - Zbar and (stage 2) W*_i - W^n_i are
+ * formed in FP64 first, so the double-float arithmetic acts on the
+ * differences that carry the residual.  Same arrays, arguments and results
+ * as RD_FP64 to within round-off.  The untiled per-triangle step only: no
+ * tiling (RD_ENOTSUP), no batched form (RD_EINVAL) and no adjoint
+ * (RD_ENOTSUP). */
+#define RD_DF64 2
 
 /* ---- vertex / triangle reordering applied inside the mesh store -------- */
 #define RD_ORDER_NONE 0

@@ -18,7 +18,7 @@ from . import build as _build
 RD_OK, RD_EINVAL, RD_ENOMEM, RD_ECUDA, RD_ENONPHYSICAL, RD_ETIMEOUT, RD_ENOTSUP = range(7)
 SCHEMES = {"N1": 0, "B2": 1, "LDA2": 2, "BMAX2": 3, "BMIN2": 4, "BX2": 5}
 LUMPING = {"global": 0, "selective": 1}
-PRECISIONS = {"fp64": 0, "fp32": 1}
+PRECISIONS = {"fp64": 0, "fp32": 1, "df64": 2}
 ORDERS = {"none": 0, "morton": 1, "rcm": 2}
 
 _lib = None

@@ -559,7 +559,8 @@ int backward(rd_state* s, rd_adjoint_store* A, const double* dLdWf, double* dLdW
 }  // namespace
 
 extern "C" int rd_adjoint_forward(rd_state* s, int32_t n_steps, int32_t ckpt_every, double* dts_out) {
-  if (s && (s->p.scheme > RD_LDA2 || s->p.lumping != RD_LUMP_GLOBAL || s->m->n_ghost || s->m->n_wall))
+  if (s && (s->p.scheme > RD_LDA2 || s->p.lumping != RD_LUMP_GLOBAL || s->m->n_ghost || s->m->n_wall ||
+            s->p.precision == RD_DF64))
     return RD_ENOTSUP;
   if (!s || n_steps < 1 || ckpt_every < 1) return RD_EINVAL;
   rd_mesh* m = s->m;
@@ -604,7 +605,8 @@ extern "C" int rd_adjoint_forward(rd_state* s, int32_t n_steps, int32_t ckpt_eve
 }
 
 extern "C" int rd_adjoint_backward(rd_state* s, const double* dL_dW_final, double* dL_dW0) {
-  if (s && (s->p.scheme > RD_LDA2 || s->p.lumping != RD_LUMP_GLOBAL || s->m->n_ghost || s->m->n_wall))
+  if (s && (s->p.scheme > RD_LDA2 || s->p.lumping != RD_LUMP_GLOBAL || s->m->n_ghost || s->m->n_wall ||
+            s->p.precision == RD_DF64))
     return RD_ENOTSUP;
   if (!s || !dL_dW_final || !dL_dW0 || !s->adj || s->adj->n_steps < 1) return RD_EINVAL;
   rd_adjoint_store* A = s->adj;
@@ -672,7 +674,8 @@ int branch_masks(rd_state* s, uint64_t* mask1, uint64_t* mask2) {
 }  // namespace
 
 extern "C" int rd_state_branch_masks(rd_state* s, uint64_t* mask1, uint64_t* mask2) {
-  if (s && (s->p.scheme > RD_LDA2 || s->p.lumping != RD_LUMP_GLOBAL || s->m->n_ghost || s->m->n_wall))
+  if (s && (s->p.scheme > RD_LDA2 || s->p.lumping != RD_LUMP_GLOBAL || s->m->n_ghost || s->m->n_wall ||
+            s->p.precision == RD_DF64))
     return RD_ENOTSUP;
   if (!s) return RD_EINVAL;
   cudaStream_t st = s->m->stream;

@@ -186,7 +186,7 @@ bool valid_params(const rd_params* p) {
   if (p->lumping != RD_LUMP_GLOBAL && p->lumping != RD_LUMP_SELECTIVE) return false;
   if (p->lumping == RD_LUMP_SELECTIVE && p->scheme == RD_N1) return false;
   if (p->reserved != 0) return false;
-  if (p->precision != RD_FP64 && p->precision != RD_FP32) return false;
+  if (p->precision != RD_FP64 && p->precision != RD_FP32 && p->precision != RD_DF64) return false;
   if (!(p->cfl > 0.0) || !(p->gamma > 1.0) || !(p->eps_fix >= 0.0)) return false;
   if (!std::isfinite(p->cfl) || !std::isfinite(p->gamma) || !std::isfinite(p->eps_fix)) return false;
   return true;
@@ -275,9 +275,13 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
   ba2.vr = vr1;
   mark(0);
   const bool tiled = s->tiles != nullptr;
+  const bool df = sizeof(T) == 8 && s->p.precision == RD_DF64;
   if (tiled) {
     CK(tiled_stage1<T>(s, a, ev));
   } else {
+  if (df) {
+    CK(launch_tri_stage1_df(s, a, gt, TB, st));
+  } else
   switch (s->p.scheme) {
     case RD_N1:
       k_tri_stage1<T, RD_N1><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, nullptr, cf, ctl);
@@ -315,7 +319,9 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
     k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)s->W[a].p, (const T*)s->R1.p, ptr, ent, nullptr, V, gamma,
                                           (T*)s->Ws.p, (T*)s->Zs.p, nullptr, ctl, nullptr, nullptr, vr1, wa1);
     mark(3);
-    if (s->p.scheme == RD_LDA2)
+    if (df)
+      CK(launch_tri_stage2_df(s, a, gt, TB, st));
+    else if (s->p.scheme == RD_LDA2)
       k_tri_stage2<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
                                                   (const T*)s->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl,
                                                   nullptr, nullptr, ba2);
@@ -501,7 +507,7 @@ extern "C" int rd_state_init(rd_mesh* m, const double* W, const rd_params* p, rd
   if (!s) return RD_ENOMEM;
   s->m = m;
   s->p = *p;
-  s->pi = p->precision == RD_FP64 ? 0 : 1;
+  s->pi = p->precision == RD_FP32 ? 1 : 0;  // RD_DF64 keeps the FP64 state
   s->ts = s->pi == 0 ? sizeof(double) : sizeof(float);
   int st = s->pi == 0 ? mesh_geometry<double>(m) : mesh_geometry<float>(m);
   if (st == RD_OK) st = alloc_state(s);
@@ -647,7 +653,7 @@ extern "C" int rd_state_autotune(rd_state* s, int32_t* tri_block, int32_t* vtx_b
   s->tri_block = best_t;
   s->vtx_block = best_v;
   // tiled step: a few tile sizes against the untiled step with the shapes above
-  if (rc == RD_OK && s->m->h.nt >= 4096) {
+  if (rc == RD_OK && s->m->h.nt >= 4096 && s->p.precision != RD_DF64) {
     float untiled = 1e30f;
     rc = rd_state_set_tiling(s, 0, 0);
     if (rc == RD_OK) rc = time_step(best_t, best_v, untiled);

@@ -102,6 +102,13 @@ struct rd_mesh {
   bool wgeo_ready[2] = {false, false};
 };
 
+namespace rd {
+// Triangle kernels of an RD_DF64 state (rd_df64.cu): stage 1 reads buffer a,
+// stage 2 reads W^n from buffer a and W*, Z* from the stage scratch.
+int launch_tri_stage1_df(const rd_state* s, int a, unsigned grid, int block, cudaStream_t st);
+int launch_tri_stage2_df(const rd_state* s, int a, unsigned grid, int block, cudaStream_t st);
+}
+
 // The state handle: double-buffered vertex state, step scratch and the device
 // control block (dt, time, step count, status).
 struct rd_state {

@@ -1,0 +1,238 @@
+// rd_df64.cu -- triangle kernels of the RD_DF64 precision: FP64 state, FP64
+// vertex kernels, per-triangle algebra (Sec. 3.2-3.4) in double-float.
+//
+// GB300 runs FP64 at 1/64 of its FP32 rate and the FP64 triangle kernels keep
+// the FP64 pipe ~90 % busy.  These kernels form, in double precision, only
+// the quantities whose cancellation carries the residual -- the nodal mean
+// Zbar and the differences Z_i - Zbar of each triangle, and in stage 2 the
+// state change W*_i - W^n_i -- and run everything else (Roe state, eigen-split,
+// phi^T, the 4x4 LU, N / LDA / blend, stage-2 totals) in double-float
+// arithmetic (rd_dfloat.cuh) on the FP32 pipe.  Inputs and outputs keep the
+// FP64 layout of the plain step, so the gathers, updates and the dt reduction
+// are the FP64 ones; the stage-2 record phi^N(W^n), phi^T(W^n) stays in
+// double-float (two floats per value: the bytes of one double).
+#include <cuda_runtime.h>
+
+#include "rd_device.h"
+#include "rd_dfloat.cuh"
+#include "rd_internal.h"
+#include "rd_kernels.cuh"
+#include "rd_tiled.h"
+
+namespace rd {
+
+namespace {
+
+__device__ __forceinline__ dfloat to_df(double x) {
+  const float h = __double2float_rn(x);
+  return dfloat(h, __double2float_rn(x - (double)h));
+}
+__device__ __forceinline__ double from_df(dfloat a) { return (double)a.hi + (double)a.lo; }
+
+// Zbar (double, then split) and dZ_i = Z_i - Zbar of one triangle.
+__device__ __forceinline__ void split_nodal(const double Z[3][4], dfloat Zb[4], dfloat dZ[3][4]) {
+  const double third = 1.0 / 3.0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double zb = (Z[0][k] + Z[1][k] + Z[2][k]) * third;
+    Zb[k] = to_df(zb);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dZ[c][k] = to_df(Z[c][k] - zb);
+  }
+}
+
+// 16-value stage-2 record in double-float: 32 floats, eight 16-byte vectors.
+__device__ __forceinline__ void st_rec(dfloat* p, const dfloat r[16]) {
+  float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) q[k] = make_float4(r[2 * k].hi, r[2 * k].lo, r[2 * k + 1].hi, r[2 * k + 1].lo);
+}
+__device__ __forceinline__ void ld_rec(const dfloat* p, dfloat r[16]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float4 a = __ldg(q + k);
+    r[2 * k] = dfloat(a.x, a.y);
+    r[2 * k + 1] = dfloat(a.z, a.w);
+  }
+}
+
+template <int SCHEME>
+__global__ void __launch_bounds__(256, 1)
+    k_tri_stage1_df(int nt, const int* __restrict__ tri, DevGeo<double> g, const double* __restrict__ Z,
+                    const double* __restrict__ spd, Gas<dfloat> gas, dfloat eps, double* __restrict__ share,
+                    dfloat* __restrict__ rec, double* __restrict__ cfl, DevCtl* ctl, BlendArgs<double> ba) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt || ctl->stop) return;
+  int v[3];
+  double nx[3], ny[3], hl[3], Zc[3][4];
+  load_tri(t, nt, tri, g, v, nx, ny, hl);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) load_vec4(Z, v[c], Zc[c]);
+  {
+    double s0 = __ldg(spd + v[0]), s1 = __ldg(spd + v[1]), s2 = __ldg(spd + v[2]);
+    double lam = mag_less(s1, s0) ? s0 : s1;  // speeds are >= 0
+    lam = mag_less(s2, lam) ? lam : s2;
+    cfl[t] = __ldg(g.lmax + t) * lam;
+  }
+  const int mode = SCHEME == RD_BMAX2 ? ba.mode : BLEND_B;
+  double thx = 0.0;
+  if (SCHEME == RD_BMAX2 && mode == BLEND_X)
+    thx = bx_theta(Zc, nx, ny, hl, __ldg(g.area + t), ba.L, vrange_of<double>(ba.vr));
+  dfloat Zb[4], dZ[3][4], nxd[3], nyd[3], hld[3];
+  split_nodal(Zc, Zb, dZ);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    nxd[c] = to_df(nx[c]);
+    nyd[c] = to_df(ny[c]);
+    hld[c] = to_df(hl[c]);
+  }
+  dfloat out[3][4], r[16];
+  int st = stage1_body_d<dfloat, SCHEME>(Zb, dZ, nxd, nyd, hld, gas, eps, out, r, mode, to_df(thx));
+  if (st) {
+    atomicOr(&ctl->status, st);
+    return;
+  }
+  if (SCHEME != RD_N1) st_rec(rec + (size_t)t * 16, r);
+  double* sp = share + (size_t)t * 12;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double o[4] = {from_df(out[i][0]), from_df(out[i][1]), from_df(out[i][2]), from_df(out[i][3])};
+    st4(sp + 4 * i, o);
+  }
+}
+
+template <int SCHEME>
+__global__ void __launch_bounds__(256, 1)
+    k_tri_stage2_df(int nt, const int* __restrict__ tri, DevGeo<double> g, const double* __restrict__ Zs,
+                    const double* __restrict__ Wn, const double* __restrict__ Ws, const dfloat* __restrict__ rec,
+                    Gas<dfloat> gas, dfloat eps, double* __restrict__ share, DevCtl* ctl, BlendArgs<double> ba) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt || ctl->stop) return;
+  int v[3];
+  double nx[3], ny[3], hl[3], Zc[3][4];
+  load_tri(t, nt, tri, g, v, nx, ny, hl);
+  dfloat dW[3][4];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double wn[4], ws[4];
+    load_vec4(Zs, v[c], Zc[c]);
+    load_vec4(Wn, v[c], wn);
+    load_vec4(Ws, v[c], ws);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dW[c][k] = to_df(ws[k] - wn[k]);
+  }
+  dfloat r[16];
+  ld_rec(rec + (size_t)t * 16, r);
+  const double area = __ldg(g.area + t);
+  const int mode = SCHEME == RD_BMAX2 ? ba.mode : BLEND_B;
+  const int sl = (SCHEME == RD_BMAX2 || SCHEME == RD_LDA2) ? ba.sl : 0;
+  double thx = 0.0;
+  if (SCHEME == RD_BMAX2 && mode == BLEND_X) thx = bx_theta(Zc, nx, ny, hl, area, ba.L, vrange_of<double>(ba.vr));
+  dfloat Zb[4], dZ[3][4], nxd[3], nyd[3], hld[3];
+  split_nodal(Zc, Zb, dZ);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    nxd[c] = to_df(nx[c]);
+    nyd[c] = to_df(ny[c]);
+    hld[c] = to_df(hl[c]);
+  }
+  dfloat out[3][4];
+  int st = stage2_body_d<dfloat, SCHEME>(Zb, dZ, dW, r, nxd, nyd, hld, to_df(area), to_df(ctl->dt), gas, eps, out,
+                                         mode, to_df(thx), sl);
+  if (st) {
+    atomicOr(&ctl->status, st);
+    return;
+  }
+  double* sp = share + (size_t)t * 12;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double o[4] = {from_df(out[i][0]), from_df(out[i][1]), from_df(out[i][2]), from_df(out[i][3])};
+    st4(sp + 4 * i, o);
+  }
+}
+
+Gas<dfloat> gas_df(double gamma) {
+  Gas<dfloat> q;
+  q.gamma = dfloat(gamma);
+  q.g1 = dfloat(gamma - 1.0);
+  q.g = dfloat((gamma - 1.0) / gamma);
+  q.ig = dfloat(1.0 / gamma);
+  return q;
+}
+
+}  // namespace
+
+// Stage-1 triangle kernel of an RD_DF64 state (the FP64 kernel's arguments).
+int launch_tri_stage1_df(const rd_state* s, int a, unsigned grid, int block, cudaStream_t st) {
+  const rd_mesh* m = s->m;
+  const int nt = m->h.nt;
+  DevGeo<double> g;
+  g.nx = (const double*)m->geo[0][0].p;
+  g.ny = (const double*)m->geo[0][1].p;
+  g.hl = (const double*)m->geo[0][2].p;
+  g.area = (const double*)m->geo[0][3].p;
+  g.lmax = (const double*)m->geo[0][4].p;
+  const int* tri = (const int*)m->tri.p;
+  DevCtl* ctl = (DevCtl*)s->ctl.p;
+  const Gas<dfloat> gas = gas_df(s->p.gamma);
+  const dfloat eps(s->p.eps_fix);
+  const double* Za = (const double*)s->Z[a].p;
+  const double* Sa = (const double*)s->spd[a].p;
+  double* share = (double*)s->share.p;
+  dfloat* rec = (dfloat*)s->rec.p;
+  double* cf = (double*)s->cfl.p;
+  BlendArgs<double> ba = tile_blend_args<double>(s);
+  unsigned long long* vr0 = (unsigned long long*)s->vr.p;
+  ba.vr = vr0;
+  switch (s->p.scheme) {
+    case RD_N1:
+      k_tri_stage1_df<RD_N1><<<grid, block, 0, st>>>(nt, tri, g, Za, Sa, gas, eps, share, nullptr, cf, ctl, ba);
+      break;
+    case RD_LDA2:
+      k_tri_stage1_df<RD_LDA2><<<grid, block, 0, st>>>(nt, tri, g, Za, Sa, gas, eps, share, rec, cf, ctl, ba);
+      break;
+    default:
+      if (s->p.scheme == RD_B2 && s->p.lumping == RD_LUMP_GLOBAL)
+        k_tri_stage1_df<RD_B2><<<grid, block, 0, st>>>(nt, tri, g, Za, Sa, gas, eps, share, rec, cf, ctl, ba);
+      else
+        k_tri_stage1_df<RD_BMAX2><<<grid, block, 0, st>>>(nt, tri, g, Za, Sa, gas, eps, share, rec, cf, ctl, ba);
+      break;
+  }
+  CU(cudaGetLastError());
+  return RD_OK;
+}
+
+// Stage-2 triangle kernel of an RD_DF64 state reading W^n from buffer a.
+int launch_tri_stage2_df(const rd_state* s, int a, unsigned grid, int block, cudaStream_t st) {
+  const rd_mesh* m = s->m;
+  const int nt = m->h.nt;
+  DevGeo<double> g;
+  g.nx = (const double*)m->geo[0][0].p;
+  g.ny = (const double*)m->geo[0][1].p;
+  g.hl = (const double*)m->geo[0][2].p;
+  g.area = (const double*)m->geo[0][3].p;
+  g.lmax = (const double*)m->geo[0][4].p;
+  const int* tri = (const int*)m->tri.p;
+  DevCtl* ctl = (DevCtl*)s->ctl.p;
+  const Gas<dfloat> gas = gas_df(s->p.gamma);
+  const dfloat eps(s->p.eps_fix);
+  const double* Zs = (const double*)s->Zs.p;
+  const double* Wn = (const double*)s->W[a].p;
+  const double* Ws = (const double*)s->Ws.p;
+  const dfloat* rec = (const dfloat*)s->rec.p;
+  double* share = (double*)s->share.p;
+  BlendArgs<double> ba = tile_blend_args<double>(s);
+  unsigned long long* vr0 = (unsigned long long*)s->vr.p;
+  ba.vr = vr0 ? vr0 + 2 : nullptr;
+  if (s->p.scheme == RD_LDA2)
+    k_tri_stage2_df<RD_LDA2><<<grid, block, 0, st>>>(nt, tri, g, Zs, Wn, Ws, rec, gas, eps, share, ctl, ba);
+  else if (s->p.scheme == RD_B2 && s->p.lumping == RD_LUMP_GLOBAL)
+    k_tri_stage2_df<RD_B2><<<grid, block, 0, st>>>(nt, tri, g, Zs, Wn, Ws, rec, gas, eps, share, ctl, ba);
+  else
+    k_tri_stage2_df<RD_BMAX2><<<grid, block, 0, st>>>(nt, tri, g, Zs, Wn, Ws, rec, gas, eps, share, ctl, ba);
+  CU(cudaGetLastError());
+  return RD_OK;
+}
+
+}  // namespace rd

@@ -341,13 +341,20 @@ struct TriLin {
   T Zb[4], gx[4], gy[4], Wh[3][4], win[4];
 };
 
+// Core of the linearisation.  Zb is the nodal mean Zbar; Z are the nodal
+// values entering phi^T = dF/dZ(Zbar) sum_i (n_i/2) Z_i + ... and the
+// linearised states W^_i = dW/dZ(Zbar) Z_i.  Because sum_i n_i = 0 and the N
+// scheme only sees differences W^_i - W^_j, the nodal values may be given
+// relative to any common reference: linearise() passes Z_i itself; the
+// double-float kernels pass Z_i - Zbar, formed in double precision, so that
+// their 48-bit arithmetic acts on the differences (which carry the residual)
+// rather than on the full states (App. A algebra unchanged).
 template <class T>
-RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3],
-                                         const Gas<T>& gas, T eps, TriLin<T>& L) {
-  const T third = T(1) / T(3);
+RD_HD int linearise_core(const T Zbar[4], const T Z[3][4], const T nx[3], const T ny[3], const T hl[3],
+                         const Gas<T>& gas, T eps, TriLin<T>& L) {
   T* Zb = L.Zb;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) Zb[k] = (Z[0][k] + Z[1][k] + Z[2][k]) * third;
+  for (int k = 0; k < 4; ++k) Zb[k] = Zbar[k];
   RoeState<T>& r = L.r;
   r.g1 = gas.g1;
   T iz = rcp(Zb[0]);
@@ -517,6 +524,16 @@ RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3]
 }
 
 template <class T>
+RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3],
+                    const Gas<T>& gas, T eps, TriLin<T>& L) {
+  const T third = T(1) / T(3);
+  T Zb[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Zb[k] = (Z[0][k] + Z[1][k] + Z[2][k]) * third;
+  return linearise_core(Zb, Z, nx, ny, hl, gas, eps, L);
+}
+
+template <class T>
 RD_HD int linearise(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3], T gamma, T eps, TriLin<T>& L) {
   return linearise(Z, nx, ny, hl, Gas<T>::of(gamma), eps, L);
 }
@@ -647,17 +664,38 @@ __device__ __forceinline__ void load_vec4(const T* __restrict__ A, int i, T out[
 // RD_LDA2 -> phi^LDA, RD_B2 -> phi^B (Sec. 3.3).  rec (two-stage schemes):
 // phi^N_0..2 and phi^T at W^n, reused by stage 2.  Returns an ST_* status.
 template <class T, int SCHEME>
+RD_HD void stage1_shares(const TriLin<T>& L, T out[3][4], T rec[16], int bmode, T theta_x);
+
+template <class T, int SCHEME>
 RD_HD int stage1_body(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3], const Gas<T>& gas, T eps,
                       T out[3][4], T rec[16], int bmode = BLEND_B, T theta_x = T(0)) {
   TriLin<T> L;
   int st = linearise(Z, nx, ny, hl, gas, eps, L);
   if (st) return st;
+  stage1_shares<T, SCHEME>(L, out, rec, bmode, theta_x);
+  return 0;
+}
+
+// Stage-1 shares from a linearisation given as Zbar and the nodal differences
+// dZ_i = Z_i - Zbar (the double-float kernels).
+template <class T, int SCHEME>
+RD_HD int stage1_body_d(const T Zb[4], const T dZ[3][4], const T nx[3], const T ny[3], const T hl[3],
+                        const Gas<T>& gas, T eps, T out[3][4], T rec[16], int bmode = BLEND_B, T theta_x = T(0)) {
+  TriLin<T> L;
+  int st = linearise_core(Zb, dZ, nx, ny, hl, gas, eps, L);
+  if (st) return st;
+  stage1_shares<T, SCHEME>(L, out, rec, bmode, theta_x);
+  return 0;
+}
+
+template <class T, int SCHEME>
+RD_HD void stage1_shares(const TriLin<T>& L, T out[3][4], T rec[16], int bmode, T theta_x) {
   if (SCHEME == RD_N1) {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int k = 0; k < 4; ++k) out[i][k] = L.phiN[i][k];
-    return 0;
+    return;
   }
   T lda[3][4];
   lda_apply(L, L.phiT, lda);
@@ -675,7 +713,7 @@ RD_HD int stage1_body(const T Z[3][4], const T nx[3], const T ny[3], const T hl[
     for (int k = 0; k < 4; ++k) rec[4 * i + k] = L.phiN[i][k];
 #pragma unroll
   for (int k = 0; k < 4; ++k) rec[12 + k] = L.phiT[k];
-  return 0;
+  return;
 }
 
 // Stage 2 (Sec. 3.4): total residuals at (W^n, W*).
@@ -685,6 +723,26 @@ RD_HD int stage1_body(const T Z[3][4], const T nx[3], const T ny[3], const T hl[
 //   Phi_i     = Theta Phi^N_i + (I - Theta) Phi^LDA_i, Theta from (Phi^T, Phi^N)
 // Total residuals of stage 2 from the W* linearisation L, the stage-1 record
 // and the mass term (m = |T|/3 (W* - W^n) / dt).
+// dW[i][k] = W*_i - W^n_i (formed by the caller; the double-float kernels form it
+// in double precision).
+template <class T>
+RD_HD void stage2_totals_dw(const TriLin<T>& L, const T dW[3][4], const T rec[16], T area, T idt, T PhiN[3][4],
+                            T PhiT[4]) {
+  const T q = area * (T(1) / T(3)) * idt;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) PhiT[k] = T(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      T m = dW[i][k] * q;
+      PhiN[i][k] = m + (L.phiN[i][k] + rec[4 * i + k]) * T(0.5);
+      PhiT[k] += m;
+    }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) PhiT[k] += (rec[12 + k] + L.phiT[k]) * T(0.5);
+}
+
 template <class T>
 RD_HD void stage2_totals(const TriLin<T>& L, const T Wn[3][4], const T Ws[3][4], const T rec[16], T area, T idt,
                          T PhiN[3][4], T PhiT[4]) {
@@ -704,6 +762,10 @@ RD_HD void stage2_totals(const TriLin<T>& L, const T Wn[3][4], const T Ws[3][4],
 }
 
 template <class T, int SCHEME>
+RD_HD void stage2_shares(const TriLin<T>& L, const T PhiN[3][4], const T PhiT[4], const T dW[3][4], T area, T idt,
+                         T out[3][4], int bmode, T theta_x, int sl);
+
+template <class T, int SCHEME>
 RD_HD int stage2_body(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], const T rec[16], const T nx[3],
                       const T ny[3], const T hl[3], T area, T dt, const Gas<T>& gas, T eps, T out[3][4],
                       int bmode = BLEND_B, T theta_x = T(0), int sl = 0) {
@@ -713,6 +775,36 @@ RD_HD int stage2_body(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], cons
   T idt = rcp(dt);
   T PhiN[3][4], PhiT[4];
   stage2_totals(L, Wn, Ws, rec, area, idt, PhiN, PhiT);
+  T dW[3][4];
+  if (sl) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) dW[i][k] = Ws[i][k] - Wn[i][k];
+  }
+  stage2_shares<T, SCHEME>(L, PhiN, PhiT, dW, area, idt, out, bmode, theta_x, sl);
+  return 0;
+}
+
+// Stage-2 shares from the W* linearisation given as Zbar* and dZ*_i = Z*_i - Zbar*,
+// and dW_i = W*_i - W^n_i (the double-float kernels).
+template <class T, int SCHEME>
+RD_HD int stage2_body_d(const T Zbs[4], const T dZs[3][4], const T dW[3][4], const T rec[16], const T nx[3],
+                        const T ny[3], const T hl[3], T area, T dt, const Gas<T>& gas, T eps, T out[3][4],
+                        int bmode = BLEND_B, T theta_x = T(0), int sl = 0) {
+  TriLin<T> L;
+  int st = linearise_core(Zbs, dZs, nx, ny, hl, gas, eps, L);
+  if (st) return st;
+  T idt = rcp(dt);
+  T PhiN[3][4], PhiT[4];
+  stage2_totals_dw(L, dW, rec, area, idt, PhiN, PhiT);
+  stage2_shares<T, SCHEME>(L, PhiN, PhiT, dW, area, idt, out, bmode, theta_x, sl);
+  return 0;
+}
+
+template <class T, int SCHEME>
+RD_HD void stage2_shares(const TriLin<T>& L, const T PhiN[3][4], const T PhiT[4], const T dW[3][4], T area, T idt,
+                         T out[3][4], int bmode, T theta_x, int sl) {
   T lda[3][4];
   lda_apply(L, PhiT, lda);
   if (SCHEME == RD_LDA2) {
@@ -729,14 +821,13 @@ RD_HD int stage2_body(const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], cons
     const T q = area * T(0.25) * idt, tw = area * (T(1) / T(12)) * idt;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      T d0 = Ws[0][k] - Wn[0][k], d1 = Ws[1][k] - Wn[1][k], d2 = Ws[2][k] - Wn[2][k];
+      T d0 = dW[0][k], d1 = dW[1][k], d2 = dW[2][k];
       T sum = tw * (d0 + d1 + d2);
       out[0][k] += q * d0 - sum;
       out[1][k] += q * d1 - sum;
       out[2][k] += q * d2 - sum;
     }
   }
-  return 0;
 }
 
 template <class T, int SCHEME>

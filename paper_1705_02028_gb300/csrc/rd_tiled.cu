@@ -615,6 +615,7 @@ extern "C" int rd_state_set_tiling(rd_state* s, int32_t tile_triangles, int32_t 
       s->tiles = nullptr;
     }
   } else {
+    if (s->p.precision == RD_DF64) return RD_ENOTSUP;  // the double-float kernels are untiled
     if (threads < 32 || threads > TILE_MAX_THREADS || threads % 32) return RD_EINVAL;
     if (tile_triangles < 32 || tile_triangles > MAX_TILE_TRIANGLES || tile_triangles % 32) return RD_EINVAL;
     TilePlanHost hp;

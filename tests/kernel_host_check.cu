@@ -1,6 +1,8 @@
 // Host build of the triangle kernels' per-triangle code (the same functions the
 // CUDA kernels run, compiled for the CPU), for the CPU test that holds them to
-// the oracle's per-triangle shares without a GPU.
+// the oracle's per-triangle shares without a GPU.  Scheme codes + 16 select the
+// double-float bodies of the RD_DF64 kernels (Zbar, Z_i - Zbar and W*_i - W^n_i
+// formed in double, the rest in double-float), as rd_df64.cu calls them.
 //
 // Input (binary): nv, nt, Lx, Ly, has_shift, xy, tri, shift as in
 // tile_plan_check.cpp, then gamma, eps, dt (double), scheme (int32: 0 N1,
@@ -11,8 +13,60 @@
 #include <cstdlib>
 #include <vector>
 
+#include "rd_dfloat.cuh"
 #include "rd_internal.h"
 #include "rd_kernels.cuh"
+
+template <int SCHEME>
+static int run_df(const rd::HostMesh& h, const std::vector<double>& Wn, const std::vector<double>& Ws, double gamma,
+                  double eps, double dt, std::vector<double>& s1, std::vector<double>& s2) {
+  using rd::dfloat;
+  const int nt = h.nt, nv = h.nv;
+  rd::Gas<dfloat> gas;
+  gas.gamma = dfloat(gamma);
+  gas.g1 = dfloat(gamma - 1.0);
+  gas.g = dfloat((gamma - 1.0) / gamma);
+  gas.ig = dfloat(1.0 / gamma);
+  for (int t = 0; t < nt; ++t) {
+    double Zn[3][4], Zs[3][4], wn[3][4], ws[3][4];
+    dfloat nx[3], ny[3], hl[3];
+    for (int c = 0; c < 3; ++c) {
+      const int vi = h.tri[(size_t)c * nt + t], vc = h.vperm[vi];
+      for (int k = 0; k < 4; ++k) {
+        wn[c][k] = Wn[(size_t)k * nv + vc];
+        ws[c][k] = Ws[(size_t)k * nv + vc];
+      }
+      double sp;
+      if (!rd::vertex_Z(wn[c], gamma, Zn[c], sp) || !rd::vertex_Z(ws[c], gamma, Zs[c], sp)) return 2;
+      nx[c] = dfloat(h.nx[(size_t)c * nt + t]);
+      ny[c] = dfloat(h.ny[(size_t)c * nt + t]);
+      hl[c] = dfloat(h.hl[(size_t)c * nt + t]);
+    }
+    dfloat Zb[4], dZ[3][4], Zbs[4], dZs[3][4], dW[3][4], out[3][4], rec[16];
+    for (int k = 0; k < 4; ++k) {
+      const double zb = (Zn[0][k] + Zn[1][k] + Zn[2][k]) * (1.0 / 3.0);
+      const double zs = (Zs[0][k] + Zs[1][k] + Zs[2][k]) * (1.0 / 3.0);
+      Zb[k] = dfloat(zb);
+      Zbs[k] = dfloat(zs);
+      for (int c = 0; c < 3; ++c) {
+        dZ[c][k] = dfloat(Zn[c][k] - zb);
+        dZs[c][k] = dfloat(Zs[c][k] - zs);
+        dW[c][k] = dfloat(ws[c][k] - wn[c][k]);
+      }
+    }
+    if (rd::stage1_body_d<dfloat, SCHEME>(Zb, dZ, nx, ny, hl, gas, dfloat(eps), out, rec)) return 3;
+    const size_t tc = (size_t)h.tperm[t];
+    for (int c = 0; c < 3; ++c)
+      for (int k = 0; k < 4; ++k) s1[12 * tc + 4 * c + k] = (double)out[c][k];
+    if (SCHEME == RD_N1) continue;
+    if (rd::stage2_body_d<dfloat, SCHEME>(Zbs, dZs, dW, rec, nx, ny, hl, dfloat(h.area[t]), dfloat(dt), gas,
+                                          dfloat(eps), out))
+      return 4;
+    for (int c = 0; c < 3; ++c)
+      for (int k = 0; k < 4; ++k) s2[12 * tc + 4 * c + k] = (double)out[c][k];
+  }
+  return 0;
+}
 
 template <int SCHEME>
 static int run(const rd::HostMesh& h, const std::vector<double>& Wn, const std::vector<double>& Ws, double gamma,
@@ -69,9 +123,17 @@ int main(int argc, char** argv) {
   if (rd::build_host_mesh(nv, xy.data(), nt, tri.data(), has_shift ? sh.data() : nullptr, Lx, Ly, RD_ORDER_MORTON, h))
     return 1;
   std::vector<double> s1(12 * (size_t)nt, 0.0), s2(12 * (size_t)nt, 0.0);
-  int rc = scheme == 0 ? run<RD_N1>(h, Wn, Ws, gamma, eps, dt, s1, s2)
-           : scheme == 1 ? run<RD_B2>(h, Wn, Ws, gamma, eps, dt, s1, s2)
-                         : run<RD_LDA2>(h, Wn, Ws, gamma, eps, dt, s1, s2);
+  const bool df = (scheme & 16) != 0;
+  scheme &= 15;
+  int rc;
+  if (df)
+    rc = scheme == 0 ? run_df<RD_N1>(h, Wn, Ws, gamma, eps, dt, s1, s2)
+         : scheme == 1 ? run_df<RD_B2>(h, Wn, Ws, gamma, eps, dt, s1, s2)
+                       : run_df<RD_LDA2>(h, Wn, Ws, gamma, eps, dt, s1, s2);
+  else
+    rc = scheme == 0 ? run<RD_N1>(h, Wn, Ws, gamma, eps, dt, s1, s2)
+         : scheme == 1 ? run<RD_B2>(h, Wn, Ws, gamma, eps, dt, s1, s2)
+                       : run<RD_LDA2>(h, Wn, Ws, gamma, eps, dt, s1, s2);
   if (rc) return rc;
   FILE* o = std::fopen(argv[2], "wb");
   if (!o) return 2;

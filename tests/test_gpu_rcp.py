@@ -39,10 +39,17 @@ def test_rcp_against_ieee_division_on_random_doubles():
     got = binding.math_eval("rcp", xd).cpu().numpy()
     ieee = (1.0 / xd).cpu().numpy()
     ulp = _ulp_distance(got, ieee)
-    mism = int((ulp != 0).sum())
-    print(f"rcp vs IEEE 1/x on {n} doubles: {mism} differ, max {int(ulp.max())} ulp")
+    mism_rand = int((ulp[8192:] != 0).sum())
+    mism_pow2 = int((ulp[:4096] != 0).sum())
+    mism_ones = int((ulp[4096:8192] != 0).sum())
+    print(f"rcp vs IEEE 1/x: random mantissas {mism_rand} of {n - 8192} differ, powers of two {mism_pow2} of 4096, "
+          f"all-ones mantissas {mism_ones} of 4096; max {int(ulp.max())} ulp")
+    # two Newton steps from the hardware approximation leave the result within one ulp
+    # of the correctly rounded 1/x (measured: bitwise equal on random mantissas and on
+    # powers of two; one ulp on mantissas of all ones, just below a power of two)
     assert int(ulp.max()) <= 1
-    assert mism <= n // 10000
+    assert mism_rand <= (n - 8192) // 10000
+    assert mism_pow2 == 0
 
 
 def test_rcp_edges_take_the_ieee_division():
