@@ -302,6 +302,69 @@ int rd_cfl_dt_noalloc(int32_t n_vertex, int32_t n_tri, int32_t precision, const 
                       const void *lmax, const void *V, const int32_t *csr_ptr, const int32_t *csr_ent,
                       double gamma, double cfl, double *dt_out, void *cuda_stream);
 
+/* ---- vertex-partitioned step (one part per GPU) ------------------------------
+ * The step of Sec. 3.4 (Fig. of the paper's GPU data flow, Sec. 4.2) reads per
+ * triangle the states of its three corners and gathers the shares per vertex.
+ * Part r of P owns the contiguous internal vertex range
+ * [r nv / P, (r + 1) nv / P) of the mesh store's Morton (or RCM) order and
+ * computes every triangle with an owned corner (triangles on a part boundary
+ * are computed by each part that touches them, from identical inputs); the
+ * other corners of those triangles are its ghost vertices.  Per step the
+ * caller moves the ghosts' W^n (before stage 1) and W* (before stage 2) from
+ * their owners and replaces each part's CFL dt by the minimum over the parts;
+ * the owned vertices then equal the single-part step bitwise.
+ *
+ * rd_partition_plan: the plan of part `part` of `n_parts` on the host only (no
+ *   GPU needed), for the mesh given as to rd_mesh_create.  sizes[4] =
+ *   {owned, ghosts, local triangles, send entries}; call once with the array
+ *   pointers NULL to get the sizes, then with arrays of those sizes:
+ *   local_vertices [owned + ghosts] caller vertex ids (owned first, ghosts in
+ *   ascending internal order); local_triangles [local triangles] caller ids;
+ *   local_corners [3][local triangles] local vertex ids; csr_ptr [owned + 1],
+ *   csr_ent [..]: owned vertex -> local (triangle, corner) entries 3 k + c in
+ *   the global CSR order; send_ptr [n_parts + 1], send_idx [send entries]:
+ *   owned local vertices to send to each part, in that part's ghost order;
+ *   recv_ptr [n_parts + 1]: the ghost slots [recv_ptr[q], recv_ptr[q+1])
+ *   (counted from the first ghost) that part q owns.
+ * rd_part_create: part `part` of `n_parts` of a state on mesh m (periodic
+ *   meshes; RD_BX2, whose blend needs the global |v| range, and meshes with
+ *   boundary conditions return RD_ENOTSUP), initialised from the full state W
+ *   (host, caller order, component-major).  The plan is rd_partition_plan's.
+ * rd_part_phase: one phase of a step on the mesh's stream, in this order:
+ *   RD_PART_PACK_W (buf: device [send entries][4] of the state's word type,
+ *   written), exchange, RD_PART_UNPACK_W (buf: device [ghosts][4], read),
+ *   RD_PART_STAGE1, dt <- min over parts (rd_part_dt_device / rd_part_set_dt),
+ *   RD_PART_UPDATE1 (N1: the step is complete), RD_PART_PACK_WS, exchange,
+ *   RD_PART_UNPACK_WS, RD_PART_STAGE2.  buf is ignored by the other phases.
+ * rd_part_dt_device: device address of this part's dt (one double), for an
+ *   in-place all-reduce (min) between RD_PART_STAGE1 and RD_PART_UPDATE1.
+ * rd_part_get_dt / rd_part_set_dt: the same through the host (synchronising).
+ * rd_part_get_owned: W of the owned vertices, [4][owned] host, in the order
+ *   of local_vertices.  rd_part_status: time, step count and status.       */
+typedef struct rd_part rd_part;
+#define RD_PART_PACK_W 0
+#define RD_PART_UNPACK_W 1
+#define RD_PART_STAGE1 2
+#define RD_PART_UPDATE1 3
+#define RD_PART_PACK_WS 4
+#define RD_PART_UNPACK_WS 5
+#define RD_PART_STAGE2 6
+int rd_partition_plan(int32_t n_vertex, const double *xy, int32_t n_tri, const int32_t *tri,
+                      const int8_t *image_shift, double Lx, double Ly, int32_t reorder, int32_t n_parts,
+                      int32_t part, int32_t sizes[4], int32_t *local_vertices, int32_t *local_triangles,
+                      int32_t *local_corners, int32_t *csr_ptr, int32_t *csr_ent, int32_t *send_ptr,
+                      int32_t *send_idx, int32_t *recv_ptr);
+int rd_part_create(rd_mesh *m, int32_t n_parts, int32_t part, const double *W, const rd_params *p, rd_part **out);
+int rd_part_sizes(const rd_part *q, int32_t sizes[4]);
+int rd_part_lists(const rd_part *q, int32_t *local_vertices, int32_t *send_ptr, int32_t *recv_ptr);
+int rd_part_phase(rd_part *q, int32_t phase, void *buf);
+int rd_part_dt_device(rd_part *q, void **dt);
+int rd_part_get_dt(const rd_part *q, double *dt);
+int rd_part_set_dt(rd_part *q, double dt);
+int rd_part_get_owned(const rd_part *q, double *W_out);
+int rd_part_status(const rd_part *q, double *t, int64_t *steps);
+void rd_part_destroy(rd_part *q);
+
 /* ---- discrete adjoint of a rollout ------------------------------------------
  * rd_adjoint_forward: advance s by n_steps ordinary steps (CFL dt), recording
  * every step's dt (dts_out, nullable, [n_steps] host) and keeping the state

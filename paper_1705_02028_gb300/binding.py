@@ -106,6 +106,20 @@ _SIGS = {
     "rd_batch_sizes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "rd_batch_autotune": (ctypes.c_int, [_vp, _i32p, _i32p]),
     "rd_batch_profile": (ctypes.c_int, [_vp, ctypes.c_int32, _dp]),
+    "rd_partition_plan": (ctypes.c_int, [ctypes.c_int32, _dp, ctypes.c_int32, _i32p, _i8p, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _i32p,
+                                         _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p]),
+    "rd_part_create": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _dp, ctypes.POINTER(Params),
+                                      ctypes.POINTER(_vp)]),
+    "rd_part_sizes": (ctypes.c_int, [_vp, _i32p]),
+    "rd_part_lists": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p]),
+    "rd_part_phase": (ctypes.c_int, [_vp, ctypes.c_int32, _vp]),
+    "rd_part_dt_device": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
+    "rd_part_get_dt": (ctypes.c_int, [_vp, _dp]),
+    "rd_part_set_dt": (ctypes.c_int, [_vp, ctypes.c_double]),
+    "rd_part_get_owned": (ctypes.c_int, [_vp, _dp]),
+    "rd_part_status": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_int64)]),
+    "rd_part_destroy": (None, [_vp]),
 }
 
 
@@ -558,3 +572,195 @@ def meshgen(max_circumradius: float, Lx: float = 1.0, Ly: float = 1.0, quality: 
                 unit=lx.value / px.value,
                 ms=dict(zip(("quality_locate", "cavities", "insert", "flips", "total"), ms.tolist())))
     return mesh, info
+
+
+# ---------------------------------------------------------------------------
+# vertex-partitioned step (rd_partition_plan, rd_part_*)
+# ---------------------------------------------------------------------------
+PART_PACK_W, PART_UNPACK_W, PART_STAGE1, PART_UPDATE1, PART_PACK_WS, PART_UNPACK_WS, PART_STAGE2 = range(7)
+
+
+def partition_plan(mesh, n_parts: int, part: int, reorder: str = "morton") -> dict:
+    """Plan of one part of a vertex partition, computed on the host (no GPU needed)."""
+    lib = load()
+    xy = np.ascontiguousarray(mesh.xy, dtype=np.float64)
+    tri = np.ascontiguousarray(mesh.tri, dtype=np.int32)
+    sh = None if mesh.shift is None else np.ascontiguousarray(mesh.shift, dtype=np.int8)
+    args = (int(mesh.nv), _ptr(xy), int(mesh.nt), _ptr(tri, ctypes.c_int32), _ptr(sh, ctypes.c_int8),
+            float(mesh.Lx), float(mesh.Ly), ORDERS[reorder], int(n_parts), int(part))
+    sizes = np.zeros(4, dtype=np.int32)
+    i32 = lambda a: _ptr(a, ctypes.c_int32)
+    _check(lib.rd_partition_plan(*args, i32(sizes), *([None] * 8)), "rd_partition_plan")
+    n_own, n_gh, nlt, n_send = (int(x) for x in sizes)
+    out = dict(n_owned=n_own, n_ghost=n_gh, n_local_tri=nlt, n_send=n_send,
+               local_vertices=np.empty(n_own + n_gh, np.int32), local_triangles=np.empty(nlt, np.int32),
+               local_corners=np.empty((3, nlt), np.int32), csr_ptr=np.empty(n_own + 1, np.int32),
+               csr_ent=np.empty(0, np.int32), send_ptr=np.empty(n_parts + 1, np.int32),
+               send_idx=np.empty(n_send, np.int32), recv_ptr=np.empty(n_parts + 1, np.int32))
+    _check(lib.rd_partition_plan(*args, i32(sizes), None, None, None, i32(out["csr_ptr"]), None, None, None, None),
+           "rd_partition_plan")
+    out["csr_ent"] = np.empty(int(out["csr_ptr"][-1]), np.int32)
+    _check(lib.rd_partition_plan(*args, i32(sizes), i32(out["local_vertices"]), i32(out["local_triangles"]),
+                                 i32(out["local_corners"]), i32(out["csr_ptr"]), i32(out["csr_ent"]),
+                                 i32(out["send_ptr"]), i32(out["send_idx"]), i32(out["recv_ptr"])),
+           "rd_partition_plan")
+    return out
+
+
+class Part:
+    """One part of a vertex-partitioned state (rd_part_create ... rd_part_destroy)."""
+
+    def __init__(self, mesh: Mesh, n_parts: int, part: int, W, scheme="B2", precision="fp64", cfl=0.8, gamma=1.4,
+                 eps_fix=1e-6, lumping="global"):
+        torch = _require_gpu()
+        load()
+        self.mesh = mesh
+        self.n_parts, self.part = int(n_parts), int(part)
+        self.params = _params(scheme, precision, cfl, gamma, eps_fix, lumping)
+        self.two_stage = self.params.scheme != SCHEMES["N1"]
+        Wc = np.ascontiguousarray(W, dtype=np.float64)
+        if Wc.shape != (4, mesh.nv):
+            raise ValueError(f"W must have shape (4, {mesh.nv})")
+        h = _vp()
+        _check(_lib.rd_part_create(mesh.handle, self.n_parts, self.part, _ptr(Wc), ctypes.byref(self.params),
+                                   ctypes.byref(h)), "rd_part_create")
+        self.handle = h
+        sz = np.zeros(4, dtype=np.int32)
+        _check(_lib.rd_part_sizes(h, _ptr(sz, ctypes.c_int32)), "rd_part_sizes")
+        self.n_owned, self.n_ghost, self.n_local_tri, self.n_send = (int(x) for x in sz)
+        self.local_vertices = np.empty(self.n_owned + self.n_ghost, np.int32)
+        self.send_ptr = np.empty(self.n_parts + 1, np.int32)
+        self.recv_ptr = np.empty(self.n_parts + 1, np.int32)
+        _check(_lib.rd_part_lists(h, _ptr(self.local_vertices, ctypes.c_int32), _ptr(self.send_ptr, ctypes.c_int32),
+                                  _ptr(self.recv_ptr, ctypes.c_int32)), "rd_part_lists")
+        dtype = torch.float32 if self.params.precision == PRECISIONS["fp32"] else torch.float64
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.send_buf = torch.empty((max(self.n_send, 1), 4), dtype=dtype, device=dev)
+        self.recv_buf = torch.empty((max(self.n_ghost, 1), 4), dtype=dtype, device=dev)
+        dp = _vp()
+        _check(_lib.rd_part_dt_device(h, ctypes.byref(dp)), "rd_part_dt_device")
+        self._dt_ptr = dp.value
+
+    def phase(self, ph: int, buf=None):
+        _check(_lib.rd_part_phase(self.handle, int(ph), _vp(buf.data_ptr()) if buf is not None else None),
+               "rd_part_phase")
+
+    def dt_tensor(self):
+        """A one-element float64 CUDA tensor viewing this part's dt in place (for an all-reduce)."""
+        import torch
+
+        class _View:
+            pass
+        v = _View()
+        v.__cuda_array_interface__ = {"shape": (1,), "typestr": "<f8", "data": (self._dt_ptr, False), "version": 3}
+        return torch.as_tensor(v, device=torch.device("cuda", torch.cuda.current_device()))
+
+    def get_dt(self) -> float:
+        out = ctypes.c_double()
+        _check(_lib.rd_part_get_dt(self.handle, ctypes.byref(out)), "rd_part_get_dt")
+        return out.value
+
+    def set_dt(self, dt: float):
+        _check(_lib.rd_part_set_dt(self.handle, float(dt)), "rd_part_set_dt")
+
+    def owned(self) -> np.ndarray:
+        W = np.empty((4, self.n_owned))
+        _check(_lib.rd_part_get_owned(self.handle, _ptr(W)), "rd_part_get_owned")
+        return W
+
+    def status(self):
+        t, n = ctypes.c_double(), ctypes.c_int64()
+        _check(_lib.rd_part_status(self.handle, ctypes.byref(t), ctypes.byref(n)), "rd_part_status")
+        return t.value, n.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.rd_part_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _exchange_local(parts, pack, unpack):
+    """Ghost exchange between parts that share one device: each part packs its
+    send list, then copies the slice part q needs into q's receive buffer."""
+    import torch
+    for p in parts:
+        p.phase(pack, p.send_buf)
+    torch.cuda.synchronize()
+    for q in parts:
+        for p in parts:
+            a, b = int(p.send_ptr[q.part]), int(p.send_ptr[q.part + 1])
+            c, d = int(q.recv_ptr[p.part]), int(q.recv_ptr[p.part + 1])
+            if b > a:
+                q.recv_buf[c:d].copy_(p.send_buf[a:b])
+    torch.cuda.synchronize()
+    for q in parts:
+        q.phase(unpack, q.recv_buf)
+
+
+def run_parts_local(parts, n_steps: int):
+    """Advance all parts of one partitioned state held on this device by n_steps
+    (the exchange is a device copy between the parts' buffers; dt is the minimum
+    of the parts' dt, taken through the host)."""
+    import torch
+    for _ in range(int(n_steps)):
+        _exchange_local(parts, PART_PACK_W, PART_UNPACK_W)
+        for p in parts:
+            p.phase(PART_STAGE1)
+        dt = min(p.get_dt() for p in parts)
+        for p in parts:
+            p.set_dt(dt)
+            p.phase(PART_UPDATE1)
+        if parts[0].two_stage:
+            _exchange_local(parts, PART_PACK_WS, PART_UNPACK_WS)
+            for p in parts:
+                p.phase(PART_STAGE2)
+    torch.cuda.synchronize()
+    for p in parts:
+        p.status()
+
+
+def run_part_distributed(part: Part, n_steps: int, group=None):
+    """Advance this rank's part by n_steps with torch.distributed: ghost states
+    through point-to-point send/recv with every peer that shares vertices with
+    this part, dt through an in-place all-reduce (min) on the device.  Every
+    rank of the group runs this with its own part of the same partition."""
+    import torch
+    import torch.distributed as dist
+
+    def exchange(pack, unpack):
+        part.phase(pack, part.send_buf)
+        torch.cuda.current_stream().wait_stream(part.mesh.stream)
+        ops = []
+        for q in range(part.n_parts):
+            if q == part.part:
+                continue
+            a, b = int(part.send_ptr[q]), int(part.send_ptr[q + 1])
+            c, d = int(part.recv_ptr[q]), int(part.recv_ptr[q + 1])
+            if b > a:
+                ops.append(dist.P2POp(dist.isend, part.send_buf[a:b], q, group))
+            if d > c:
+                ops.append(dist.P2POp(dist.irecv, part.recv_buf[c:d], q, group))
+        if ops:
+            for w in dist.batch_isend_irecv(ops):
+                w.wait()
+        part.mesh.stream.wait_stream(torch.cuda.current_stream())
+        part.phase(unpack, part.recv_buf)
+
+    dt = part.dt_tensor()
+    for _ in range(int(n_steps)):
+        exchange(PART_PACK_W, PART_UNPACK_W)
+        part.phase(PART_STAGE1)
+        torch.cuda.current_stream().wait_stream(part.mesh.stream)
+        dist.all_reduce(dt, op=dist.ReduceOp.MIN, group=group)
+        part.mesh.stream.wait_stream(torch.cuda.current_stream())
+        part.phase(PART_UPDATE1)
+        if part.two_stage:
+            exchange(PART_PACK_WS, PART_UNPACK_WS)
+            part.phase(PART_STAGE2)
+    torch.cuda.synchronize()

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include "rd_device.h"
+#include "rd_df64.h"
 #include "rd_dfloat.cuh"
 #include "rd_internal.h"
 #include "rd_kernels.cuh"
@@ -163,76 +164,87 @@ Gas<dfloat> gas_df(double gamma) {
 
 }  // namespace
 
-// Stage-1 triangle kernel of an RD_DF64 state (the FP64 kernel's arguments).
-int launch_tri_stage1_df(const rd_state* s, int a, unsigned grid, int block, cudaStream_t st) {
-  const rd_mesh* m = s->m;
-  const int nt = m->h.nt;
-  DevGeo<double> g;
-  g.nx = (const double*)m->geo[0][0].p;
-  g.ny = (const double*)m->geo[0][1].p;
-  g.hl = (const double*)m->geo[0][2].p;
-  g.area = (const double*)m->geo[0][3].p;
-  g.lmax = (const double*)m->geo[0][4].p;
-  const int* tri = (const int*)m->tri.p;
-  DevCtl* ctl = (DevCtl*)s->ctl.p;
-  const Gas<dfloat> gas = gas_df(s->p.gamma);
-  const dfloat eps(s->p.eps_fix);
-  const double* Za = (const double*)s->Z[a].p;
-  const double* Sa = (const double*)s->spd[a].p;
-  double* share = (double*)s->share.p;
-  dfloat* rec = (dfloat*)s->rec.p;
-  double* cf = (double*)s->cfl.p;
-  BlendArgs<double> ba = tile_blend_args<double>(s);
-  unsigned long long* vr0 = (unsigned long long*)s->vr.p;
-  ba.vr = vr0;
-  switch (s->p.scheme) {
+int launch_tri_stage1_df(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
+                         cudaStream_t st) {
+  const Gas<dfloat> gas = gas_df(p.gamma);
+  const dfloat eps(p.eps_fix);
+  dfloat* rec = (dfloat*)a.rec;
+  switch (p.scheme) {
     case RD_N1:
-      k_tri_stage1_df<RD_N1><<<grid, block, 0, st>>>(nt, tri, g, Za, Sa, gas, eps, share, nullptr, cf, ctl, ba);
+      k_tri_stage1_df<RD_N1><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, nullptr,
+                                                     a.cfl, a.ctl, ba);
       break;
     case RD_LDA2:
-      k_tri_stage1_df<RD_LDA2><<<grid, block, 0, st>>>(nt, tri, g, Za, Sa, gas, eps, share, rec, cf, ctl, ba);
+      k_tri_stage1_df<RD_LDA2><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, rec, a.cfl,
+                                                       a.ctl, ba);
       break;
     default:
-      if (s->p.scheme == RD_B2 && s->p.lumping == RD_LUMP_GLOBAL)
-        k_tri_stage1_df<RD_B2><<<grid, block, 0, st>>>(nt, tri, g, Za, Sa, gas, eps, share, rec, cf, ctl, ba);
+      if (p.scheme == RD_B2 && p.lumping == RD_LUMP_GLOBAL)
+        k_tri_stage1_df<RD_B2><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, rec, a.cfl,
+                                                       a.ctl, ba);
       else
-        k_tri_stage1_df<RD_BMAX2><<<grid, block, 0, st>>>(nt, tri, g, Za, Sa, gas, eps, share, rec, cf, ctl, ba);
+        k_tri_stage1_df<RD_BMAX2><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, rec,
+                                                          a.cfl, a.ctl, ba);
       break;
   }
   CU(cudaGetLastError());
   return RD_OK;
 }
 
-// Stage-2 triangle kernel of an RD_DF64 state reading W^n from buffer a.
-int launch_tri_stage2_df(const rd_state* s, int a, unsigned grid, int block, cudaStream_t st) {
+int launch_tri_stage2_df(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
+                         cudaStream_t st) {
+  const Gas<dfloat> gas = gas_df(p.gamma);
+  const dfloat eps(p.eps_fix);
+  const dfloat* rec = (const dfloat*)a.rec;
+  if (p.scheme == RD_LDA2)
+    k_tri_stage2_df<RD_LDA2><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.Wn, a.Ws, rec, gas, eps, a.share,
+                                                     a.ctl, ba);
+  else if (p.scheme == RD_B2 && p.lumping == RD_LUMP_GLOBAL)
+    k_tri_stage2_df<RD_B2><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.Wn, a.Ws, rec, gas, eps, a.share, a.ctl,
+                                                   ba);
+  else
+    k_tri_stage2_df<RD_BMAX2><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.Wn, a.Ws, rec, gas, eps, a.share,
+                                                      a.ctl, ba);
+  CU(cudaGetLastError());
+  return RD_OK;
+}
+
+// The state's arrays for the launchers above.
+static TriArraysDF state_arrays(const rd_state* s) {
   const rd_mesh* m = s->m;
-  const int nt = m->h.nt;
-  DevGeo<double> g;
-  g.nx = (const double*)m->geo[0][0].p;
-  g.ny = (const double*)m->geo[0][1].p;
-  g.hl = (const double*)m->geo[0][2].p;
-  g.area = (const double*)m->geo[0][3].p;
-  g.lmax = (const double*)m->geo[0][4].p;
-  const int* tri = (const int*)m->tri.p;
-  DevCtl* ctl = (DevCtl*)s->ctl.p;
-  const Gas<dfloat> gas = gas_df(s->p.gamma);
-  const dfloat eps(s->p.eps_fix);
-  const double* Zs = (const double*)s->Zs.p;
-  const double* Wn = (const double*)s->W[a].p;
-  const double* Ws = (const double*)s->Ws.p;
-  const dfloat* rec = (const dfloat*)s->rec.p;
-  double* share = (double*)s->share.p;
+  TriArraysDF a;
+  a.nt = m->h.nt;
+  a.tri = (const int*)m->tri.p;
+  a.g.nx = (const double*)m->geo[0][0].p;
+  a.g.ny = (const double*)m->geo[0][1].p;
+  a.g.hl = (const double*)m->geo[0][2].p;
+  a.g.area = (const double*)m->geo[0][3].p;
+  a.g.lmax = (const double*)m->geo[0][4].p;
+  a.share = (double*)s->share.p;
+  a.rec = s->rec.p;
+  a.cfl = (double*)s->cfl.p;
+  a.ctl = (DevCtl*)s->ctl.p;
+  return a;
+}
+
+int launch_tri_stage1_df(const rd_state* s, int a, unsigned grid, int block, cudaStream_t st) {
+  TriArraysDF x = state_arrays(s);
+  x.Z = (const double*)s->Z[a].p;
+  x.spd = (const double*)s->spd[a].p;
+  BlendArgs<double> ba = tile_blend_args<double>(s);
+  ba.vr = (unsigned long long*)s->vr.p;
+  return launch_tri_stage1_df(s->p, x, ba, grid, block, st);
+}
+
+int launch_tri_stage2_df(const rd_state* s, int a, unsigned grid, int block, cudaStream_t st) {
+  TriArraysDF x = state_arrays(s);
+  x.Z = (const double*)s->Zs.p;
+  x.Wn = (const double*)s->W[a].p;
+  x.Ws = (const double*)s->Ws.p;
   BlendArgs<double> ba = tile_blend_args<double>(s);
   unsigned long long* vr0 = (unsigned long long*)s->vr.p;
   ba.vr = vr0 ? vr0 + 2 : nullptr;
-  if (s->p.scheme == RD_LDA2)
-    k_tri_stage2_df<RD_LDA2><<<grid, block, 0, st>>>(nt, tri, g, Zs, Wn, Ws, rec, gas, eps, share, ctl, ba);
-  else if (s->p.scheme == RD_B2 && s->p.lumping == RD_LUMP_GLOBAL)
-    k_tri_stage2_df<RD_B2><<<grid, block, 0, st>>>(nt, tri, g, Zs, Wn, Ws, rec, gas, eps, share, ctl, ba);
-  else
-    k_tri_stage2_df<RD_BMAX2><<<grid, block, 0, st>>>(nt, tri, g, Zs, Wn, Ws, rec, gas, eps, share, ctl, ba);
-  CU(cudaGetLastError());
-  return RD_OK;
+  return launch_tri_stage2_df(s->p, x, ba, grid, block, st);
 }
 
 }  // namespace rd

@@ -30,6 +30,21 @@ struct HostMesh {
 int build_host_mesh(int32_t nv, const double* xy, int32_t nt, const int32_t* tri,
                     const int8_t* shift, double Lx, double Ly, int32_t reorder, HostMesh& out);
 
+// Plan of part r of a P-way vertex partition (rd_partition.cpp): owned
+// internal vertex range [v0, v1); local vertices lv (owned first, then the
+// ghost vertices ascending); local triangles lt (ascending internal ids: every
+// triangle with an owned corner) with their corners ltri [3][nlt] in local
+// vertex ids; the CSR of the owned local vertices over local triangle
+// entries 3 k + c; per peer q the ghosts it owns, local slots
+// [n_own + recv_ptr[q], n_own + recv_ptr[q+1]), and the owned local vertices
+// it needs, send_idx[send_ptr[q] .. send_ptr[q+1]) in q's ghost order.
+struct PartPlanHost {
+  int P = 1, r = 0;
+  int32_t v0 = 0, v1 = 0;
+  std::vector<int32_t> lv, lt, ltri, csr_ptr, csr_ent, recv_ptr, send_ptr, send_idx;
+};
+int build_part_plan(const HostMesh& h, int P, int r, PartPlanHost& out);
+
 // Tile plan of the tiled step (host form; the device copy is rd::TilePlan).
 // Triangles, sorted by their smallest vertex id, form tiles of tt consecutive
 // triangles; tile p owns the vertices [vs[p], vs[p+1]); its halo vertices are
