@@ -12,8 +12,11 @@ L2 (537 MB of FP64 vertex state), so no L2 flush is needed between steps.
 
 --impl reference times the CPU oracle (the plain FP64 reference of the
 method, on the host cores) on a bounded sample of the same workload.
-Under torchrun every rank advances its own replica (weak scaling, no
-data-path collective); rank 0 prints one JSON line.
+Under torchrun (N > 1) the mesh is split into N vertex parts, one per rank,
+with the ghost states moved by NCCL point-to-point before each stage and dt
+taken by an all-reduce (min) -- strong scaling; --multi replicas runs N
+independent replicas instead (weak scaling).  The batched workload splits its
+64 meshes across the ranks.  Rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -110,6 +113,9 @@ def parse():
                     help="tiled step: 'auto' (the autotuner's choice), 'none', or TRIANGLESxTHREADS, e.g. 512x128")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-rollout companion measurement")
     ap.add_argument("--no-meshgen", action="store_true", help="skip the mesh-generation companion measurement")
+    ap.add_argument("--multi", choices=["partition", "replicas"], default="partition",
+                    help="with N > 1 ranks: one mesh split into N vertex parts with NCCL ghost exchange "
+                         "(strong scaling), or N independent replicas (weak scaling)")
     return ap.parse_args()
 
 
@@ -273,9 +279,9 @@ def ours_batched(args, ws, rank, local):
     torch.cuda.set_device(local)
     bt = batched(args, ws, args.steps)
     line = {"metric": METRIC, "value": bt["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": bt["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": bt["ms_per_step"], "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
-            "data": "synthetic (64 seeded periodic meshes, vortex / shear states)",
+            "data": "synthetic (64 seeded periodic meshes, vortex / shear states; whole meshes split across ranks)",
             "config": {"workload": "batch64_B2", "meshes": bt["meshes"], "triangles": bt["triangles"],
                        "scheme": "B2", "cfl": 0.8, "precision": args.precision,
                        "l2": "inputs larger than L2", "steps_per_graph_launch": args.steps},
@@ -291,6 +297,8 @@ def ours(args, ws, rank, local):
 
     if args.workload == "batch64_B2":
         return ours_batched(args, ws, rank, local)
+    if ws > 1 and args.multi == "partition":
+        return ours_partitioned(args, ws, rank, local)
     torch.cuda.set_device(local)
     mesh, W0, scheme = build_inputs(args.workload)
     if args.scheme:
@@ -444,6 +452,51 @@ def ours(args, ws, rank, local):
     return line
 
 
+def ours_partitioned(args, ws, rank, local):
+    """The workload's mesh split into ws vertex parts, one per rank (rd_part_*): ghost
+    states through NCCL point-to-point before each stage, dt through an all-reduce
+    (min).  Strong scaling: the whole job advances the one mesh."""
+    import torch
+
+    from paper_1705_02028_gb300 import binding
+    torch.cuda.set_device(local)
+    mesh, W0, scheme = build_inputs(args.workload)
+    if args.scheme:
+        scheme = args.scheme
+    m = binding.Mesh(mesh, reorder=args.reorder)
+    part = binding.Part(m, ws, rank, W0, scheme=scheme, precision=args.precision)
+    binding.run_part_distributed(part, args.warmup)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    binding.run_part_distributed(part, args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks.stop_and_keep()
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps, ws)
+    nt = mesh.nt
+    line = {"metric": METRIC, "value": nt / (ms_step * 1e-3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "df64": "f64/df32x2"}[args.precision],
+            "data": "synthetic (seeded KHI shear layer / generated periodic triangulation)",
+            "config": {"workload": args.workload, "triangles": nt, "vertices": mesh.nv, "scheme": scheme,
+                       "cfl": 0.8, "precision": args.precision, "reorder": args.reorder,
+                       "parallelism": f"vertex partition x{ws} (NCCL ghost exchange, all-reduce min dt)",
+                       "owned_vertices_rank0": part.n_owned, "ghost_vertices_rank0": part.n_ghost,
+                       "l2": "inputs larger than L2"},
+            "clocks": clocks.result,
+            "e2e": None,
+            "gpu_launches": None}
+    part.close()
+    m.close()
+    return line
+
+
 def accuracy_leg(binding, m, W0, scheme, nt, mesh, steps=20):
     """FP32 L1 density error and the RD_DF64 max-norm difference, both against the
     FP64 path (itself held to the oracle at 1e-12 by the parity tests), after
@@ -479,7 +532,10 @@ def batched(args, ws, steps):
     import torch
 
     from paper_1705_02028_gb300 import binding, inputs
-    work = inputs.batch_workload(n_mesh=64, seed=2)
+    work_all = inputs.batch_workload(n_mesh=64, seed=2)
+    nt_all = sum(m.nt for m, _, _ in work_all)
+    rank = int(os.environ.get("RANK", "0"))
+    work = work_all[rank::ws]          # whole meshes per rank: independent units, no collective
     stream = torch.cuda.Stream()
     meshes = [binding.Mesh(m, stream=stream) for m, _, _ in work]
     b = binding.Batch(meshes, [W for _, W, _ in work], scheme="B2", precision=args.precision)
@@ -502,8 +558,9 @@ def batched(args, ws, steps):
     b.close()
     for mm in meshes:
         mm.close()
-    return {"value": ws * nt / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "meshes": len(work),
-            "triangles": nt, "vertices": nv, "steps_per_graph_launch": steps,
+    return {"value": nt_all / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "meshes": len(work_all),
+            "meshes_per_rank": len(work), "triangles": nt_all, "triangles_rank0": nt, "vertices_rank0": nv,
+            "steps_per_graph_launch": steps,
             "sides": [int(mm.Nx) for mm, _, _ in work], "dt_min": float(dts.min()), "dt_max": float(dts.max()),
             "launch_shapes": {"tri_block": shapes[0], "vtx_block": shapes[1], "source": "rd_batch_autotune"}
             if shapes else None, "per_kernel_ms": pk, "precision": args.precision}
