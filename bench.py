@@ -424,8 +424,8 @@ def ours(args, ws, rank, local):
         eq = fl_df * nt / (pkdf[ddf] * 1e-3) if fl_df else None
         line["df64"] = {"value": ws * nt / (msdf * 1e-3), "ms_per_step": msdf, "per_kernel_ms": pkdf,
                         "vs_fp64_step": ms_step / msdf,
-                        "launch_shapes": {"tri_block": sdf.shapes[0], "vtx_block": sdf.shapes[1]}
-                        if sdf.shapes else None,
+                        "launch_shapes": dict(zip(("tri_block", "vtx_block", "register_budget"),
+                                                  sdf.launch_shapes())),
                         "dominant_kernel": ddf,
                         "counted_fp64_equivalent_tflops": eq / 1e12 if eq else None,
                         "vs_measured_fp64_fma_peak": eq / fp64_peak if eq else None,

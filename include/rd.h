@@ -435,6 +435,11 @@ int rd_math_eval(int32_t fn, int64_t n, const double *x, double *out, void *cuda
  * be NULL; the tiling is read with rd_state_get_tiling).  Results do not
  * depend on the launch shape (every sum has a fixed order). */
 int rd_state_autotune(rd_state *s, int32_t *tri_block, int32_t *vtx_block);
+/* Launch shapes a state uses (after rd_state_autotune): triangle and vertex
+ * block sizes and, for RD_DF64, the register budget of its triangle kernels
+ * (1: up to 255 registers per thread; 2: 128, twice the resident warps).  The
+ * autotuner times both budgets for RD_DF64 states.  Any pointer may be NULL. */
+int rd_state_launch_shapes(const rd_state *s, int32_t *tri_block, int32_t *vtx_block, int32_t *df_occ);
 
 /* Tiled step (Sec. 3.3-3.4 and Eqs. eqRK1/eqRK2 computed as in rd_step; the
  * distribution of Sec. 4.2.1 done on chip).  The triangles, in the mesh

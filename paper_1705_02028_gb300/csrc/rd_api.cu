@@ -639,12 +639,18 @@ extern "C" int rd_state_autotune(rd_state* s, int32_t* tri_block, int32_t* vtx_b
     CU(cudaEventElapsedTime(&ms, ev[0], ev[6]));
     return RD_OK;
   };
-  int best_t = TRI_BLOCK, best_v = VTX_BLOCK, rc = RD_OK;
+  int best_t = TRI_BLOCK, best_v = VTX_BLOCK, best_o = 1, rc = RD_OK;
   float best = 1e30f, ms = 0.f;
-  for (int tb : tri_c) {
-    if ((rc = time_step(tb, VTX_BLOCK, ms)) != RD_OK) break;
-    if (ms < best) { best = ms; best_t = tb; }
+  const int n_occ = s->p.precision == RD_DF64 ? 2 : 1;  // DF64: 255- and 128-register triangle kernels
+  for (int o = 1; o <= n_occ; ++o) {
+    s->df_occ = o;
+    for (int tb : tri_c) {
+      if ((rc = time_step(tb, VTX_BLOCK, ms)) != RD_OK) break;
+      if (ms < best) { best = ms; best_t = tb; best_o = o; }
+    }
+    if (rc != RD_OK) break;
   }
+  s->df_occ = best_o;
   best = 1e30f;
   for (int vb : vtx_c) {
     if (rc != RD_OK || (rc = time_step(best_t, vb, ms)) != RD_OK) break;
@@ -683,6 +689,14 @@ extern "C" int rd_state_autotune(rd_state* s, int32_t* tri_block, int32_t* vtx_b
   if (tri_block) *tri_block = best_t;
   if (vtx_block) *vtx_block = best_v;
   return rc;
+}
+
+extern "C" int rd_state_launch_shapes(const rd_state* s, int32_t* tri_block, int32_t* vtx_block, int32_t* df_occ) {
+  if (!s) return RD_EINVAL;
+  if (tri_block) *tri_block = s->tri_block;
+  if (vtx_block) *vtx_block = s->vtx_block;
+  if (df_occ) *df_occ = s->df_occ;
+  return RD_OK;
 }
 
 extern "C" int rd_get_state(const rd_state* s, double* W_out) {

