@@ -115,6 +115,10 @@ RD_HD dfloat two_prod(float a, float b) {
 
 RD_HD dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
 
+#ifndef RD_DF_ACCURATE_ADD
+#define RD_DF_ACCURATE_ADD 0
+#endif
+#if RD_DF_ACCURATE_ADD
 // accurate double-word sum
 RD_HD dfloat operator+(dfloat x, dfloat y) {
   const dfloat s = two_sum(x.hi, y.hi);
@@ -124,6 +128,17 @@ RD_HD dfloat operator+(dfloat x, dfloat y) {
   const float w = dfo::add(t.lo, v.lo);
   return fast_two_sum(v.hi, w);
 }
+#else
+// double-word sum with one error-free transformation (Dekker's add2): the error
+// is below about 2 u^2 (|x| + |y|), i.e. of the order of the operands' own
+// representation error, which is what every later operation of the triangle
+// algebra sees anyway; half the operations of the accurate sum.
+RD_HD dfloat operator+(dfloat x, dfloat y) {
+  const dfloat s = two_sum(x.hi, y.hi);
+  const float e = dfo::add(s.lo, dfo::add(x.lo, y.lo));
+  return fast_two_sum(s.hi, e);
+}
+#endif
 RD_HD dfloat operator-(dfloat x, dfloat y) { return x + (-y); }
 
 // double-word product with FMAs
