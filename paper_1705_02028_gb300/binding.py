@@ -97,6 +97,7 @@ _SIGS = {
     "rd_batch_destroy": (None, [_vp]),
     "rd_state_autotune": (ctypes.c_int, [_vp, _i32p, _i32p]),
     "rd_state_launch_shapes": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p]),
+    "rd_state_set_launch_shapes": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "rd_state_set_tiling": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
     "rd_state_get_tiling": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p]),
     "rd_adjoint_forward": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _dp]),
@@ -415,6 +416,10 @@ class State:
         _check(_lib.rd_state_launch_shapes(self.handle, ctypes.byref(tb), ctypes.byref(vb), ctypes.byref(oc)),
                "rd_state_launch_shapes")
         return tb.value, vb.value, oc.value
+
+    def set_launch_shapes(self, tri_block: int, vtx_block: int, df_occ: int = 1):
+        _check(_lib.rd_state_set_launch_shapes(self.handle, int(tri_block), int(vtx_block), int(df_occ)),
+               "rd_state_set_launch_shapes")
 
     def set_tiling(self, tile_triangles: int, threads: int = 128):
         """Tiled step with tiles of `tile_triangles` triangles (0: untiled); rd_state_set_tiling."""

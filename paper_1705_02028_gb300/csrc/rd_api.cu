@@ -641,7 +641,8 @@ extern "C" int rd_state_autotune(rd_state* s, int32_t* tri_block, int32_t* vtx_b
   };
   int best_t = TRI_BLOCK, best_v = VTX_BLOCK, best_o = 1, rc = RD_OK;
   float best = 1e30f, ms = 0.f;
-  const int n_occ = s->p.precision == RD_DF64 ? 2 : 1;  // DF64: 255- and 128-register triangle kernels
+  // DF64: 255- and 128-register triangle kernels, the latter also with block barriers between phases
+  const int n_occ = s->p.precision == RD_DF64 ? 3 : 1;
   for (int o = 1; o <= n_occ; ++o) {
     s->df_occ = o;
     for (int tb : tri_c) {
@@ -696,6 +697,22 @@ extern "C" int rd_state_launch_shapes(const rd_state* s, int32_t* tri_block, int
   if (tri_block) *tri_block = s->tri_block;
   if (vtx_block) *vtx_block = s->vtx_block;
   if (df_occ) *df_occ = s->df_occ;
+  return RD_OK;
+}
+
+extern "C" int rd_state_set_launch_shapes(rd_state* s, int32_t tri_block, int32_t vtx_block, int32_t df_occ) {
+  if (!s) return RD_EINVAL;
+  if (tri_block != 64 && tri_block != 128 && tri_block != 192 && tri_block != 256) return RD_EINVAL;
+  if (vtx_block != 128 && vtx_block != 256 && vtx_block != 512) return RD_EINVAL;
+  if (df_occ < 1 || df_occ > 3) return RD_EINVAL;
+  s->tri_block = tri_block;
+  s->vtx_block = vtx_block;
+  s->df_occ = df_occ;
+  if (s->g2) {  // the captured graph holds the old launch shapes
+    cudaStreamSynchronize(s->m->stream);
+    cudaGraphExecDestroy(s->g2);
+    s->g2 = nullptr;
+  }
   return RD_OK;
 }
 

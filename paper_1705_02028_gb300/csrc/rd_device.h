@@ -125,7 +125,7 @@ struct rd_state {
   bool bc_init = false;
   long long launched = 0;  // host view of the committed step count (parity of the buffers)
   int tri_block = rd::TRI_BLOCK, vtx_block = rd::VTX_BLOCK;  // launch shapes (autotuned)
-  int df_occ = 1;  // RD_DF64: register budget of the triangle kernels (1: 255, 2: 128 registers; autotuned)
+  int df_occ = 1;  // RD_DF64 triangle-kernel variant (1: 255 registers, 2: 128, 3: 128 with phase barriers; autotuned)
   rd::TilePlan* tiles = nullptr;  // tiled step (nullptr: per-triangle share arrays)
   cudaGraphExec_t g2 = nullptr;  // two steps (even -> odd -> even)
   bool graph_failed = false;

@@ -60,14 +60,40 @@ __device__ __forceinline__ void ld_rec(const dfloat* p, dfloat r[16]) {
 
 // OCC: minimum resident 256-thread blocks per SM asked of the compiler (1: up
 // to 255 registers per thread, no spills; 2: 128 registers, a few hundred bytes
-// of spills, twice the resident warps); the autotuner picks one.
-template <int SCHEME, int OCC>
+// of spills, twice the resident warps).  SYNC: a block barrier between the
+// phases of the per-triangle algebra.  The body is ~10^4 instructions of
+// straight-line code, far more than the instruction caches hold, and warps
+// that drift apart miss in them (ncu: "no instruction" is the leading stall);
+// the barriers keep a block's warps on the same stretch of code.  Every
+// thread reaches every barrier: threads past the last triangle repeat the
+// last one without storing, and a failed phase only skips the later phases'
+// arithmetic.  The autotuner picks the variant.
+__device__ __forceinline__ void phase_sync(bool on) {
+  if (on) __syncthreads();
+}
+
+// One flag per block: the control block's stop word read once, so that every
+// thread of the block takes the same branch around the barriers.
+__device__ __forceinline__ bool block_stop(const DevCtl* ctl) {
+  __shared__ int stop;
+  if (threadIdx.x == 0) stop = ctl->stop;
+  __syncthreads();
+  return stop != 0;
+}
+
+template <int SCHEME, int OCC, bool SYNC>
 __global__ void __launch_bounds__(256, OCC)
     k_tri_stage1_df(int nt, const int* __restrict__ tri, DevGeo<double> g, const double* __restrict__ Z,
                     const double* __restrict__ spd, Gas<dfloat> gas, dfloat eps, double* __restrict__ share,
                     dfloat* __restrict__ rec, double* __restrict__ cfl, DevCtl* ctl, BlendArgs<double> ba) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nt || ctl->stop) return;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (SYNC) {
+    if (block_stop(ctl)) return;
+  } else if (t0 >= nt || ctl->stop) {
+    return;
+  }
+  const bool act = t0 < nt;
+  const int t = act ? t0 : nt - 1;
   int v[3];
   double nx[3], ny[3], hl[3], Zc[3][4];
   load_tri(t, nt, tri, g, v, nx, ny, hl);
@@ -77,7 +103,7 @@ __global__ void __launch_bounds__(256, OCC)
     double s0 = __ldg(spd + v[0]), s1 = __ldg(spd + v[1]), s2 = __ldg(spd + v[2]);
     double lam = mag_less(s1, s0) ? s0 : s1;  // speeds are >= 0
     lam = mag_less(s2, lam) ? lam : s2;
-    cfl[t] = __ldg(g.lmax + t) * lam;
+    if (act) cfl[t] = __ldg(g.lmax + t) * lam;
   }
   const int mode = SCHEME == RD_BMAX2 ? ba.mode : BLEND_B;
   double thx = 0.0;
@@ -92,7 +118,21 @@ __global__ void __launch_bounds__(256, OCC)
     hld[c] = to_df(hl[c]);
   }
   dfloat out[3][4], r[16];
-  int st = stage1_body_d<dfloat, SCHEME>(Zb, dZ, nxd, nyd, hld, gas, eps, out, r, mode, to_df(thx));
+  int st;
+  if (SYNC) {
+    TriLin<dfloat> L;
+    phase_sync(true);
+    st = lin_roe_split(Zb, dZ, nxd, nyd, hld, gas, eps, L);
+    phase_sync(true);
+    if (!st) st = lin_assemble(L);
+    phase_sync(true);
+    if (!st) lin_nshares(dZ, gas, L);
+    phase_sync(true);
+    if (!st) stage1_shares<dfloat, SCHEME>(L, out, r, mode, to_df(thx));
+  } else {
+    st = stage1_body_d<dfloat, SCHEME>(Zb, dZ, nxd, nyd, hld, gas, eps, out, r, mode, to_df(thx));
+  }
+  if (!act) return;
   if (st) {
     atomicOr(&ctl->status, st);
     return;
@@ -106,13 +146,19 @@ __global__ void __launch_bounds__(256, OCC)
   }
 }
 
-template <int SCHEME, int OCC>
+template <int SCHEME, int OCC, bool SYNC>
 __global__ void __launch_bounds__(256, OCC)
     k_tri_stage2_df(int nt, const int* __restrict__ tri, DevGeo<double> g, const double* __restrict__ Zs,
                     const double* __restrict__ Wn, const double* __restrict__ Ws, const dfloat* __restrict__ rec,
                     Gas<dfloat> gas, dfloat eps, double* __restrict__ share, DevCtl* ctl, BlendArgs<double> ba) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nt || ctl->stop) return;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (SYNC) {
+    if (block_stop(ctl)) return;
+  } else if (t0 >= nt || ctl->stop) {
+    return;
+  }
+  const bool act = t0 < nt;
+  const int t = act ? t0 : nt - 1;
   int v[3];
   double nx[3], ny[3], hl[3], Zc[3][4];
   load_tri(t, nt, tri, g, v, nx, ny, hl);
@@ -142,8 +188,28 @@ __global__ void __launch_bounds__(256, OCC)
     hld[c] = to_df(hl[c]);
   }
   dfloat out[3][4];
-  int st = stage2_body_d<dfloat, SCHEME>(Zb, dZ, dW, r, nxd, nyd, hld, to_df(area), to_df(ctl->dt), gas, eps, out,
-                                         mode, to_df(thx), sl);
+  const dfloat dt = to_df(ctl->dt), aread = to_df(area);
+  int st;
+  if (SYNC) {
+    TriLin<dfloat> L;
+    phase_sync(true);
+    st = lin_roe_split(Zb, dZ, nxd, nyd, hld, gas, eps, L);
+    phase_sync(true);
+    if (!st) st = lin_assemble(L);
+    phase_sync(true);
+    if (!st) lin_nshares(dZ, gas, L);
+    phase_sync(true);
+    if (!st) {
+      const dfloat idt = rcp(dt);
+      dfloat PhiN[3][4], PhiT[4];
+      stage2_totals_dw(L, dW, r, aread, idt, PhiN, PhiT);
+      stage2_shares<dfloat, SCHEME>(L, PhiN, PhiT, dW, aread, idt, out, mode, to_df(thx), sl);
+    }
+  } else {
+    st = stage2_body_d<dfloat, SCHEME>(Zb, dZ, dW, r, nxd, nyd, hld, aread, dt, gas, eps, out, mode, to_df(thx),
+                                       sl);
+  }
+  if (!act) return;
   if (st) {
     atomicOr(&ctl->status, st);
     return;
@@ -167,7 +233,7 @@ Gas<dfloat> gas_df(double gamma) {
 
 }  // namespace
 
-template <int OCC>
+template <int OCC, bool SYNC>
 int stage1_df_occ(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
                   cudaStream_t st) {
   const Gas<dfloat> gas = gas_df(p.gamma);
@@ -175,19 +241,19 @@ int stage1_df_occ(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba
   dfloat* rec = (dfloat*)a.rec;
   switch (p.scheme) {
     case RD_N1:
-      k_tri_stage1_df<RD_N1, OCC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, nullptr,
+      k_tri_stage1_df<RD_N1, OCC, SYNC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, nullptr,
                                                           a.cfl, a.ctl, ba);
       break;
     case RD_LDA2:
-      k_tri_stage1_df<RD_LDA2, OCC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, rec,
+      k_tri_stage1_df<RD_LDA2, OCC, SYNC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, rec,
                                                             a.cfl, a.ctl, ba);
       break;
     default:
       if (p.scheme == RD_B2 && p.lumping == RD_LUMP_GLOBAL)
-        k_tri_stage1_df<RD_B2, OCC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, rec,
+        k_tri_stage1_df<RD_B2, OCC, SYNC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, rec,
                                                             a.cfl, a.ctl, ba);
       else
-        k_tri_stage1_df<RD_BMAX2, OCC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, rec,
+        k_tri_stage1_df<RD_BMAX2, OCC, SYNC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.spd, gas, eps, a.share, rec,
                                                                a.cfl, a.ctl, ba);
       break;
   }
@@ -195,20 +261,20 @@ int stage1_df_occ(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba
   return RD_OK;
 }
 
-template <int OCC>
+template <int OCC, bool SYNC>
 int stage2_df_occ(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
                   cudaStream_t st) {
   const Gas<dfloat> gas = gas_df(p.gamma);
   const dfloat eps(p.eps_fix);
   const dfloat* rec = (const dfloat*)a.rec;
   if (p.scheme == RD_LDA2)
-    k_tri_stage2_df<RD_LDA2, OCC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.Wn, a.Ws, rec, gas, eps, a.share,
+    k_tri_stage2_df<RD_LDA2, OCC, SYNC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.Wn, a.Ws, rec, gas, eps, a.share,
                                                           a.ctl, ba);
   else if (p.scheme == RD_B2 && p.lumping == RD_LUMP_GLOBAL)
-    k_tri_stage2_df<RD_B2, OCC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.Wn, a.Ws, rec, gas, eps, a.share,
+    k_tri_stage2_df<RD_B2, OCC, SYNC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.Wn, a.Ws, rec, gas, eps, a.share,
                                                         a.ctl, ba);
   else
-    k_tri_stage2_df<RD_BMAX2, OCC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.Wn, a.Ws, rec, gas, eps,
+    k_tri_stage2_df<RD_BMAX2, OCC, SYNC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.Wn, a.Ws, rec, gas, eps,
                                                            a.share, a.ctl, ba);
   CU(cudaGetLastError());
   return RD_OK;
@@ -216,12 +282,16 @@ int stage2_df_occ(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba
 
 int launch_tri_stage1_df(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
                          cudaStream_t st) {
-  return a.occ == 2 ? stage1_df_occ<2>(p, a, ba, grid, block, st) : stage1_df_occ<1>(p, a, ba, grid, block, st);
+  if (a.occ == 3) return stage1_df_occ<2, true>(p, a, ba, grid, block, st);
+  return a.occ == 2 ? stage1_df_occ<2, false>(p, a, ba, grid, block, st)
+                    : stage1_df_occ<1, false>(p, a, ba, grid, block, st);
 }
 
 int launch_tri_stage2_df(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
                          cudaStream_t st) {
-  return a.occ == 2 ? stage2_df_occ<2>(p, a, ba, grid, block, st) : stage2_df_occ<1>(p, a, ba, grid, block, st);
+  if (a.occ == 3) return stage2_df_occ<2, true>(p, a, ba, grid, block, st);
+  return a.occ == 2 ? stage2_df_occ<2, false>(p, a, ba, grid, block, st)
+                    : stage2_df_occ<1, false>(p, a, ba, grid, block, st);
 }
 
 // The state's arrays for the launchers above.

@@ -18,7 +18,7 @@ struct TriArraysDF {
   void* rec = nullptr;
   double* cfl = nullptr;
   DevCtl* ctl = nullptr;
-  int occ = 1;  // register budget of the kernels: 1 (255 registers) or 2 (128)
+  int occ = 1;  // kernel variant: 1 (255 registers), 2 (128), 3 (128, block barriers between phases)
 };
 int launch_tri_stage1_df(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
                          cudaStream_t st);

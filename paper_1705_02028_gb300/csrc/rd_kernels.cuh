@@ -364,8 +364,8 @@ struct TriLin {
 // their 48-bit arithmetic acts on the differences (which carry the residual)
 // rather than on the full states (App. A algebra unchanged).
 template <class T>
-RD_HD int linearise_core(const T Zbar[4], const T Z[3][4], const T nx[3], const T ny[3], const T hl[3],
-                         const Gas<T>& gas, T eps, TriLin<T>& L) {
+RD_HD int lin_roe_split(const T Zbar[4], const T Z[3][4], const T nx[3], const T ny[3], const T hl[3],
+                        const Gas<T>& gas, T eps, TriLin<T>& L) {
   T* Zb = L.Zb;
 #pragma unroll
   for (int k = 0; k < 4; ++k) Zb[k] = Zbar[k];
@@ -451,6 +451,13 @@ RD_HD int linearise_core(const T Zbar[4], const T Z[3][4], const T nx[3], const 
     n.s2[1] = q2 - Yi;
   }
 
+  return 0;
+}
+
+// Phase 2 of the linearisation: sum_j K_j^- assembled and LU-factorised.
+template <class T>
+RD_HD int lin_assemble(TriLin<T>& L) {
+  const RoeState<T>& r = L.r;
   // sum_j K_j^- = (sum l3) I + e P^T + sum_j d_j q_j^T,
   //   P = (sum s1) a + sum_j s2_j b_j,  q_j = s2_j a + hp_j b_j.
   // With d_j = (0, nx, ny, w)_j and b_j = (-w, nx, ny, 0)_j the rows
@@ -491,7 +498,14 @@ RD_HD int linearise_core(const T Zbar[4], const T Z[3][4], const T nx[3], const 
 #pragma unroll
     for (int k = 0; k < 4; ++k) L.lu.a[k][k] += L3;
   }
-  if (!L.lu.factor()) return ST_SINGULAR;
+  return L.lu.factor() ? 0 : ST_SINGULAR;
+}
+
+// Phase 3: linearised states, N^ sum_j K_j^- W^_j and the N-scheme shares.
+template <class T>
+RD_HD void lin_nshares(const T Z[3][4], const Gas<T>& gas, TriLin<T>& L) {
+  const RoeState<T>& r = L.r;
+  const T* Zb = L.Zb;
 
   // conservative linearised states W^_i = dW/dZ(Zbar) Z_i and
   // S = sum_j K_j^- W^_j = sum_j l3_j W^_j + e sum_j P_j + sum_j d_j Q_j
@@ -534,6 +548,19 @@ RD_HD int linearise_core(const T Zbar[4], const T Z[3][4], const T nx[3], const 
     for (int k = 0; k < 4; ++k) d[k] = Wh[i][k] - win[k];
     Kpm_apply<T, true>(r, L.nd[i], d, L.phiN[i]);
   }
+}
+
+// The linearisation in its three phases (the double-float kernels may place a
+// block barrier between them so that the warps of a block fetch the long
+// straight-line code together).
+template <class T>
+RD_HD int linearise_core(const T Zbar[4], const T Z[3][4], const T nx[3], const T ny[3], const T hl[3],
+                         const Gas<T>& gas, T eps, TriLin<T>& L) {
+  int st = lin_roe_split(Zbar, Z, nx, ny, hl, gas, eps, L);
+  if (st) return st;
+  st = lin_assemble(L);
+  if (st) return st;
+  lin_nshares(Z, gas, L);
   return 0;
 }
 
