@@ -13,6 +13,7 @@
 #include <new>
 #include <vector>
 
+#include "rd_df64.h"
 #include "rd_device.h"
 #include "rd_internal.h"
 #include "rd_kernels.cuh"
@@ -155,6 +156,7 @@ extern "C" void rd_mesh_destroy(rd_mesh* m) {
   dev_free(m->vperm);
   for (int p = 0; p < 2; ++p)
     for (int k = 0; k < 6; ++k) dev_free(m->geo[p][k]);
+  for (int k = 0; k < 4; ++k) dev_free(m->geo_df[k]);
   mesh_boundary_free(m);
   if (m->own_stream) cudaStreamDestroy(m->stream);
   delete m;
@@ -317,7 +319,8 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
   } else {
     if (vr1) k_vr_reset<<<1, 1, 0, st>>>(vr1, ctl, 0);
     k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)s->W[a].p, (const T*)s->R1.p, ptr, ent, nullptr, V, gamma,
-                                          (T*)s->Ws.p, (T*)s->Zs.p, nullptr, ctl, nullptr, nullptr, vr1, wa1);
+                                          (T*)s->Ws.p, (T*)s->Zs.p, nullptr, ctl, nullptr, nullptr, vr1, wa1,
+                                          GhostArgs<T>(), df ? (float2*)s->dWdf.p : nullptr);
     mark(3);
     if (df)
       CK(launch_tri_stage2_df(s, a, gt, TB, st));
@@ -438,6 +441,7 @@ int alloc_state(rd_state* s) {
     CK(dev_alloc(s->Ws, 4 * nv * ts, st));
     CK(dev_alloc(s->Zs, 4 * nv * ts, st));
     CK(dev_alloc(s->rec, 16 * nt * ts, st));
+    if (s->p.precision == RD_DF64) CK(dev_alloc(s->dWdf, 4 * nv * 2 * sizeof(float), st));
   }
   DevCtl c{};
   CU(cudaMemcpyAsync(s->ctl.p, &c, sizeof(DevCtl), cudaMemcpyHostToDevice, st));
@@ -510,6 +514,7 @@ extern "C" int rd_state_init(rd_mesh* m, const double* W, const rd_params* p, rd
   s->pi = p->precision == RD_FP32 ? 1 : 0;  // RD_DF64 keeps the FP64 state
   s->ts = s->pi == 0 ? sizeof(double) : sizeof(float);
   int st = s->pi == 0 ? mesh_geometry<double>(m) : mesh_geometry<float>(m);
+  if (st == RD_OK && p->precision == RD_DF64) st = mesh_geometry_df(m);
   if (st == RD_OK) st = alloc_state(s);
   if (st == RD_OK) st = s->pi == 0 ? upload_state<double>(s, W, 0) : upload_state<float>(s, W, 0);
   if (st != RD_OK) {
@@ -639,11 +644,11 @@ extern "C" int rd_state_autotune(rd_state* s, int32_t* tri_block, int32_t* vtx_b
     CU(cudaEventElapsedTime(&ms, ev[0], ev[6]));
     return RD_OK;
   };
-  int best_t = TRI_BLOCK, best_v = VTX_BLOCK, best_o = 1, rc = RD_OK;
+  int best_t = TRI_BLOCK, best_v = VTX_BLOCK, best_o = s->df_occ, rc = RD_OK;
   float best = 1e30f, ms = 0.f;
-  // DF64: 255- and 128-register triangle kernels, the latter also with block barriers between phases
-  const int n_occ = s->p.precision == RD_DF64 ? 3 : 1;
-  for (int o = 1; o <= n_occ; ++o) {
+  // DF64: the triangle kernels without and with block barriers between phases
+  const int o0 = s->p.precision == RD_DF64 ? 2 : s->df_occ, o1 = s->p.precision == RD_DF64 ? 3 : s->df_occ;
+  for (int o = o0; o <= o1; ++o) {
     s->df_occ = o;
     for (int tb : tri_c) {
       if ((rc = time_step(tb, VTX_BLOCK, ms)) != RD_OK) break;
@@ -704,7 +709,7 @@ extern "C" int rd_state_set_launch_shapes(rd_state* s, int32_t tri_block, int32_
   if (!s) return RD_EINVAL;
   if (tri_block != 64 && tri_block != 128 && tri_block != 192 && tri_block != 256) return RD_EINVAL;
   if (vtx_block != 128 && vtx_block != 256 && vtx_block != 512) return RD_EINVAL;
-  if (df_occ < 1 || df_occ > 3) return RD_EINVAL;
+  if (df_occ < 2 || df_occ > 3) return RD_EINVAL;
   s->tri_block = tri_block;
   s->vtx_block = vtx_block;
   s->df_occ = df_occ;
@@ -817,7 +822,7 @@ extern "C" void rd_state_destroy(rd_state* s) {
     dev_free(s->spd[b]);
   }
   DevBuf* bufs[] = {&s->Ws, &s->Zs, &s->R1, &s->share, &s->rec, &s->cfl, &s->partial, &s->ctl,
-                    &s->cons_partial, &s->cons_out, &s->stage, &s->vr, &s->ghostW};
+                    &s->cons_partial, &s->cons_out, &s->stage, &s->vr, &s->ghostW, &s->dWdf};
   for (DevBuf* b : bufs) dev_free(*b);
   adjoint_free(s->adj);
   tile_plan_free(s->tiles);

@@ -89,6 +89,9 @@ struct rd_mesh {
   // geometry per precision (0: double, 1: float): nx, ny, hl, area, lmax, V
   rd::DevBuf geo[2][6];
   bool geo_ready[2] = {false, false};
+  // RD_DF64: nx, ny, hl [3][nt] and area [nt] as double-float pairs (float2)
+  rd::DevBuf geo_df[4];
+  bool geo_df_ready = false;
   // boundary conditions (Sec. 3.5), set by rd_mesh_set_boundary
   int bc_version = 0;
   int32_t n_ghost = 0, n_wall = 0;
@@ -118,6 +121,7 @@ struct rd_state {
   size_t ts = 8;  // sizeof(T)
   rd::DevBuf W[2], Z[2], spd[2];
   rd::DevBuf Ws, Zs, R1, share, rec, cfl, partial, ctl, cons_partial, cons_out;
+  rd::DevBuf dWdf;         // RD_DF64 two-stage: W* - W^n as double-float pairs, [nv][4] float2
   rd::DevBuf stage;        // [4][nv] double, caller vertex order (host I/O)
   rd::DevBuf vr;           // RD_BX2: |v| max / min bits, slot 0 (W^n) and slot 1 (W*)
   rd::DevBuf ghostW;       // [n_ghost][4] T: initial state of the ghost vertices
@@ -125,7 +129,7 @@ struct rd_state {
   bool bc_init = false;
   long long launched = 0;  // host view of the committed step count (parity of the buffers)
   int tri_block = rd::TRI_BLOCK, vtx_block = rd::VTX_BLOCK;  // launch shapes (autotuned)
-  int df_occ = 1;  // RD_DF64 triangle-kernel variant (1: 255 registers, 2: 128, 3: 128 with phase barriers; autotuned)
+  int df_occ = 2;  // RD_DF64 triangle-kernel variant (2: 128 registers, 3: 128 with phase barriers; autotuned)
   rd::TilePlan* tiles = nullptr;  // tiled step (nullptr: per-triangle share arrays)
   cudaGraphExec_t g2 = nullptr;  // two steps (even -> odd -> even)
   bool graph_failed = false;

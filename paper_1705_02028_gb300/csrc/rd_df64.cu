@@ -13,6 +13,8 @@
 // double-float (two floats per value: the bytes of one double).
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "rd_device.h"
 #include "rd_df64.h"
 #include "rd_dfloat.cuh"
@@ -24,21 +26,38 @@ namespace rd {
 
 namespace {
 
-__device__ __forceinline__ dfloat to_df(double x) {
-  const float h = __double2float_rn(x);
-  return dfloat(h, __double2float_rn(x - (double)h));
-}
-__device__ __forceinline__ double from_df(dfloat a) { return (double)a.hi + (double)a.lo; }
+using dw::from_df;
+using dw::to_df;
 
-// Zbar (double, then split) and dZ_i = Z_i - Zbar of one triangle.
+// Zbar (double, then split) and dZ_i = Z_i - Zbar of one triangle; the double
+// operations are non-contractible so that every kernel variant forms the same bits.
 __device__ __forceinline__ void split_nodal(const double Z[3][4], dfloat Zb[4], dfloat dZ[3][4]) {
   const double third = 1.0 / 3.0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const double zb = (Z[0][k] + Z[1][k] + Z[2][k]) * third;
+    const double zb = __dmul_rn(__dadd_rn(__dadd_rn(Z[0][k], Z[1][k]), Z[2][k]), third);
     Zb[k] = to_df(zb);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) dZ[c][k] = to_df(Z[c][k] - zb);
+    for (int c = 0; c < 3; ++c) dZ[c][k] = to_df(__dsub_rn(Z[c][k], zb));
+  }
+}
+
+__device__ __forceinline__ dfloat ld_df(const float2* p) {
+  const float2 a = __ldg(p);
+  return dfloat(a.x, a.y);
+}
+
+// Per-triangle geometry of the double-float kernels: unit normals and half
+// edge lengths [3][nt] and areas [nt] already split into double-float pairs
+// (float2), so no conversion runs per triangle; l_max in double for the CFL term.
+__device__ __forceinline__ void load_tri_df(int t, int nt, const int* __restrict__ tri, const DevGeoDF& g, int v[3],
+                                            dfloat nx[3], dfloat ny[3], dfloat hl[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    v[c] = __ldg(tri + (size_t)c * nt + t);
+    nx[c] = ld_df(g.nx + (size_t)c * nt + t);
+    ny[c] = ld_df(g.ny + (size_t)c * nt + t);
+    hl[c] = ld_df(g.hl + (size_t)c * nt + t);
   }
 }
 
@@ -58,9 +77,10 @@ __device__ __forceinline__ void ld_rec(const dfloat* p, dfloat r[16]) {
   }
 }
 
-// OCC: minimum resident 256-thread blocks per SM asked of the compiler (1: up
-// to 255 registers per thread, no spills; 2: 128 registers, a few hundred bytes
-// of spills, twice the resident warps).  SYNC: a block barrier between the
+// OCC: minimum resident 256-thread blocks per SM asked of the compiler (2: 128
+// registers per thread, a few hundred bytes of spills; measured 1.4-1.7x faster
+// than the spill-free 255-register build, which leaves too few warps to hide
+// the double-float dependency chains).  SYNC: a block barrier between the
 // phases of the per-triangle algebra.  The body is ~10^4 instructions of
 // straight-line code, far more than the instruction caches hold, and warps
 // that drift apart miss in them (ncu: "no instruction" is the leading stall);
@@ -83,7 +103,7 @@ __device__ __forceinline__ bool block_stop(const DevCtl* ctl) {
 
 template <int SCHEME, int OCC, bool SYNC>
 __global__ void __launch_bounds__(256, OCC)
-    k_tri_stage1_df(int nt, const int* __restrict__ tri, DevGeo<double> g, const double* __restrict__ Z,
+    k_tri_stage1_df(int nt, const int* __restrict__ tri, DevGeoDF g, const double* __restrict__ Z,
                     const double* __restrict__ spd, Gas<dfloat> gas, dfloat eps, double* __restrict__ share,
                     dfloat* __restrict__ rec, double* __restrict__ cfl, DevCtl* ctl, BlendArgs<double> ba) {
   const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -95,28 +115,31 @@ __global__ void __launch_bounds__(256, OCC)
   const bool act = t0 < nt;
   const int t = act ? t0 : nt - 1;
   int v[3];
-  double nx[3], ny[3], hl[3], Zc[3][4];
-  load_tri(t, nt, tri, g, v, nx, ny, hl);
+  double Zc[3][4];
+  dfloat nxd[3], nyd[3], hld[3];
+  load_tri_df(t, nt, tri, g, v, nxd, nyd, hld);
 #pragma unroll
   for (int c = 0; c < 3; ++c) load_vec4(Z, v[c], Zc[c]);
   {
     double s0 = __ldg(spd + v[0]), s1 = __ldg(spd + v[1]), s2 = __ldg(spd + v[2]);
     double lam = mag_less(s1, s0) ? s0 : s1;  // speeds are >= 0
     lam = mag_less(s2, lam) ? lam : s2;
-    if (act) cfl[t] = __ldg(g.lmax + t) * lam;
+    if (act) cfl[t] = __dmul_rn(__ldg(g.lmax + t), lam);
   }
   const int mode = SCHEME == RD_BMAX2 ? ba.mode : BLEND_B;
   double thx = 0.0;
-  if (SCHEME == RD_BMAX2 && mode == BLEND_X)
-    thx = bx_theta(Zc, nx, ny, hl, __ldg(g.area + t), ba.L, vrange_of<double>(ba.vr));
-  dfloat Zb[4], dZ[3][4], nxd[3], nyd[3], hld[3];
-  split_nodal(Zc, Zb, dZ);
+  if (SCHEME == RD_BMAX2 && mode == BLEND_X) {
+    double nx[3], ny[3], hl[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    nxd[c] = to_df(nx[c]);
-    nyd[c] = to_df(ny[c]);
-    hld[c] = to_df(hl[c]);
+    for (int c = 0; c < 3; ++c) {
+      nx[c] = from_df(nxd[c]);
+      ny[c] = from_df(nyd[c]);
+      hl[c] = from_df(hld[c]);
+    }
+    thx = bx_theta(Zc, nx, ny, hl, from_df(ld_df(g.area + t)), ba.L, vrange_of<double>(ba.vr));
   }
+  dfloat Zb[4], dZ[3][4];
+  split_nodal(Zc, Zb, dZ);
   dfloat out[3][4], r[16];
   int st;
   if (SYNC) {
@@ -148,9 +171,9 @@ __global__ void __launch_bounds__(256, OCC)
 
 template <int SCHEME, int OCC, bool SYNC>
 __global__ void __launch_bounds__(256, OCC)
-    k_tri_stage2_df(int nt, const int* __restrict__ tri, DevGeo<double> g, const double* __restrict__ Zs,
-                    const double* __restrict__ Wn, const double* __restrict__ Ws, const dfloat* __restrict__ rec,
-                    Gas<dfloat> gas, dfloat eps, double* __restrict__ share, DevCtl* ctl, BlendArgs<double> ba) {
+    k_tri_stage2_df(int nt, const int* __restrict__ tri, DevGeoDF g, const double* __restrict__ Zs,
+                    const float2* __restrict__ dw, const dfloat* __restrict__ rec, Gas<dfloat> gas, dfloat eps,
+                    double* __restrict__ share, DevCtl* ctl, BlendArgs<double> ba) {
   const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (SYNC) {
     if (block_stop(ctl)) return;
@@ -160,35 +183,41 @@ __global__ void __launch_bounds__(256, OCC)
   const bool act = t0 < nt;
   const int t = act ? t0 : nt - 1;
   int v[3];
-  double nx[3], ny[3], hl[3], Zc[3][4];
-  load_tri(t, nt, tri, g, v, nx, ny, hl);
+  double Zc[3][4];
+  dfloat nxd[3], nyd[3], hld[3];
+  load_tri_df(t, nt, tri, g, v, nxd, nyd, hld);
+  // W*_i - W^n_i, split into double-float by the stage-1 vertex update
   dfloat dW[3][4];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    double wn[4], ws[4];
     load_vec4(Zs, v[c], Zc[c]);
-    load_vec4(Wn, v[c], wn);
-    load_vec4(Ws, v[c], ws);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) dW[c][k] = to_df(ws[k] - wn[k]);
+    const float4* q = reinterpret_cast<const float4*>(dw + 4 * (size_t)v[c]);
+    const float4 a = __ldg(q), b = __ldg(q + 1);
+    dW[c][0] = dfloat(a.x, a.y);
+    dW[c][1] = dfloat(a.z, a.w);
+    dW[c][2] = dfloat(b.x, b.y);
+    dW[c][3] = dfloat(b.z, b.w);
   }
   dfloat r[16];
   ld_rec(rec + (size_t)t * 16, r);
-  const double area = __ldg(g.area + t);
+  const dfloat aread = ld_df(g.area + t);
   const int mode = SCHEME == RD_BMAX2 ? ba.mode : BLEND_B;
   const int sl = (SCHEME == RD_BMAX2 || SCHEME == RD_LDA2) ? ba.sl : 0;
   double thx = 0.0;
-  if (SCHEME == RD_BMAX2 && mode == BLEND_X) thx = bx_theta(Zc, nx, ny, hl, area, ba.L, vrange_of<double>(ba.vr));
-  dfloat Zb[4], dZ[3][4], nxd[3], nyd[3], hld[3];
-  split_nodal(Zc, Zb, dZ);
+  if (SCHEME == RD_BMAX2 && mode == BLEND_X) {
+    double nx[3], ny[3], hl[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    nxd[c] = to_df(nx[c]);
-    nyd[c] = to_df(ny[c]);
-    hld[c] = to_df(hl[c]);
+    for (int c = 0; c < 3; ++c) {
+      nx[c] = from_df(nxd[c]);
+      ny[c] = from_df(nyd[c]);
+      hl[c] = from_df(hld[c]);
+    }
+    thx = bx_theta(Zc, nx, ny, hl, from_df(aread), ba.L, vrange_of<double>(ba.vr));
   }
+  dfloat Zb[4], dZ[3][4];
+  split_nodal(Zc, Zb, dZ);
   dfloat out[3][4];
-  const dfloat dt = to_df(ctl->dt), aread = to_df(area);
+  const dfloat dt = to_df(ctl->dt);
   int st;
   if (SYNC) {
     TriLin<dfloat> L;
@@ -268,30 +297,27 @@ int stage2_df_occ(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba
   const dfloat eps(p.eps_fix);
   const dfloat* rec = (const dfloat*)a.rec;
   if (p.scheme == RD_LDA2)
-    k_tri_stage2_df<RD_LDA2, OCC, SYNC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.Wn, a.Ws, rec, gas, eps, a.share,
+    k_tri_stage2_df<RD_LDA2, OCC, SYNC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.dw, rec, gas, eps, a.share,
                                                           a.ctl, ba);
   else if (p.scheme == RD_B2 && p.lumping == RD_LUMP_GLOBAL)
-    k_tri_stage2_df<RD_B2, OCC, SYNC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.Wn, a.Ws, rec, gas, eps, a.share,
+    k_tri_stage2_df<RD_B2, OCC, SYNC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.dw, rec, gas, eps, a.share,
                                                         a.ctl, ba);
   else
-    k_tri_stage2_df<RD_BMAX2, OCC, SYNC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.Wn, a.Ws, rec, gas, eps,
-                                                           a.share, a.ctl, ba);
+    k_tri_stage2_df<RD_BMAX2, OCC, SYNC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.dw, rec, gas, eps, a.share, a.ctl, ba);
   CU(cudaGetLastError());
   return RD_OK;
 }
 
 int launch_tri_stage1_df(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
                          cudaStream_t st) {
-  if (a.occ == 3) return stage1_df_occ<2, true>(p, a, ba, grid, block, st);
-  return a.occ == 2 ? stage1_df_occ<2, false>(p, a, ba, grid, block, st)
-                    : stage1_df_occ<1, false>(p, a, ba, grid, block, st);
+  return a.occ == 3 ? stage1_df_occ<2, true>(p, a, ba, grid, block, st)
+                    : stage1_df_occ<2, false>(p, a, ba, grid, block, st);
 }
 
 int launch_tri_stage2_df(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
                          cudaStream_t st) {
-  if (a.occ == 3) return stage2_df_occ<2, true>(p, a, ba, grid, block, st);
-  return a.occ == 2 ? stage2_df_occ<2, false>(p, a, ba, grid, block, st)
-                    : stage2_df_occ<1, false>(p, a, ba, grid, block, st);
+  return a.occ == 3 ? stage2_df_occ<2, true>(p, a, ba, grid, block, st)
+                    : stage2_df_occ<2, false>(p, a, ba, grid, block, st);
 }
 
 // The state's arrays for the launchers above.
@@ -300,10 +326,10 @@ static TriArraysDF state_arrays(const rd_state* s) {
   TriArraysDF a;
   a.nt = m->h.nt;
   a.tri = (const int*)m->tri.p;
-  a.g.nx = (const double*)m->geo[0][0].p;
-  a.g.ny = (const double*)m->geo[0][1].p;
-  a.g.hl = (const double*)m->geo[0][2].p;
-  a.g.area = (const double*)m->geo[0][3].p;
+  a.g.nx = (const float2*)m->geo_df[0].p;
+  a.g.ny = (const float2*)m->geo_df[1].p;
+  a.g.hl = (const float2*)m->geo_df[2].p;
+  a.g.area = (const float2*)m->geo_df[3].p;
   a.g.lmax = (const double*)m->geo[0][4].p;
   a.share = (double*)s->share.p;
   a.rec = s->rec.p;
@@ -325,12 +351,35 @@ int launch_tri_stage1_df(const rd_state* s, int a, unsigned grid, int block, cud
 int launch_tri_stage2_df(const rd_state* s, int a, unsigned grid, int block, cudaStream_t st) {
   TriArraysDF x = state_arrays(s);
   x.Z = (const double*)s->Zs.p;
-  x.Wn = (const double*)s->W[a].p;
-  x.Ws = (const double*)s->Ws.p;
+  x.dw = (const float2*)s->dWdf.p;
   BlendArgs<double> ba = tile_blend_args<double>(s);
   unsigned long long* vr0 = (unsigned long long*)s->vr.p;
   ba.vr = vr0 ? vr0 + 2 : nullptr;
   return launch_tri_stage2_df(s->p, x, ba, grid, block, st);
+}
+
+// Per-triangle geometry split into double-float pairs (the same split as
+// to_df on the device): nx, ny, hl [3][nt] and area [nt] as float2.
+int mesh_geometry_df(rd_mesh* m) {
+  if (m->geo_df_ready) return RD_OK;
+  const std::vector<double>* src[4] = {&m->h.nx, &m->h.ny, &m->h.hl, &m->h.area};
+  std::vector<float2> tmp;
+  for (int k = 0; k < 4; ++k) {
+    split_df_host(*src[k], tmp);
+    CK(dev_alloc(m->geo_df[k], tmp.size() * sizeof(float2), m->stream));
+    CU(cudaMemcpyAsync(m->geo_df[k].p, tmp.data(), tmp.size() * sizeof(float2), cudaMemcpyHostToDevice, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+  }
+  m->geo_df_ready = true;
+  return RD_OK;
+}
+
+void split_df_host(const std::vector<double>& x, std::vector<float2>& out) {
+  out.resize(x.size());
+  for (size_t i = 0; i < x.size(); ++i) {
+    const float h = (float)x[i];
+    out[i] = make_float2(h, (float)(x[i] - (double)h));
+  }
 }
 
 }  // namespace rd

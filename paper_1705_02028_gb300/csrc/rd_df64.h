@@ -5,24 +5,39 @@
 #include "rd_device.h"
 #include "rd_kernels.cuh"
 
+#include <vector>
+
 namespace rd {
 
-// FP64 layout; rec holds 16 double-float values per triangle.  Stage 1 reads
-// Z, spd; stage 2 reads Z (= Z*), Wn, Ws.
+// Geometry of the double-float kernels: nx, ny, hl [3][nt] and area [nt] as
+// double-float pairs (float2 hi, lo), l_max [nt] in double.
+struct DevGeoDF {
+  const float2 *nx = nullptr, *ny = nullptr, *hl = nullptr, *area = nullptr;
+  const double* lmax = nullptr;
+};
+
+// FP64 state layout; rec holds 16 double-float values per triangle.  Stage 1
+// reads Z, spd; stage 2 reads Z (= Z*) and dw = W* - W^n split into
+// double-float pairs ([nv][4] float2, written by the stage-1 update).
 struct TriArraysDF {
   int nt = 0;
   const int* tri = nullptr;
-  DevGeo<double> g{};
-  const double *Z = nullptr, *spd = nullptr, *Wn = nullptr, *Ws = nullptr;
+  DevGeoDF g{};
+  const double *Z = nullptr, *spd = nullptr;
+  const float2* dw = nullptr;
   double* share = nullptr;
   void* rec = nullptr;
   double* cfl = nullptr;
   DevCtl* ctl = nullptr;
-  int occ = 1;  // kernel variant: 1 (255 registers), 2 (128), 3 (128, block barriers between phases)
+  int occ = 2;  // kernel variant: 2 (128 registers), 3 (128, block barriers between phases)
 };
 int launch_tri_stage1_df(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
                          cudaStream_t st);
 int launch_tri_stage2_df(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
                          cudaStream_t st);
+
+// Upload the mesh's double-float geometry once (rd_mesh::geo_df).
+int mesh_geometry_df(rd_mesh* m);
+void split_df_host(const std::vector<double>& x, std::vector<float2>& out);
 
 }  // namespace rd

@@ -183,6 +183,17 @@ RD_HD bool operator>(dfloat a, dfloat b) { return b < a; }
 RD_HD bool operator<=(dfloat a, dfloat b) { return !(b < a); }
 RD_HD bool operator>=(dfloat a, dfloat b) { return !(a < b); }
 
+#if defined(__CUDACC__)
+// double -> double-float (hi = x rounded to single, lo = the rest rounded to
+// single) and back, with the double operations written as non-contractible
+// intrinsics so that every kernel forms the same bits.
+__device__ __forceinline__ dfloat to_df(double x) {
+  const float h = __double2float_rn(x);
+  return dfloat(h, __double2float_rn(__dsub_rn(x, (double)h)));
+}
+__device__ __forceinline__ double from_df(dfloat a) { return __dadd_rn((double)a.hi, (double)a.lo); }
+#endif
+
 }  // namespace dw
 using dw::dfloat;
 

@@ -29,6 +29,7 @@
 #include "rd_internal.h"
 
 #define RD_HD __host__ __device__ __forceinline__
+#include "rd_dfloat.cuh"
 
 namespace rd {
 
@@ -1236,7 +1237,8 @@ __global__ void __launch_bounds__(512) k_update(int nv, const T* __restrict__ Wi
                                                 DevCtl* ctl, const double* __restrict__ dtm = nullptr,
                                                 const uint16_t* __restrict__ vmesh = nullptr,
                                                 unsigned long long* __restrict__ vr_out = nullptr,
-                                                WallArgs<T> wa = WallArgs<T>(), GhostArgs<T> ga = GhostArgs<T>()) {
+                                                WallArgs<T> wa = WallArgs<T>(), GhostArgs<T> ga = GhostArgs<T>(),
+                                                float2* __restrict__ dw_df = nullptr) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool act = i < nv && !ctl->stop;
   if (!act && !vr_out) return;
@@ -1273,6 +1275,18 @@ __global__ void __launch_bounds__(512) k_update(int nv, const T* __restrict__ Wi
   st4(Wout + 4 * (size_t)i, W);
   st4(Zout + 4 * (size_t)i, Z);
   if (spdout) spdout[i] = spd;
+  if constexpr (sizeof(T) == 8) {
+    if (dw_df) {  // RD_DF64 stage 1: W* - W^n as double-float pairs for the stage-2 triangle kernel
+      T w0[4];
+      load_vec4(Win, i, w0);
+      dfloat d[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) d[k] = dw::to_df(__dsub_rn(W[k], w0[k]));
+      float4* o = reinterpret_cast<float4*>(dw_df + 4 * (size_t)i);
+      o[0] = make_float4(d[0].hi, d[0].lo, d[1].hi, d[1].lo);
+      o[1] = make_float4(d[2].hi, d[2].lo, d[3].hi, d[3].lo);
+    }
+  }
   if (!ok) {
     atomicOr(&ctl->status, ST_NONPHYS_VERTEX);
     ctl->stop = 1;

@@ -39,6 +39,7 @@ struct rd_part {
   int32_t n_own = 0, n_gh = 0, nlt = 0, n_send = 0;
   DevBuf tri, ptr, ent, sidx, geo[6];  // geo: nx, ny, hl [3][nlt], area, lmax [nlt], V [n_local]
   DevBuf W[2], Z[2], spd[2], Ws, Zs, spds, R1, share, rec, cfl, partial, ctl, stage;
+  DevBuf geo_df[4], dWdf;  // RD_DF64: double-float geometry of the local triangles, W* - W^n of the local vertices
   int a = 0;
   int tri_block = TRI_BLOCK, vtx_block = VTX_BLOCK;
 };
@@ -86,6 +87,23 @@ __global__ void k_part_out(int n, const T* __restrict__ W, double* __restrict__ 
   for (int k = 0; k < 4; ++k) out[(size_t)k * n + i] = (double)W[4 * (size_t)i + k];
 }
 
+// RD_DF64: W* - W^n of the ghost vertices as double-float pairs (the owned
+// ones come from the stage-1 update).
+__global__ void k_dw_split(int n, const double* __restrict__ Wn, const double* __restrict__ Ws,
+                           float2* __restrict__ dw) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a[4], b[4];
+  load_vec4(Wn, i, a);
+  load_vec4(Ws, i, b);
+  dfloat d[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) d[k] = dw::to_df(__dsub_rn(b[k], a[k]));
+  float4* o = reinterpret_cast<float4*>(dw + 4 * (size_t)i);
+  o[0] = make_float4(d[0].hi, d[0].lo, d[1].hi, d[1].lo);
+  o[1] = make_float4(d[2].hi, d[2].lo, d[3].hi, d[3].lo);
+}
+
 template <class T>
 int upload(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
   CK(dev_alloc(b, std::max<size_t>(v.size(), 1) * sizeof(T), st));
@@ -120,6 +138,19 @@ int part_alloc(rd_part* q, const double* Wc) {
   CK(upload(q->geo[4], g1, st));
   for (size_t i = 0; i < nl; ++i) gv[i] = (T)h.V[pl.lv[i]];
   CK(upload(q->geo[5], gv, st));
+  if (q->p.precision == RD_DF64) {
+    const std::vector<double>* per[4] = {&h.nx, &h.ny, &h.hl, &h.area};
+    for (int k = 0; k < 4; ++k) {
+      const int ncomp = k < 3 ? 3 : 1;
+      std::vector<double> loc((size_t)ncomp * nlt);
+      for (int c = 0; c < ncomp; ++c)
+        for (size_t j = 0; j < nlt; ++j) loc[c * nlt + j] = (*per[k])[(size_t)c * h.nt + pl.lt[j]];
+      std::vector<float2> sp;
+      split_df_host(loc, sp);
+      CK(upload(q->geo_df[k], sp, st));
+    }
+    CK(dev_alloc(q->dWdf, 4 * nl * sizeof(float2), st));
+  }
   const size_t ts = sizeof(T);
   for (int b = 0; b < 2; ++b) {
     CK(dev_alloc(q->W[b], 4 * nl * ts, st));
@@ -178,6 +209,16 @@ DevGeo<T> part_geo(const rd_part* q) {
   return g;
 }
 
+DevGeoDF part_geo_df(const rd_part* q) {
+  DevGeoDF g;
+  g.nx = (const float2*)q->geo_df[0].p;
+  g.ny = (const float2*)q->geo_df[1].p;
+  g.hl = (const float2*)q->geo_df[2].p;
+  g.area = (const float2*)q->geo_df[3].p;
+  g.lmax = (const double*)q->geo[4].p;
+  return g;
+}
+
 template <class T>
 int part_phase(rd_part* q, int phase, void* buf) {
   cudaStream_t st = q->m->stream;
@@ -214,6 +255,12 @@ int part_phase(rd_part* q, int phase, void* buf) {
       T* Zd = (T*)(w ? q->Z[a].p : q->Zs.p) + off;
       T* Sd = (T*)(w ? q->spd[a].p : q->spds.p) + q->n_own;
       k_prepare<T><<<nblk(q->n_gh, VTX_BLOCK), VTX_BLOCK, 0, st>>>(q->n_gh, dst, gamma, Zd, Sd, ctl);
+      if constexpr (sizeof(T) == 8) {
+        if (!w && df)
+          k_dw_split<<<nblk(q->n_gh, VTX_BLOCK), VTX_BLOCK, 0, st>>>(q->n_gh, (const double*)q->W[a].p + off,
+                                                                     (const double*)q->Ws.p + off,
+                                                                     (float2*)q->dWdf.p + off);
+      }
       break;
     }
     case RD_PART_STAGE1: {
@@ -229,7 +276,7 @@ int part_phase(rd_part* q, int phase, void* buf) {
             TriArraysDF x;
             x.nt = q->nlt;
             x.tri = tri;
-            x.g = g;
+            x.g = part_geo_df(q);
             x.Z = Za;
             x.spd = Sa;
             x.share = share;
@@ -261,7 +308,8 @@ int part_phase(rd_part* q, int phase, void* buf) {
         q->a = b;
       } else {
         k_update<T><<<gv, VB, 0, st>>>(q->n_own, (const T*)q->W[a].p, (const T*)q->R1.p, ptr, ent, nullptr, V, gamma,
-                                       (T*)q->Ws.p, (T*)q->Zs.p, nullptr, ctl);
+                                       (T*)q->Ws.p, (T*)q->Zs.p, nullptr, ctl, nullptr, nullptr, nullptr,
+                                       WallArgs<T>(), GhostArgs<T>(), df ? (float2*)q->dWdf.p : nullptr);
       }
       break;
     }
@@ -274,10 +322,9 @@ int part_phase(rd_part* q, int phase, void* buf) {
             TriArraysDF x;
             x.nt = q->nlt;
             x.tri = tri;
-            x.g = g;
+            x.g = part_geo_df(q);
             x.Z = (const T*)q->Zs.p;
-            x.Wn = (const T*)q->W[a].p;
-            x.Ws = (const T*)q->Ws.p;
+            x.dw = (const float2*)q->dWdf.p;
             x.share = share;
             x.rec = q->rec.p;
             x.ctl = ctl;
@@ -357,6 +404,8 @@ extern "C" void rd_part_destroy(rd_part* q) {
                     &q->ctl, &q->stage};
   for (DevBuf* b : bufs) dev_free(*b);
   for (auto& g : q->geo) dev_free(g);
+  for (auto& g : q->geo_df) dev_free(g);
+  dev_free(q->dWdf);
   delete q;
 }
 
