@@ -103,20 +103,6 @@ RD_HD double rcp(double x) {
 #endif
 }
 
-// In single precision on the device: the hardware's approximate reciprocal
-// (rcp.approx.ftz.f32, within about one ulp), one instruction instead of the
-// IEEE division sequence; the FP32 path's accuracy measure is its L1 error
-// against the FP64 oracle, which this does not change measurably.
-RD_HD float rcp(float x) {
-#if defined(__CUDA_ARCH__) && RD_FAST_RCP
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-#else
-  return 1.0f / x;
-#endif
-}
-
 // Blends of N and LDA (Sec. 3.3.3): diagonal Theta (B), every diagonal entry
 // max_k / min_k Theta_kk (Bmax / Bmin), or the scalar shock-sensor theta (Bx).
 enum : int { BLEND_B = 0, BLEND_MAX = 1, BLEND_MIN = 2, BLEND_X = 3 };
