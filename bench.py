@@ -87,6 +87,23 @@ def kernel_alg_bytes(kernel: str, scheme: str, s: int) -> float:
     raise KeyError(kernel)
 
 
+def design_min_bytes(scheme: str, s: int) -> float:
+    """This design's own floor of DRAM bytes per triangle-update of the untiled step:
+    the per-triangle arrays it reads and writes (geometry 11 words + 12 B ids per
+    triangle kernel, the 12-word shares written and gathered back once, the 16-word
+    stage-2 record written and read, the CFL term) plus the vertex arrays at N_v =
+    N_t / 2 (stage 1: Z, |v|+c in; gather: R1 out; update: W^n, R1 in, W*, Z* out;
+    stage 2: Z*, W^n, W* in; update: W*, W out, Z, |v|+c out)."""
+    geo = 11 * s + 12
+    if alg_scheme(scheme) == "N1":
+        tri = geo + 12 * s + 12 * s + s + s                      # shares out + back, CFL term out + back
+        vtx = 0.5 * (5 * s + 4 * s + 4 * s + 9 * s)              # Z, spd in; R1; W, R1 in; W, Z, spd out
+        return tri + vtx
+    tri = 2 * geo + 2 * (12 * s + 12 * s) + 2 * 16 * s + 2 * s     # two stages: shares, record, CFL term
+    vtx = 0.5 * (5 * s + 4 * s + 8 * s + 8 * s + 12 * s + 8 * s + 9 * s)
+    return tri + vtx
+
+
 def parse():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -110,7 +127,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form companion measurement")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tiling", default="auto",
-                    help="tiled step: 'auto' (the autotuner's choice), 'none', or TRIANGLESxTHREADS, e.g. 512x128")
+                    help="tiled step: 'auto' (the autotuner's choice), 'none', or TRIANGLESxTHREADS, e.g. 512x128 "
+                         "(suffix g: geometry staged in shared memory, e.g. 512x128g)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-rollout companion measurement")
     ap.add_argument("--no-meshgen", action="store_true", help="skip the mesh-generation companion measurement")
     ap.add_argument("--multi", choices=["partition", "replicas"], default="partition",
@@ -223,25 +241,36 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def tiling_info(t):
+def tiling_info(t, flags=0):
     """Tiled-step choice of the autotuner (rd_state_get_tiling), None when untiled."""
     if not t or not t[0]:
         return None
-    return {"tile_triangles": t[0], "threads": t[1], "boundary_vertices": t[2]}
+    return {"tile_triangles": t[0], "threads": t[1], "boundary_vertices": t[2],
+            "geometry_in_shared_memory": bool(flags & 1)}
+
+
+# ncu captures are taken on a smaller case of the same kernel (full-set captures
+# of the 4096^2 workload are too large to replay); DRAM bytes per triangle carry
+# over because every per-triangle and per-vertex array is touched once per launch.
+TRAFFIC_CAPTURE = {"khi4096_B2": "khi2048_B2", "khi4096j_B2": "khi2048j_B2"}
 
 
 def ncu_traffic(workload, precision, kernel, nt):
     """DRAM bytes per launch of a kernel from the committed ncu summary, scaled to nt
-    triangles; None when missing or taken on a different kernel source."""
+    triangles, with the workload it was captured on; None when missing or taken on a
+    different kernel source."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         d = json.load(open(path))
     except Exception:
         return None
-    e = d.get(f"{workload}:{precision}:{kernel}")
+    cap = workload if f"{workload}:{precision}:{kernel}" in d else TRAFFIC_CAPTURE.get(workload, workload)
+    e = d.get(f"{cap}:{precision}:{kernel}")
     if not e or e.get("source_hash") != kernel_source_hash():
         return None
-    return float(e["dram_bytes_per_triangle"]) * nt
+    return {"bytes_per_launch": float(e["dram_bytes_per_triangle"]) * nt,
+            "bytes_per_triangle": float(e["dram_bytes_per_triangle"]),
+            "captured_on": cap, "scaled": cap != workload}
 
 
 def run_state_timing(binding, mesh_dev, W0, scheme, precision, steps, warmup, ws, clocks=None, autotune=True,
@@ -252,8 +281,9 @@ def run_state_timing(binding, mesh_dev, W0, scheme, precision, steps, warmup, ws
     if tiling == "none":
         s.set_tiling(0)
     elif tiling != "auto":
-        tt, bt = (int(x) for x in tiling.lower().split("x"))
-        s.set_tiling(tt, bt)
+        gs = tiling.lower().endswith("g")
+        tt, bt = (int(x) for x in tiling.lower().rstrip("g").split("x"))
+        s.set_tiling(tt, bt, stage_geometry=gs)
     s.tiles = s.tiling()
     s.run(warmup)
     st = mesh_dev.stream
@@ -337,7 +367,10 @@ def ours(args, ws, rank, local):
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e12, "peak": peak / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / peak, "flops_per_triangle": fl,
                 "peak_source": "measured FP64 FMA probe (rd_probe_fma_peak), same GPU, same run",
-                "traffic": ncu_traffic(args.workload, args.precision, dom, nt)}
+                "traffic": None}
+        tr = ncu_traffic(args.workload, args.precision, dom, nt)
+        roof["traffic"] = tr["bytes_per_launch"] if tr else None
+        roof["traffic_source"] = tr
     else:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
@@ -347,7 +380,10 @@ def ours(args, ws, rank, local):
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm if achieved else None, "bytes_per_triangle": bpt,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
-                "traffic": ncu_traffic(args.workload, args.precision, dom, nt)}
+                "traffic": None}
+        tr = ncu_traffic(args.workload, args.precision, dom, nt)
+        roof["traffic"] = tr["bytes_per_launch"] if tr else None
+        roof["traffic_source"] = tr
     step_bytes = ALG_BYTES_STEP.get((alg_scheme(scheme), s_bytes))
     hbm_peak = 6765.0
     try:
@@ -356,7 +392,12 @@ def ours(args, ws, rank, local):
         pass
     step_hbm = {"alg_bytes_per_triangle": step_bytes,
                 "achieved_gbs": step_bytes * nt / (ms_step * 1e-3) / 1e9 if step_bytes else None,
-                "frac_of_measured_hbm": (step_bytes * nt / (ms_step * 1e-3) / 1e9) / hbm_peak if step_bytes else None}
+                "frac_of_measured_hbm": (step_bytes * nt / (ms_step * 1e-3) / 1e9) / hbm_peak if step_bytes else None,
+                "note": "alg_bytes_per_triangle is the ideal floor (22 s + 24 B: vertex arrays once per pass, "
+                        "geometry recomputed from coordinates); design_min_bytes_per_triangle is this design's own "
+                        "floor (precomputed per-triangle geometry, per-triangle shares and stage-2 record, every "
+                        "array touched once)",
+                "design_min_bytes_per_triangle": design_min_bytes(scheme, s_bytes)}
 
     # end to end through the public API with host buffers (pinned), every step
     Wh = torch.empty((4, nv), dtype=torch.float64, pin_memory=True).numpy()
@@ -389,7 +430,7 @@ def ours(args, ws, rank, local):
             "ms_per_step_graph": ms_graph, "per_kernel_ms": per_kernel,
             "launch_shapes": {"tri_block": shapes[0], "vtx_block": shapes[1], "source": "rd_state_autotune"}
             if shapes else None,
-            "tiling": tiling_info(s.tiles),
+            "tiling": tiling_info(s.tiles, s.tiling_flags()),
             "roofline": roof, "step_hbm": step_hbm, "e2e": e2e,
             "gpu_launches": launches * args.steps + 1,
             "clocks": clk}
@@ -405,10 +446,12 @@ def ours(args, ws, rank, local):
         a32 = b32 * nt / (pk32[d32] * 1e-3) / 1e9 if b32 else None
         sb32 = ALG_BYTES_STEP.get((alg_scheme(scheme), 4))
         line["fp32"] = {"value": ws * nt / (ms32 * 1e-3), "ms_per_step": ms32, "per_kernel_ms": pk32,
-                        "tiling": tiling_info(s32.tiles),
+                        "tiling": tiling_info(s32.tiles, s32.tiling_flags()),
                         "roofline": {"bound": "hbm", "kernel": d32, "achieved": a32, "peak": hbm, "unit": "GB/s",
                                      "frac": a32 / hbm if a32 else None, "bytes_per_triangle": b32,
-                                     "traffic": ncu_traffic(args.workload, "fp32", d32, nt)},
+                                     "traffic": (ncu_traffic(args.workload, "fp32", d32, nt) or {}).get(
+                                         "bytes_per_launch"),
+                                     "traffic_source": ncu_traffic(args.workload, "fp32", d32, nt)},
                         "step_hbm_frac_of_measured": sb32 * nt / (ms32 * 1e-3) / 1e9 / hbm}
         s32.close()
     # RD_DF64 companion: the same step with the triangle algebra in double-float

@@ -466,10 +466,18 @@ int rd_state_set_launch_shapes(rd_state *s, int32_t tri_block, int32_t vtx_block
  * per-block limit.  The host builds the tile plan (O(n_tri log) work) and
  * uploads it; the state's captured graph is rebuilt on the next rd_run. */
 int rd_state_set_tiling(rd_state *s, int32_t tile_triangles, int32_t threads);
+/* rd_state_set_tiling with flags: RD_TILE_STAGE_GEOMETRY copies each tile's
+ * geometry (normals, half edge lengths, areas, l_max, corner slots, boundary
+ * masks) into shared memory with the vertex states, before the triangle loop,
+ * so that the loop reads no device memory.  Results are bitwise the same. */
+#define RD_TILE_STAGE_GEOMETRY 1
+int rd_state_set_tiling_ex(rd_state *s, int32_t tile_triangles, int32_t threads, int32_t flags);
 /* Current tiling (0, 0, 0 when untiled) and the number of boundary vertices;
  * any pointer may be NULL. */
 int rd_state_get_tiling(const rd_state *s, int32_t *tile_triangles, int32_t *threads,
                         int32_t *n_boundary_vertices);
+/* Flags of the current tiling (0 when untiled). */
+int rd_state_get_tiling_flags(const rd_state *s, int32_t *flags);
 
 /* ---- batched form: many independent meshes, one graph launch -------------
  * rd_batch_create: n_mesh (1..65535) meshes created on the same stream, with

@@ -99,6 +99,8 @@ _SIGS = {
     "rd_state_launch_shapes": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p]),
     "rd_state_set_launch_shapes": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "rd_state_set_tiling": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
+    "rd_state_set_tiling_ex": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "rd_state_get_tiling_flags": (ctypes.c_int, [_vp, _i32p]),
     "rd_state_get_tiling": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p]),
     "rd_adjoint_forward": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _dp]),
     "rd_adjoint_backward": (ctypes.c_int, [_vp, _dp, _dp]),
@@ -421,9 +423,16 @@ class State:
         _check(_lib.rd_state_set_launch_shapes(self.handle, int(tri_block), int(vtx_block), int(df_occ)),
                "rd_state_set_launch_shapes")
 
-    def set_tiling(self, tile_triangles: int, threads: int = 128):
-        """Tiled step with tiles of `tile_triangles` triangles (0: untiled); rd_state_set_tiling."""
-        _check(_lib.rd_state_set_tiling(self.handle, int(tile_triangles), int(threads)), "rd_state_set_tiling")
+    def set_tiling(self, tile_triangles: int, threads: int = 128, stage_geometry: bool = False):
+        """Tiled step with tiles of `tile_triangles` triangles (0: untiled); rd_state_set_tiling_ex,
+        with the tile's geometry staged in shared memory when stage_geometry."""
+        _check(_lib.rd_state_set_tiling_ex(self.handle, int(tile_triangles), int(threads), 1 if stage_geometry else 0),
+               "rd_state_set_tiling_ex")
+
+    def tiling_flags(self) -> int:
+        out = ctypes.c_int32()
+        _check(_lib.rd_state_get_tiling_flags(self.handle, ctypes.byref(out)), "rd_state_get_tiling_flags")
+        return out.value
 
     def tiling(self):
         """(tile_triangles, threads, boundary vertices) of the current tiling; zeros when untiled."""

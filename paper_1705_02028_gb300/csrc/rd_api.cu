@@ -669,23 +669,27 @@ extern "C" int rd_state_autotune(rd_state* s, int32_t* tri_block, int32_t* vtx_b
     float untiled = 1e30f;
     rc = rd_state_set_tiling(s, 0, 0);
     if (rc == RD_OK) rc = time_step(best_t, best_v, untiled);
-    const int c32[][2] = {{256, 128}, {512, 128}, {512, 256}, {1024, 256}};
-    const int c64[][2] = {{128, 64}, {256, 64}, {256, 128}};
-    const int nc = s->pi == 0 ? 3 : 4;
-    int best_tt = 0, best_bt = 0;
+    // (tile triangles, threads, flags)
+    const int c32[][3] = {{256, 128, 0}, {512, 128, 0}, {512, 256, 0}, {1024, 256, 0},
+                          {256, 128, RD_TILE_STAGE_GEOMETRY}, {512, 128, RD_TILE_STAGE_GEOMETRY},
+                          {512, 256, RD_TILE_STAGE_GEOMETRY}};
+    const int c64[][3] = {{128, 64, 0}, {256, 64, 0}, {256, 128, 0}};
+    const int nc = s->pi == 0 ? 3 : 7;
+    int best_tt = 0, best_bt = 0, best_fl = 0;
     float best_tiled = untiled;
     for (int k = 0; k < nc && rc == RD_OK; ++k) {
-      const int tt = s->pi == 0 ? c64[k][0] : c32[k][0], bt = s->pi == 0 ? c64[k][1] : c32[k][1];
-      int r = rd_state_set_tiling(s, tt, bt);
-      if (r == RD_ENOTSUP) break;  // this mesh has no tile plan
+      const int* c = s->pi == 0 ? c64[k] : c32[k];
+      int r = rd_state_set_tiling_ex(s, c[0], c[1], c[2]);
+      if (r == RD_ENOTSUP) continue;  // no tile plan for this mesh, or not enough shared memory
       if ((rc = r) != RD_OK || (rc = time_step(best_t, best_v, ms)) != RD_OK) break;
-      if (ms < best_tiled) { best_tiled = ms; best_tt = tt; best_bt = bt; }
+      if (ms < best_tiled) { best_tiled = ms; best_tt = c[0]; best_bt = c[1]; best_fl = c[2]; }
     }
     if (best_tt && !(best_tiled < 0.98f * untiled)) {  // keep the untiled step unless tiling wins clearly
       best_tt = 0;
       best_bt = 0;
+      best_fl = 0;
     }
-    if (rc == RD_OK) rc = rd_state_set_tiling(s, best_tt, best_bt);
+    if (rc == RD_OK) rc = rd_state_set_tiling_ex(s, best_tt, best_bt, best_fl);
   }
   for (auto& e : ev) cudaEventDestroy(e);
   if (s->g2) {  // the captured graph holds the old launch shapes

@@ -54,6 +54,7 @@ void launch_gather_cfl(int vblock, cudaStream_t st, int nv, const int* ptr, cons
 // gathered on chip; the others (boundary vertices) through global memory.
 struct TilePlan {
   int tt = 0, bt = 0;     // triangles per tile, threads per block
+  bool gs = false;        // stage each tile's geometry in shared memory (RD_TILE_STAGE_GEOMETRY)
   int n_tiles = 0, n_bvert = 0;
   int slots = 0;          // max over tiles of owned + halo vertices
   DevBuf vs;              // [n_tiles + 1] int32 vertex range of each tile

@@ -55,7 +55,7 @@ struct TileView {
 
 // Shared-memory layout (bytes): shares [tt][12], CFL terms [tt] (stage 1),
 // then per slot the staged vertex records.
-inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 template <class T>
 __host__ __device__ inline size_t cfl_off(int tt) { return (size_t)12 * tt * sizeof(T); }
 template <class T>
@@ -64,6 +64,65 @@ template <class T>
 size_t smem_stage1(int tt, int slots) { return slot_off<T>(tt) + align16((size_t)4 * slots * sizeof(T)) + align16((size_t)slots * sizeof(T)); }
 template <class T>
 size_t smem_stage2(int tt, int slots) { return cfl_off<T>(tt) + 3 * align16((size_t)4 * slots * sizeof(T)); }
+template <class T>
+__host__ __device__ inline size_t smem_stage1_base(int tt, int slots) {
+  return slot_off<T>(tt) + align16((size_t)4 * slots * sizeof(T)) + align16((size_t)slots * sizeof(T));
+}
+template <class T>
+__host__ __device__ inline size_t smem_stage2_base(int tt, int slots) {
+  return cfl_off<T>(tt) + 3 * align16((size_t)4 * slots * sizeof(T));
+}
+// Geometry block of a tile staged in shared memory (plans with RD_TILE_STAGE_GEOMETRY):
+// nx, ny, hl [3][tt], area [tt], l_max [tt] in T, corner slots [3][tt] uint16,
+// boundary masks [tt] uint8.
+template <class T>
+__host__ __device__ inline size_t geo_bytes(int tt) {
+  return (((size_t)11 * tt * sizeof(T) + 15) & ~(size_t)15) + (((size_t)6 * tt + 15) & ~(size_t)15) +
+         (((size_t)tt + 15) & ~(size_t)15);
+}
+
+// Shared-memory view of a tile's staged geometry.
+template <class T>
+struct TileGeo {
+  T* g;          // [11][tt]: nx0..2, ny0..2, hl0..2, area, l_max
+  uint16_t* sl;  // [3][tt]
+  uint8_t* bm;   // [tt]
+  __device__ static TileGeo at(unsigned char* base, int tt) {
+    TileGeo q;
+    q.g = reinterpret_cast<T*>(base);
+    q.sl = reinterpret_cast<uint16_t*>(base + (((size_t)11 * tt * sizeof(T) + 15) & ~(size_t)15));
+    q.bm = reinterpret_cast<uint8_t*>(reinterpret_cast<unsigned char*>(q.sl) + (((size_t)6 * tt + 15) & ~(size_t)15));
+    return q;
+  }
+};
+
+// Copy the geometry of triangles [t0, t0 + n) of a tile into shared memory
+// (every thread of the block; coalesced loads, many in flight per thread).
+template <class T>
+__device__ __forceinline__ void stage_geometry(const TileView& P, const DevGeo<T>& g, int t0, int n, int tt,
+                                               TileGeo<T> q) {
+  const int nt = P.nt;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const int t = t0 + j;
+    T v[11];
+    uint16_t sl[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      v[c] = __ldg(g.nx + (size_t)c * nt + t);
+      v[3 + c] = __ldg(g.ny + (size_t)c * nt + t);
+      v[6 + c] = __ldg(g.hl + (size_t)c * nt + t);
+      sl[c] = __ldg(P.lslot + (size_t)c * nt + t);
+    }
+    v[9] = __ldg(g.area + t);
+    v[10] = __ldg(g.lmax + t);
+    const uint8_t bm = __ldg(P.bmask + t);
+#pragma unroll
+    for (int k = 0; k < 11; ++k) q.g[k * tt + j] = v[k];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) q.sl[c * tt + j] = sl[c];
+    q.bm[j] = bm;
+  }
+}
 
 __device__ __forceinline__ void sld4(const float* p, float o[4]) {
   float4 a = *reinterpret_cast<const float4*>(p);
@@ -84,6 +143,18 @@ __device__ __forceinline__ bool block_stopped(const DevCtl* ctl) {
 }
 
 template <class T>
+__device__ __forceinline__ void tile_geo_of(const TileGeo<T>& q, int lt, int tt, int sl[3], T nx[3], T ny[3],
+                                            T hl[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    sl[c] = q.sl[c * tt + lt];
+    nx[c] = q.g[c * tt + lt];
+    ny[c] = q.g[(3 + c) * tt + lt];
+    hl[c] = q.g[(6 + c) * tt + lt];
+  }
+}
+
+template <class T>
 __device__ __forceinline__ void load_geo(int t, int nt, const DevGeo<T>& g, const uint16_t* __restrict__ lslot,
                                          int sl[3], T nx[3], T ny[3], T hl[3]) {
 #pragma unroll
@@ -95,7 +166,7 @@ __device__ __forceinline__ void load_geo(int t, int nt, const DevGeo<T>& g, cons
   }
 }
 
-template <class T, int SCHEME>
+template <class T, int SCHEME, bool GS>
 __global__ void __launch_bounds__(TILE_MAX_THREADS, (TriOcc<T, 1>::value))
     k_tile_stage1(TileView P, DevGeo<T> g, const T* __restrict__ Z, const T* __restrict__ spd, Gas<T> gas, T eps,
                   T* __restrict__ share, T* __restrict__ rec, T* __restrict__ cfl, const T* __restrict__ V,
@@ -109,6 +180,8 @@ __global__ void __launch_bounds__(TILE_MAX_THREADS, (TriOcc<T, 1>::value))
   T* scf = reinterpret_cast<T*>(smem + cfl_off<T>(P.tt));
   T* sZ = reinterpret_cast<T*>(smem + slot_off<T>(P.tt));
   T* sS = sZ + 4 * (size_t)P.slots;
+  const TileGeo<T> sg = TileGeo<T>::at(smem + smem_stage1_base<T>(P.tt, P.slots), P.tt);
+  if (GS) stage_geometry(P, g, t0, n, P.tt, sg);
   for (int s = threadIdx.x; s < nsl; s += blockDim.x) {
     const int v = s < nown ? v0 + s : __ldg(P.hlist + h0 + s - nown);
     T z[4];
@@ -122,7 +195,10 @@ __global__ void __launch_bounds__(TILE_MAX_THREADS, (TriOcc<T, 1>::value))
     const int t = t0 + lt;
     int sl[3];
     T nx[3], ny[3], hl[3], Zc[3][4];
-    load_geo(t, nt, g, P.lslot, sl, nx, ny, hl);
+    if (GS)
+      tile_geo_of(sg, lt, P.tt, sl, nx, ny, hl);
+    else
+      load_geo(t, nt, g, P.lslot, sl, nx, ny, hl);
 #pragma unroll
     for (int c = 0; c < 3; ++c) sld4(sZ + 4 * sl[c], Zc[c]);
     T lam;
@@ -131,11 +207,11 @@ __global__ void __launch_bounds__(TILE_MAX_THREADS, (TriOcc<T, 1>::value))
       lam = mag_less(s1, s0) ? s0 : s1;  // speeds are >= 0
       lam = mag_less(s2, lam) ? lam : s2;
     }
-    const T cf = __ldg(g.lmax + t) * lam;
+    const T cf = (GS ? sg.g[10 * P.tt + lt] : __ldg(g.lmax + t)) * lam;
     T out[3][4], r[16];
     T thx = T(0);
     if (SCHEME == RD_BMAX2 && mode == BLEND_X)
-      thx = bx_theta(Zc, nx, ny, hl, __ldg(g.area + t), ba.L, vrange_of<T>(ba.vr));
+      thx = bx_theta(Zc, nx, ny, hl, GS ? sg.g[9 * P.tt + lt] : __ldg(g.area + t), ba.L, vrange_of<T>(ba.vr));
     const int st = stage1_body<T, SCHEME>(Zc, nx, ny, hl, gas, eps, out, r, mode, thx);
     if (st) {
       atomicOr(&ctl->status, st);
@@ -151,7 +227,7 @@ __global__ void __launch_bounds__(TILE_MAX_THREADS, (TriOcc<T, 1>::value))
 #pragma unroll
     for (int i = 0; i < 3; ++i) st4(sh + 12 * lt + 4 * i, out[i]);
     scf[lt] = cf;
-    const unsigned bm = __ldg(P.bmask + t);
+    const unsigned bm = GS ? (unsigned)sg.bm[lt] : (unsigned)__ldg(P.bmask + t);
     if (bm) {
       cfl[t] = cf;
 #pragma unroll
@@ -204,7 +280,7 @@ __global__ void __launch_bounds__(TILE_BND_BLOCK) k_tile_bnd1(TileView P, const 
   dt_finish(ratio, partial, P.n_tiles + blockIdx.x, P.n_tiles + gridDim.x, cflnum, ctl);
 }
 
-template <class T, int SCHEME>
+template <class T, int SCHEME, bool GS>
 __global__ void __launch_bounds__(TILE_MAX_THREADS, (TriOcc<T, 2>::value))
     k_tile_stage2(TileView P, DevGeo<T> g, const T* __restrict__ Wn, const T* __restrict__ R1,
                   const T* __restrict__ V, const T* __restrict__ rec, Gas<T> gas, T gamma, T eps,
@@ -220,6 +296,8 @@ __global__ void __launch_bounds__(TILE_MAX_THREADS, (TriOcc<T, 2>::value))
   T* sWn = reinterpret_cast<T*>(smem + cfl_off<T>(P.tt));
   T* sWs = sWn + 4 * (size_t)P.slots;
   T* sZs = sWs + 4 * (size_t)P.slots;
+  const TileGeo<T> sg = TileGeo<T>::at(smem + smem_stage2_base<T>(P.tt, P.slots), P.tt);
+  if (GS) stage_geometry(P, g, t0, n, P.tt, sg);
   // W* = W^n - dt/V R1 and Z(W*) of the tile's owned and halo vertices
   for (int s = threadIdx.x; s < nsl; s += blockDim.x) {
     const int v = s < nown ? v0 + s : __ldg(P.hlist + h0 + s - nown);
@@ -244,7 +322,10 @@ __global__ void __launch_bounds__(TILE_MAX_THREADS, (TriOcc<T, 2>::value))
     const int t = t0 + lt;
     int sl[3];
     T nx[3], ny[3], hl[3], Zc[3][4], wn[3][4], ws[3][4], r[16];
-    load_geo(t, nt, g, P.lslot, sl, nx, ny, hl);
+    if (GS)
+      tile_geo_of(sg, lt, P.tt, sl, nx, ny, hl);
+    else
+      load_geo(t, nt, g, P.lslot, sl, nx, ny, hl);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       sld4(sZs + 4 * sl[c], Zc[c]);
@@ -255,7 +336,7 @@ __global__ void __launch_bounds__(TILE_MAX_THREADS, (TriOcc<T, 2>::value))
 #pragma unroll
     for (int k = 0; k < 4; ++k) ld4(rp + 4 * k, r + 4 * k);
     T out[3][4];
-    const T area = __ldg(g.area + t);
+    const T area = GS ? sg.g[9 * P.tt + lt] : __ldg(g.area + t);
     const int st = stage2_body<T, SCHEME>(Zc, wn, ws, r, nx, ny, hl, area, dt, gas, eps, out, mode, T(0), slump);
     if (st) {
       atomicOr(&ctl->status, st);
@@ -266,7 +347,7 @@ __global__ void __launch_bounds__(TILE_MAX_THREADS, (TriOcc<T, 2>::value))
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) st4(sh + 12 * lt + 4 * i, out[i]);
-    const unsigned bm = __ldg(P.bmask + t);
+    const unsigned bm = GS ? (unsigned)sg.bm[lt] : (unsigned)__ldg(P.bmask + t);
     if (bm) {
 #pragma unroll
       for (int i = 0; i < 3; ++i)
@@ -366,6 +447,18 @@ DevGeo<T> geo_view(const rd_mesh* m) {
   return g;
 }
 
+template <class T, bool GS>
+int smem_attrs_gs(size_t b1, size_t b2) {
+  CU(cudaFuncSetAttribute(k_tile_stage1<T, RD_N1, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1));
+  CU(cudaFuncSetAttribute(k_tile_stage1<T, RD_LDA2, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1));
+  CU(cudaFuncSetAttribute(k_tile_stage1<T, RD_B2, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1));
+  CU(cudaFuncSetAttribute(k_tile_stage1<T, RD_BMAX2, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1));
+  CU(cudaFuncSetAttribute(k_tile_stage2<T, RD_LDA2, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b2));
+  CU(cudaFuncSetAttribute(k_tile_stage2<T, RD_B2, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b2));
+  CU(cudaFuncSetAttribute(k_tile_stage2<T, RD_BMAX2, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b2));
+  return RD_OK;
+}
+
 // Opt every instantiation of a precision into the dynamic shared memory it
 // needs (above the 48 KB default).  The limits only grow, so that the plans of
 // other states stay launchable.
@@ -374,13 +467,8 @@ int tile_smem_attrs(size_t b1, size_t b2) {
   static size_t lim1 = 0, lim2 = 0;
   b1 = std::max(b1, lim1);
   b2 = std::max(b2, lim2);
-  CU(cudaFuncSetAttribute(k_tile_stage1<T, RD_N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1));
-  CU(cudaFuncSetAttribute(k_tile_stage1<T, RD_LDA2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1));
-  CU(cudaFuncSetAttribute(k_tile_stage1<T, RD_B2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1));
-  CU(cudaFuncSetAttribute(k_tile_stage1<T, RD_BMAX2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1));
-  CU(cudaFuncSetAttribute(k_tile_stage2<T, RD_LDA2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b2));
-  CU(cudaFuncSetAttribute(k_tile_stage2<T, RD_B2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b2));
-  CU(cudaFuncSetAttribute(k_tile_stage2<T, RD_BMAX2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b2));
+  CK((smem_attrs_gs<T, false>(b1, b2)));
+  CK((smem_attrs_gs<T, true>(b1, b2)));
   lim1 = b1;
   lim2 = b2;
   return RD_OK;
@@ -461,13 +549,54 @@ void tile_plan_free(TilePlan* tp) {
   delete tp;
 }
 
-size_t tile_smem_bytes(int precision, int stage, int tt, int slots) {
-  if (precision == RD_FP64) return stage == 1 ? smem_stage1<double>(tt, slots) : smem_stage2<double>(tt, slots);
-  return stage == 1 ? smem_stage1<float>(tt, slots) : smem_stage2<float>(tt, slots);
+size_t tile_smem_bytes(int precision, int stage, int tt, int slots, bool gs) {
+  if (precision == RD_FP64)
+    return (stage == 1 ? smem_stage1<double>(tt, slots) : smem_stage2<double>(tt, slots)) +
+           (gs ? geo_bytes<double>(tt) : 0);
+  return (stage == 1 ? smem_stage1<float>(tt, slots) : smem_stage2<float>(tt, slots)) + (gs ? geo_bytes<float>(tt) : 0);
 }
 
 bool tiled_stage2_applies(const rd_state* s) {
   return s->p.scheme != RD_N1 && s->p.scheme != RD_BX2 && s->m->n_wall == 0 && s->m->n_ghost == 0;
+}
+
+template <class T, bool GS>
+void launch_tile_stage1(const rd_params& pr, unsigned grid, int bt, size_t b1, cudaStream_t st, const TileView& P,
+                        const DevGeo<T>& g, const T* Za, const T* Sa, const Gas<T>& gas, T eps, T* share, T* rec, T* cf,
+                        const T* V, T* R1, T* partial, DevCtl* ctl, const BlendArgs<T>& ba) {
+  switch (pr.scheme) {
+    case RD_N1:
+      k_tile_stage1<T, RD_N1, GS><<<grid, bt, b1, st>>>(P, g, Za, Sa, gas, eps, share, rec, cf, V, R1, partial, ctl,
+                                                        ba);
+      break;
+    case RD_LDA2:
+      k_tile_stage1<T, RD_LDA2, GS><<<grid, bt, b1, st>>>(P, g, Za, Sa, gas, eps, share, rec, cf, V, R1, partial, ctl,
+                                                          ba);
+      break;
+    default:
+      if (pr.scheme == RD_B2 && pr.lumping == RD_LUMP_GLOBAL)
+        k_tile_stage1<T, RD_B2, GS><<<grid, bt, b1, st>>>(P, g, Za, Sa, gas, eps, share, rec, cf, V, R1, partial, ctl,
+                                                          ba);
+      else
+        k_tile_stage1<T, RD_BMAX2, GS><<<grid, bt, b1, st>>>(P, g, Za, Sa, gas, eps, share, rec, cf, V, R1, partial,
+                                                             ctl, ba);
+      break;
+  }
+}
+
+template <class T, bool GS>
+void launch_tile_stage2(const rd_params& pr, unsigned grid, int bt, size_t b2, cudaStream_t st, const TileView& P,
+                        const DevGeo<T>& g, const T* Wa, const T* R1, const T* V, const T* rec, const Gas<T>& gas,
+                        T gamma, T eps, T* share, T* Wb, T* Zb, T* Sb, DevCtl* ctl, const BlendArgs<T>& ba) {
+  if (pr.scheme == RD_LDA2)
+    k_tile_stage2<T, RD_LDA2, GS><<<grid, bt, b2, st>>>(P, g, Wa, R1, V, rec, gas, gamma, eps, share, Wb, Zb, Sb, ctl,
+                                                        ba);
+  else if (pr.scheme == RD_B2 && pr.lumping == RD_LUMP_GLOBAL)
+    k_tile_stage2<T, RD_B2, GS><<<grid, bt, b2, st>>>(P, g, Wa, R1, V, rec, gas, gamma, eps, share, Wb, Zb, Sb, ctl,
+                                                      ba);
+  else
+    k_tile_stage2<T, RD_BMAX2, GS><<<grid, bt, b2, st>>>(P, g, Wa, R1, V, rec, gas, gamma, eps, share, Wb, Zb, Sb, ctl,
+                                                         ba);
 }
 
 template <class T>
@@ -490,24 +619,14 @@ int tiled_stage1(rd_state* s, int a, cudaEvent_t* ev) {
   const T eps = (T)s->p.eps_fix;
   BlendArgs<T> ba = tile_blend_args<T>(s);
   ba.vr = (unsigned long long*)s->vr.p;  // |v| range of W^n
-  const size_t b1 = smem_stage1<T>(tp->tt, tp->slots);
+  const size_t b1 = smem_stage1<T>(tp->tt, tp->slots) + (tp->gs ? geo_bytes<T>(tp->tt) : 0);
   const unsigned grid = (unsigned)tp->n_tiles;
   const int bt = tp->bt;
-  switch (s->p.scheme) {
-    case RD_N1:
-      k_tile_stage1<T, RD_N1><<<grid, bt, b1, st>>>(P, g, Za, Sa, gas, eps, share, rec, cf, V, R1, partial, ctl, ba);
-      break;
-    case RD_LDA2:
-      k_tile_stage1<T, RD_LDA2><<<grid, bt, b1, st>>>(P, g, Za, Sa, gas, eps, share, rec, cf, V, R1, partial, ctl, ba);
-      break;
-    default:
-      if (s->p.scheme == RD_B2 && s->p.lumping == RD_LUMP_GLOBAL)
-        k_tile_stage1<T, RD_B2><<<grid, bt, b1, st>>>(P, g, Za, Sa, gas, eps, share, rec, cf, V, R1, partial, ctl, ba);
-      else
-        k_tile_stage1<T, RD_BMAX2><<<grid, bt, b1, st>>>(P, g, Za, Sa, gas, eps, share, rec, cf, V, R1, partial, ctl,
-                                                         ba);
-      break;
-  }
+  if (tp->gs)
+    launch_tile_stage1<T, true>(s->p, grid, bt, b1, st, P, g, Za, Sa, gas, eps, share, rec, cf, V, R1, partial, ctl, ba);
+  else
+    launch_tile_stage1<T, false>(s->p, grid, bt, b1, st, P, g, Za, Sa, gas, eps, share, rec, cf, V, R1, partial, ctl,
+                                 ba);
   if (ev) cudaEventRecord(ev[1], st);
   const unsigned gb = tp->n_bvert > 0 ? nblk(tp->n_bvert, TILE_BND_BLOCK) : 1u;
   k_tile_bnd1<T><<<gb, TILE_BND_BLOCK, 0, st>>>(P, share, cf, V, R1, partial, (T)s->p.cfl, ctl);
@@ -531,20 +650,19 @@ int tiled_stage2(rd_state* s, int a, cudaEvent_t* ev) {
   const T gamma = (T)s->p.gamma, eps = (T)s->p.eps_fix;
   const Gas<T> gas = Gas<T>::of(gamma);
   const BlendArgs<T> ba = tile_blend_args<T>(s);
-  const size_t b2 = smem_stage2<T>(tp->tt, tp->slots);
+  const size_t b2 = smem_stage2<T>(tp->tt, tp->slots) + (tp->gs ? geo_bytes<T>(tp->tt) : 0);
   const unsigned grid = (unsigned)tp->n_tiles;
   const int bt = tp->bt;
   T* Wb = (T*)s->W[b].p;
   T* Zb = (T*)s->Z[b].p;
   T* Sb = (T*)s->spd[b].p;
   const T* rec = (const T*)s->rec.p;
-  if (s->p.scheme == RD_LDA2)
-    k_tile_stage2<T, RD_LDA2><<<grid, bt, b2, st>>>(P, g, Wa, R1, V, rec, gas, gamma, eps, share, Wb, Zb, Sb, ctl, ba);
-  else if (s->p.scheme == RD_B2 && s->p.lumping == RD_LUMP_GLOBAL)
-    k_tile_stage2<T, RD_B2><<<grid, bt, b2, st>>>(P, g, Wa, R1, V, rec, gas, gamma, eps, share, Wb, Zb, Sb, ctl, ba);
+  if (tp->gs)
+    launch_tile_stage2<T, true>(s->p, grid, bt, b2, st, P, g, Wa, R1, V, rec, gas, gamma, eps, share, Wb, Zb, Sb, ctl,
+                                ba);
   else
-    k_tile_stage2<T, RD_BMAX2><<<grid, bt, b2, st>>>(P, g, Wa, R1, V, rec, gas, gamma, eps, share, Wb, Zb, Sb, ctl,
-                                                     ba);
+    launch_tile_stage2<T, false>(s->p, grid, bt, b2, st, P, g, Wa, R1, V, rec, gas, gamma, eps, share, Wb, Zb, Sb, ctl,
+                                 ba);
   if (ev) cudaEventRecord(ev[4], st);
   if (tp->n_bvert > 0)
     k_tile_bnd2<T><<<nblk(tp->n_bvert, TILE_BND_BLOCK), TILE_BND_BLOCK, 0, st>>>(P, share, Wa, R1, V, gamma, Wb, Zb,
@@ -559,12 +677,13 @@ template int tiled_stage2<double>(rd_state*, int, cudaEvent_t*);
 template int tiled_stage2<float>(rd_state*, int, cudaEvent_t*);
 
 // Upload a host plan into a fresh device plan of state s (bt threads per block).
-int tile_plan_upload(rd_state* s, const TilePlanHost& hp, int bt, TilePlan** out) {
+int tile_plan_upload(rd_state* s, const TilePlanHost& hp, int bt, bool gs, TilePlan** out) {
   cudaStream_t st = s->m->stream;
   TilePlan* tp = new (std::nothrow) TilePlan();
   if (!tp) return RD_ENOMEM;
   tp->tt = hp.tt;
   tp->bt = bt;
+  tp->gs = gs;
   tp->n_tiles = hp.n_tiles;
   tp->n_bvert = hp.n_bvert;
   tp->slots = hp.slots;
@@ -583,8 +702,8 @@ int tile_plan_upload(rd_state* s, const TilePlanHost& hp, int bt, TilePlan** out
   const size_t nbb = hp.n_bvert > 0 ? nblk(hp.n_bvert, TILE_BND_BLOCK) : 1u;
   if (rc == RD_OK) rc = dev_alloc(tp->partial, ((size_t)hp.n_tiles + nbb) * sizeof(double), st);
   if (rc == RD_OK) {
-    const size_t b1 = tile_smem_bytes(s->p.precision, 1, hp.tt, hp.slots);
-    const size_t b2 = tile_smem_bytes(s->p.precision, 2, hp.tt, hp.slots);
+    const size_t b1 = tile_smem_bytes(s->p.precision, 1, hp.tt, hp.slots, gs);
+    const size_t b2 = tile_smem_bytes(s->p.precision, 2, hp.tt, hp.slots, gs);
     rc = s->pi == 0 ? tile_smem_attrs<double>(b1, b2) : tile_smem_attrs<float>(b1, b2);
   }
   if (rc == RD_OK && cudaStreamSynchronize(st) != cudaSuccess) {
@@ -607,7 +726,13 @@ int tile_plan_upload(rd_state* s, const TilePlanHost& hp, int bt, TilePlan** out
 using namespace rd;
 
 extern "C" int rd_state_set_tiling(rd_state* s, int32_t tile_triangles, int32_t threads) {
+  return rd_state_set_tiling_ex(s, tile_triangles, threads, 0);
+}
+
+extern "C" int rd_state_set_tiling_ex(rd_state* s, int32_t tile_triangles, int32_t threads, int32_t flags) {
   if (!s) return RD_EINVAL;
+  if (flags & ~RD_TILE_STAGE_GEOMETRY) return RD_EINVAL;
+  const bool gs = (flags & RD_TILE_STAGE_GEOMETRY) != 0;
   if (tile_triangles == 0) {
     if (s->tiles) {
       cudaStreamSynchronize(s->m->stream);
@@ -623,11 +748,11 @@ extern "C" int rd_state_set_tiling(rd_state* s, int32_t tile_triangles, int32_t 
     int dev = 0, optin = 0;
     CU(cudaGetDevice(&dev));
     CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const size_t need = std::max(tile_smem_bytes(s->p.precision, 1, hp.tt, hp.slots),
-                                 tile_smem_bytes(s->p.precision, 2, hp.tt, hp.slots)) + 1024;
+    const size_t need = std::max(tile_smem_bytes(s->p.precision, 1, hp.tt, hp.slots, gs),
+                                 tile_smem_bytes(s->p.precision, 2, hp.tt, hp.slots, gs)) + 1024;
     if (need > (size_t)optin) return RD_ENOTSUP;
     TilePlan* tp = nullptr;
-    CK(tile_plan_upload(s, hp, threads, &tp));
+    CK(tile_plan_upload(s, hp, threads, gs, &tp));
     if (s->tiles) {
       cudaStreamSynchronize(s->m->stream);
       tile_plan_free(s->tiles);
@@ -648,5 +773,11 @@ extern "C" int rd_state_get_tiling(const rd_state* s, int32_t* tile_triangles, i
   if (tile_triangles) *tile_triangles = s->tiles ? s->tiles->tt : 0;
   if (threads) *threads = s->tiles ? s->tiles->bt : 0;
   if (n_boundary_vertices) *n_boundary_vertices = s->tiles ? s->tiles->n_bvert : 0;
+  return RD_OK;
+}
+
+extern "C" int rd_state_get_tiling_flags(const rd_state* s, int32_t* flags) {
+  if (!s || !flags) return RD_EINVAL;
+  *flags = (s->tiles && s->tiles->gs) ? RD_TILE_STAGE_GEOMETRY : 0;
   return RD_OK;
 }

@@ -12,9 +12,10 @@
 namespace rd {
 
 // Device copy of a plan for state s with bt threads per block.
-int tile_plan_upload(rd_state* s, const TilePlanHost& hp, int bt, TilePlan** out);
-// Dynamic shared memory of the stage-1 / stage-2 tile kernels.
-size_t tile_smem_bytes(int precision, int stage, int tt, int slots);
+int tile_plan_upload(rd_state* s, const TilePlanHost& hp, int bt, bool gs, TilePlan** out);
+// Dynamic shared memory of the stage-1 / stage-2 tile kernels (gs: with the
+// tile's geometry staged in shared memory).
+size_t tile_smem_bytes(int precision, int stage, int tt, int slots, bool gs);
 // Stage 1 + the boundary gather and dt (every scheme); ev[1] (nullable array)
 // is recorded between the two kernels.
 template <class T>

@@ -175,3 +175,21 @@ def test_tiled_nonphysical_and_autotune(rd):
     for x in (a, b):
         x.close()
     m.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("scheme", ["B2", "N1", "BMIN2", "B2_SL", "BX2"])
+@pytest.mark.parametrize("tt,bt", [(256, 128), (512, 256), (96, 64)])
+def test_staged_geometry_tiles_equal_untiled(rd, scheme, precision, tt, bt):
+    """Tiles whose geometry is staged in shared memory (RD_TILE_STAGE_GEOMETRY) give
+    the untiled step's states bitwise, on a mesh with a ragged last tile."""
+    _, binding = rd
+    mesh = inputs.periodic_grid(72, 61, Lx=1.0, Ly=61 / 72, relabel_seed=6)
+    W0 = inputs.khi_state(mesh)
+    m = binding.Mesh(mesh, reorder="morton")
+    a = binding.State(m, W0, scheme=scheme, precision=precision)
+    b = binding.State(m, W0, scheme=scheme, precision=precision)
+    b.set_tiling(tt, bt, stage_geometry=True)
+    assert b.tiling()[:2] == (tt, bt) and b.tiling_flags() == 1
+    assert a.run(15) == 15 and b.run(15) == 15
+    assert np.array_equal(a.get(), b.get())
