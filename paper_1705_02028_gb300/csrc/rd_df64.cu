@@ -144,14 +144,21 @@ __global__ void __launch_bounds__(256, OCC)
   int st;
   if (SYNC) {
     TriLin<dfloat> L;
+    dfloat S[4], lda[3][4];
     phase_sync(true);
-    st = lin_roe_split(Zb, dZ, nxd, nyd, hld, gas, eps, L);
+    st = lin_roe(Zb, dZ, nxd, nyd, hld, gas, L);
+    phase_sync(true);
+    if (!st) lin_split(nxd, nyd, hld, eps, L);
     phase_sync(true);
     if (!st) st = lin_assemble(L);
     phase_sync(true);
-    if (!st) lin_nshares(dZ, gas, L);
+    if (!st) lin_wh_sum(dZ, gas, L, S);
     phase_sync(true);
-    if (!st) stage1_shares<dfloat, SCHEME>(L, out, r, mode, to_df(thx));
+    if (!st) lin_nsolve(L, S);
+    phase_sync(true);
+    if (!st && SCHEME != RD_N1) lda_apply(L, L.phiT, lda);
+    phase_sync(true);
+    if (!st) stage1_finish<dfloat, SCHEME>(L, lda, out, r, mode, to_df(thx));
   } else {
     st = stage1_body_d<dfloat, SCHEME>(Zb, dZ, nxd, nyd, hld, gas, eps, out, r, mode, to_df(thx));
   }
@@ -221,19 +228,25 @@ __global__ void __launch_bounds__(256, OCC)
   int st;
   if (SYNC) {
     TriLin<dfloat> L;
+    dfloat S[4], lda[3][4], PhiN[3][4], PhiT[4];
+    const dfloat idt = rcp(dt);
     phase_sync(true);
-    st = lin_roe_split(Zb, dZ, nxd, nyd, hld, gas, eps, L);
+    st = lin_roe(Zb, dZ, nxd, nyd, hld, gas, L);
+    phase_sync(true);
+    if (!st) lin_split(nxd, nyd, hld, eps, L);
     phase_sync(true);
     if (!st) st = lin_assemble(L);
     phase_sync(true);
-    if (!st) lin_nshares(dZ, gas, L);
+    if (!st) lin_wh_sum(dZ, gas, L, S);
+    phase_sync(true);
+    if (!st) lin_nsolve(L, S);
     phase_sync(true);
     if (!st) {
-      const dfloat idt = rcp(dt);
-      dfloat PhiN[3][4], PhiT[4];
       stage2_totals_dw(L, dW, r, aread, idt, PhiN, PhiT);
-      stage2_shares<dfloat, SCHEME>(L, PhiN, PhiT, dW, aread, idt, out, mode, to_df(thx), sl);
+      lda_apply(L, PhiT, lda);
     }
+    phase_sync(true);
+    if (!st) stage2_finish<dfloat, SCHEME>(PhiN, PhiT, lda, dW, aread, idt, out, mode, to_df(thx), sl);
   } else {
     st = stage2_body_d<dfloat, SCHEME>(Zb, dZ, dW, r, nxd, nyd, hld, aread, dt, gas, eps, out, mode, to_df(thx),
                                        sl);

@@ -351,8 +351,8 @@ struct TriLin {
 // their 48-bit arithmetic acts on the differences (which carry the residual)
 // rather than on the full states (App. A algebra unchanged).
 template <class T>
-RD_HD int lin_roe_split(const T Zbar[4], const T Z[3][4], const T nx[3], const T ny[3], const T hl[3],
-                        const Gas<T>& gas, T eps, TriLin<T>& L) {
+RD_HD int lin_roe(const T Zbar[4], const T Z[3][4], const T nx[3], const T ny[3], const T hl[3], const Gas<T>& gas,
+                  TriLin<T>& L) {
   T* Zb = L.Zb;
 #pragma unroll
   for (int k = 0; k < 4; ++k) Zb[k] = Zbar[k];
@@ -397,6 +397,13 @@ RD_HD int lin_roe_split(const T Zbar[4], const T Z[3][4], const T nx[3], const T
     L.phiT[3] = Zb[3] * gx[1] + Zb[1] * gx[3] + Zb[3] * gy[2] + Zb[2] * gy[3];
   }
 
+  return 0;
+}
+
+// Eigen-split of the three nodes (after lin_roe).
+template <class T>
+RD_HD void lin_split(const T nx[3], const T ny[3], const T hl[3], T eps, TriLin<T>& L) {
+  const RoeState<T>& r = L.r;
   // eigen-split per node (App. A), regularised |lambda| below delta
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -438,6 +445,14 @@ RD_HD int lin_roe_split(const T Zbar[4], const T Z[3][4], const T nx[3], const T
     n.s2[1] = q2 - Yi;
   }
 
+}
+
+template <class T>
+RD_HD int lin_roe_split(const T Zbar[4], const T Z[3][4], const T nx[3], const T ny[3], const T hl[3],
+                        const Gas<T>& gas, T eps, TriLin<T>& L) {
+  const int st = lin_roe(Zbar, Z, nx, ny, hl, gas, L);
+  if (st) return st;
+  lin_split(nx, ny, hl, eps, L);
   return 0;
 }
 
@@ -490,7 +505,7 @@ RD_HD int lin_assemble(TriLin<T>& L) {
 
 // Phase 3: linearised states, N^ sum_j K_j^- W^_j and the N-scheme shares.
 template <class T>
-RD_HD void lin_nshares(const T Z[3][4], const Gas<T>& gas, TriLin<T>& L) {
+RD_HD void lin_wh_sum(const T Z[3][4], const Gas<T>& gas, TriLin<T>& L, T S[4]) {
   const RoeState<T>& r = L.r;
   const T* Zb = L.Zb;
 
@@ -498,7 +513,8 @@ RD_HD void lin_nshares(const T Z[3][4], const Gas<T>& gas, TriLin<T>& L) {
   // S = sum_j K_j^- W^_j = sum_j l3_j W^_j + e sum_j P_j + sum_j d_j Q_j
   // (P_j = s1 A + s2 B, Q_j = s2 A + hp B, A = a . W^_j, B = b_j . W^_j)
   T (*Wh)[4] = L.Wh;
-  T S[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) S[k] = T(0);
   {
     const T g = gas.g, ig = gas.ig;
     T SP = T(0), SQx = T(0), SQy = T(0), SQw = T(0);
@@ -525,6 +541,13 @@ RD_HD void lin_nshares(const T Z[3][4], const Gas<T>& gas, TriLin<T>& L) {
     S[2] += r.v * SP + SQy;
     S[3] += r.h * SP + SQw;
   }
+}
+
+// N-scheme shares from S = sum_j K_j^- W^_j (after lin_wh_sum).
+template <class T>
+RD_HD void lin_nsolve(TriLin<T>& L, const T S[4]) {
+  const RoeState<T>& r = L.r;
+  T (*Wh)[4] = L.Wh;
   // N scheme: phi_i^N = K_i^+ (W^_i - N^ sum_j K_j^- W^_j)
   T* win = L.win;
   L.lu.solve(S, win);
@@ -535,6 +558,13 @@ RD_HD void lin_nshares(const T Z[3][4], const Gas<T>& gas, TriLin<T>& L) {
     for (int k = 0; k < 4; ++k) d[k] = Wh[i][k] - win[k];
     Kpm_apply<T, true>(r, L.nd[i], d, L.phiN[i]);
   }
+}
+
+template <class T>
+RD_HD void lin_nshares(const T Z[3][4], const Gas<T>& gas, TriLin<T>& L) {
+  T S[4];
+  lin_wh_sum(Z, gas, L, S);
+  lin_nsolve(L, S);
 }
 
 // The linearisation in its three phases (the double-float kernels may place a
@@ -717,7 +747,7 @@ RD_HD int stage1_body_d(const T Zb[4], const T dZ[3][4], const T nx[3], const T 
 }
 
 template <class T, int SCHEME>
-RD_HD void stage1_shares(const TriLin<T>& L, T out[3][4], T rec[16], int bmode, T theta_x) {
+RD_HD void stage1_finish(const TriLin<T>& L, const T lda[3][4], T out[3][4], T rec[16], int bmode, T theta_x) {
   if (SCHEME == RD_N1) {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -725,8 +755,6 @@ RD_HD void stage1_shares(const TriLin<T>& L, T out[3][4], T rec[16], int bmode, 
       for (int k = 0; k < 4; ++k) out[i][k] = L.phiN[i][k];
     return;
   }
-  T lda[3][4];
-  lda_apply(L, L.phiT, lda);
   if (SCHEME == RD_LDA2) {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -741,7 +769,15 @@ RD_HD void stage1_shares(const TriLin<T>& L, T out[3][4], T rec[16], int bmode, 
     for (int k = 0; k < 4; ++k) rec[4 * i + k] = L.phiN[i][k];
 #pragma unroll
   for (int k = 0; k < 4; ++k) rec[12 + k] = L.phiT[k];
-  return;
+}
+
+// Stage-1 shares from a linearisation: LDA distribution of phi^T (two-stage
+// schemes), then the scheme's shares and the stage-2 record.
+template <class T, int SCHEME>
+RD_HD void stage1_shares(const TriLin<T>& L, T out[3][4], T rec[16], int bmode, T theta_x) {
+  T lda[3][4];
+  if (SCHEME != RD_N1) lda_apply(L, L.phiT, lda);
+  stage1_finish<T, SCHEME>(L, lda, out, rec, bmode, theta_x);
 }
 
 // Stage 2 (Sec. 3.4): total residuals at (W^n, W*).
@@ -831,10 +867,8 @@ RD_HD int stage2_body_d(const T Zbs[4], const T dZs[3][4], const T dW[3][4], con
 }
 
 template <class T, int SCHEME>
-RD_HD void stage2_shares(const TriLin<T>& L, const T PhiN[3][4], const T PhiT[4], const T dW[3][4], T area, T idt,
+RD_HD void stage2_finish(const T PhiN[3][4], const T PhiT[4], const T lda[3][4], const T dW[3][4], T area, T idt,
                          T out[3][4], int bmode, T theta_x, int sl) {
-  T lda[3][4];
-  lda_apply(L, PhiT, lda);
   if (SCHEME == RD_LDA2) {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -856,6 +890,14 @@ RD_HD void stage2_shares(const TriLin<T>& L, const T PhiN[3][4], const T PhiT[4]
       out[2][k] += q * d2 - sum;
     }
   }
+}
+
+template <class T, int SCHEME>
+RD_HD void stage2_shares(const TriLin<T>& L, const T PhiN[3][4], const T PhiT[4], const T dW[3][4], T area, T idt,
+                         T out[3][4], int bmode, T theta_x, int sl) {
+  T lda[3][4];
+  lda_apply(L, PhiT, lda);
+  stage2_finish<T, SCHEME>(PhiN, PhiT, lda, dW, area, idt, out, bmode, theta_x, sl);
 }
 
 template <class T, int SCHEME>
