@@ -670,11 +670,12 @@ extern "C" int rd_state_autotune(rd_state* s, int32_t* tri_block, int32_t* vtx_b
     rc = rd_state_set_tiling(s, 0, 0);
     if (rc == RD_OK) rc = time_step(best_t, best_v, untiled);
     // (tile triangles, threads, flags)
-    const int c32[][3] = {{256, 128, 0}, {512, 128, 0}, {512, 256, 0}, {1024, 256, 0},
-                          {256, 128, RD_TILE_STAGE_GEOMETRY}, {512, 128, RD_TILE_STAGE_GEOMETRY},
-                          {512, 256, RD_TILE_STAGE_GEOMETRY}};
+    // (Staging the tile geometry in shared memory, RD_TILE_STAGE_GEOMETRY, measured
+    // no faster at 4096^2 -- the tile kernels are issue-bound, not waiting on the
+    // geometry loads -- and is not among the candidates.)
+    const int c32[][3] = {{256, 128, 0}, {512, 128, 0}, {512, 256, 0}, {1024, 256, 0}};
     const int c64[][3] = {{128, 64, 0}, {256, 64, 0}, {256, 128, 0}};
-    const int nc = s->pi == 0 ? 3 : 7;
+    const int nc = s->pi == 0 ? 3 : 4;
     int best_tt = 0, best_bt = 0, best_fl = 0;
     float best_tiled = untiled;
     for (int k = 0; k < nc && rc == RD_OK; ++k) {
