@@ -53,6 +53,9 @@ WORKLOADS = {
 # xy read and R2 written in the second; W^n, R1, R2, V read and W^{n+1}
 # written in the last: 44 words per vertex and 2 x 12 B of connectivity per
 # triangle, N_v = N_t / 2 -> 22 s + 24 bytes (s = word size).
+# arithmetic type of each precision mode: df64 keeps the state, the gathers and
+# the updates in FP64 and runs the per-triangle algebra in double-float
+DTYPES = {"fp64": "f64", "fp32": "f32", "df64": "f64 state; f32x2 double-float triangle algebra"}
 ALG_BYTES_STEP = {("B2", 8): 200.0, ("B2", 4): 112.0, ("N1", 8): 112.0, ("N1", 4): 62.0}
 
 
@@ -111,7 +114,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="khi4096_B2")
-    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "df64"], default="fp64",
+                    help="df64: FP64 state, per-triangle algebra in double-float (FP32 pairs)")
     ap.add_argument("--scheme", default=None,
                     choices=["N1", "B2", "LDA2", "BMAX2", "BMIN2", "BX2", "B2_SL", "LDA2_SL", "BMAX2_SL",
                              "BMIN2_SL", "BX2_SL"],
@@ -310,7 +314,7 @@ def ours_batched(args, ws, rank, local):
     bt = batched(args, ws, args.steps)
     line = {"metric": METRIC, "value": bt["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": bt["ms_per_step"], "higher_is_better": True, "scaling": "strong",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+            "vs_baseline": None, "dtype": DTYPES[args.precision],
             "data": "synthetic (64 seeded periodic meshes, vortex / shear states; whole meshes split across ranks)",
             "config": {"workload": "batch64_B2", "meshes": bt["meshes"], "triangles": bt["triangles"],
                        "scheme": "B2", "cfl": 0.8, "precision": args.precision,
@@ -335,7 +339,7 @@ def ours(args, ws, rank, local):
         scheme = args.scheme
     nt, nv = mesh.nt, mesh.nv
     m = binding.Mesh(mesh, reorder=args.reorder)
-    s_bytes = 8 if args.precision == "fp64" else 4
+    s_bytes = 4 if args.precision == "fp32" else 8
 
     clocks = ClockSampler(local)
     s, ms_total, per_kernel, launches = run_state_timing(binding, m, W0, scheme, args.precision,
@@ -360,7 +364,7 @@ def ours(args, ws, rank, local):
     dom = max(per_kernel, key=per_kernel.get)
     dom_ms = per_kernel[dom]
     stage = 1 if dom in ("tri_stage1", "tile_stage1") else 2
-    if args.precision == "fp64" and dom in ("tri_stage1", "tri_stage2", "tile_stage1", "tile_stage2"):
+    if args.precision in ("fp64", "df64") and dom in ("tri_stage1", "tri_stage2", "tile_stage1", "tile_stage2"):
         fl = binding.count_flops(flop_scheme(scheme), stage)["total"]
         peak = binding.probe_fma_peak("fp64")
         achieved = fl * nt / (dom_ms * 1e-3)
@@ -420,7 +424,7 @@ def ours(args, ws, rank, local):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+            "vs_baseline": None, "dtype": DTYPES[args.precision],
             "data": "synthetic (seeded KHI shear layer / generated periodic triangulation)",
             "config": {"workload": args.workload, "triangles": nt, "vertices": nv, "scheme": scheme,
                        "cfl": 0.8, "precision": args.precision, "reorder": args.reorder,
@@ -525,7 +529,7 @@ def ours_partitioned(args, ws, rank, local):
     nt = mesh.nt
     line = {"metric": METRIC, "value": nt / (ms_step * 1e-3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "df64": "f64/df32x2"}[args.precision],
+            "vs_baseline": None, "dtype": DTYPES[args.precision],
             "data": "synthetic (seeded KHI shear layer / generated periodic triangulation)",
             "config": {"workload": args.workload, "triangles": nt, "vertices": mesh.nv, "scheme": scheme,
                        "cfl": 0.8, "precision": args.precision, "reorder": args.reorder,
