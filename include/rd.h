@@ -75,8 +75,8 @@ extern "C" {
  * formed in FP64 first, so the double-float arithmetic acts on the
  * differences that carry the residual.  Same arrays, arguments and results
  * as RD_FP64 to within round-off.  The untiled per-triangle step only: no
- * tiling (RD_ENOTSUP), no batched form (RD_EINVAL) and no adjoint
- * (RD_ENOTSUP). */
+ * tiling (RD_ENOTSUP) and no adjoint (RD_ENOTSUP); the batched form and the
+ * partitioned step take it. */
 #define RD_DF64 2
 
 /* ---- vertex / triangle reordering applied inside the mesh store -------- */

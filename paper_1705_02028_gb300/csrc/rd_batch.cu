@@ -14,6 +14,7 @@
 #include <new>
 #include <vector>
 
+#include "rd_df64.h"
 #include "rd_device.h"
 #include "rd_internal.h"
 #include "rd_kernels.cuh"
@@ -31,6 +32,8 @@ struct rd_batch {
   std::vector<int64_t> voff, toff;  // [n_mesh + 1]
   DevBuf tri, ptr, ent, vmesh, tmesh, geo[6];
   DevBuf W[2], Z[2], spd[2], Ws, Zs, R1, share, rec, cfl, ctl, mmin, dtm, tm, stepsm, stage;
+  DevBuf geo_df[4], dWdf;  // RD_DF64: double-float geometry, W* - W^n of every vertex
+  int df_occ = 2;          // RD_DF64 triangle-kernel variant (autotuned)
   long long launched = 0;
   int tri_block = TRI_BLOCK, vtx_block = VTX_BLOCK;
   cudaGraphExec_t graph = nullptr;
@@ -75,6 +78,29 @@ int batch_step(rd_batch* b, int a, cudaEvent_t* ev, bool commit) {
   BlendArgs<T> ba;  // Bmax / Bmin and selective lumping; Bx is not offered in batched mode
   ba.mode = b->p.scheme == RD_BMAX2 ? BLEND_MAX : b->p.scheme == RD_BMIN2 ? BLEND_MIN : BLEND_B;
   ba.sl = b->p.lumping == RD_LUMP_SELECTIVE;
+  const bool df = sizeof(T) == 8 && b->p.precision == RD_DF64;
+  TriArraysDF x;
+  if (df) {
+    x.nt = nt;
+    x.tri = tri;
+    x.g.nx = (const float2*)b->geo_df[0].p;
+    x.g.ny = (const float2*)b->geo_df[1].p;
+    x.g.hl = (const float2*)b->geo_df[2].p;
+    x.g.area = (const float2*)b->geo_df[3].p;
+    x.g.lmax = (const double*)b->geo[4].p;
+    x.share = (double*)share;
+    x.rec = rec;
+    x.cfl = (double*)cf;
+    x.ctl = ctl;
+    x.occ = b->df_occ;
+    x.dtm = dtm;
+    x.tmesh = tm;
+  }
+  if (df) {
+    x.Z = (const double*)Za;
+    x.spd = (const double*)Sa;
+    CK(launch_tri_stage1_df(b->p, x, *reinterpret_cast<const BlendArgs<double>*>(&ba), gt, TB, st));
+  } else
   switch (b->p.scheme) {
     case RD_N1:
       k_tri_stage1<T, RD_N1><<<gt, TB, 0, st>>>(nt, nv, tri, g, Za, Sa, Gas<T>::of(gamma), eps, share, nullptr, cf, ctl);
@@ -104,9 +130,14 @@ int batch_step(rd_batch* b, int a, cudaEvent_t* ev, bool commit) {
     mark(5);
   } else {
     k_update<T><<<gv, VB, 0, st>>>(nv, (const T*)b->W[a].p, (const T*)b->R1.p, ptr, ent, nullptr, V, gamma,
-                                   (T*)b->Ws.p, (T*)b->Zs.p, nullptr, ctl, dtm, vm);
+                                   (T*)b->Ws.p, (T*)b->Zs.p, nullptr, ctl, dtm, vm, nullptr, WallArgs<T>(),
+                                   GhostArgs<T>(), df ? (float2*)b->dWdf.p : nullptr);
     mark(3);
-    if (b->p.scheme == RD_LDA2)
+    if (df) {
+      x.Z = (const double*)b->Zs.p;
+      x.dw = (const float2*)b->dWdf.p;
+      CK(launch_tri_stage2_df(b->p, x, *reinterpret_cast<const BlendArgs<double>*>(&ba), gt, TB, st));
+    } else if (b->p.scheme == RD_LDA2)
       k_tri_stage2<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)b->Zs.p, (const T*)b->W[a].p,
                                                   (const T*)b->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl, dtm, tm,
                                                   ba);
@@ -158,6 +189,29 @@ int concat_geometry(rd_batch* b) {
     }
     CK(dev_alloc(b->geo[k], buf.size() * sizeof(T), b->stream));
     CU(cudaMemcpyAsync(b->geo[k].p, buf.data(), buf.size() * sizeof(T), cudaMemcpyHostToDevice, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+  }
+  return RD_OK;
+}
+
+// RD_DF64: nx, ny, hl [3][nt] and area [nt] of the concatenated meshes as
+// double-float pairs (the same split as the single-mesh store).
+int concat_geometry_df(rd_batch* b) {
+  const int64_t nt = b->nt;
+  std::vector<double> buf;
+  std::vector<float2> sp;
+  for (int k = 0; k < 4; ++k) {
+    const int comps = k < 3 ? 3 : 1;
+    buf.assign((size_t)(comps * nt), 0.0);
+    for (int32_t m = 0; m < b->n_mesh; ++m) {
+      const HostMesh& h = b->meshes[m]->h;
+      const std::vector<double>* src[4] = {&h.nx, &h.ny, &h.hl, &h.area};
+      for (int c = 0; c < comps; ++c)
+        for (int64_t i = 0; i < h.nt; ++i) buf[(size_t)(c * nt + b->toff[m] + i)] = (*src[k])[(size_t)(c * h.nt + i)];
+    }
+    split_df_host(buf, sp);
+    CK(dev_alloc(b->geo_df[k], sp.size() * sizeof(float2), b->stream));
+    CU(cudaMemcpyAsync(b->geo_df[k].p, sp.data(), sp.size() * sizeof(float2), cudaMemcpyHostToDevice, b->stream));
     CU(cudaStreamSynchronize(b->stream));
   }
   return RD_OK;
@@ -227,6 +281,7 @@ int build(rd_batch* b, const double* const* W0) {
   CK(up(b->vmesh, vm.data(), vm.size() * 2));
   CK(up(b->tmesh, tm.data(), tm.size() * 2));
   CK(b->pi == 0 ? concat_geometry<double>(b) : concat_geometry<float>(b));
+  if (b->p.precision == RD_DF64) CK(concat_geometry_df(b));
   const size_t ts = b->ts;
   for (int k = 0; k < 2; ++k) {
     CK(dev_alloc(b->W[k], 4 * nv * ts, st));
@@ -240,6 +295,7 @@ int build(rd_batch* b, const double* const* W0) {
     CK(dev_alloc(b->Ws, 4 * nv * ts, st));
     CK(dev_alloc(b->Zs, 4 * nv * ts, st));
     CK(dev_alloc(b->rec, 16 * nt * ts, st));
+    if (b->p.precision == RD_DF64) CK(dev_alloc(b->dWdf, 4 * nv * sizeof(float2), st));
   }
   CK(dev_alloc(b->ctl, sizeof(DevCtl), st));
   CK(dev_alloc(b->mmin, M * sizeof(unsigned long long), st));
@@ -308,7 +364,7 @@ extern "C" int rd_batch_create(int32_t n_mesh, rd_mesh* const* meshes, const dou
   if (p->lumping != RD_LUMP_GLOBAL && p->lumping != RD_LUMP_SELECTIVE) return RD_EINVAL;
   if ((p->lumping == RD_LUMP_SELECTIVE && p->scheme == RD_N1) || p->reserved != 0) return RD_EINVAL;
   if (p->scheme == RD_BX2) return RD_ENOTSUP;  // its |v| range is global per mesh
-  if (p->precision != RD_FP64 && p->precision != RD_FP32) return RD_EINVAL;
+  if (p->precision != RD_FP64 && p->precision != RD_FP32 && p->precision != RD_DF64) return RD_EINVAL;
   if (!(p->cfl > 0.0) || !(p->gamma > 1.0) || !(p->eps_fix >= 0.0)) return RD_EINVAL;
   for (int32_t m = 0; m < n_mesh; ++m)
     if (!meshes[m] || meshes[m]->stream != meshes[0]->stream) return RD_EINVAL;
@@ -318,7 +374,7 @@ extern "C" int rd_batch_create(int32_t n_mesh, rd_mesh* const* meshes, const dou
   if (!b) return RD_ENOMEM;
   b->n_mesh = n_mesh;
   b->p = *p;
-  b->pi = p->precision == RD_FP64 ? 0 : 1;
+  b->pi = p->precision == RD_FP32 ? 1 : 0;  // RD_DF64 keeps the FP64 state
   b->ts = b->pi == 0 ? 8 : 4;
   b->stream = meshes[0]->stream;
   b->meshes.assign(meshes, meshes + n_mesh);
@@ -402,12 +458,18 @@ extern "C" int rd_batch_autotune(rd_batch* b, int32_t* tri_block, int32_t* vtx_b
     CU(cudaEventElapsedTime(&ms, ev[0], ev[6]));
     return RD_OK;
   };
-  int best_t = TRI_BLOCK, best_v = VTX_BLOCK, rc = RD_OK;
+  int best_t = TRI_BLOCK, best_v = VTX_BLOCK, best_o = b->df_occ, rc = RD_OK;
   float best = 1e30f, ms = 0.f;
-  for (int tb : tri_c) {
-    if ((rc = time_step(tb, VTX_BLOCK, ms)) != RD_OK) break;
-    if (ms < best) { best = ms; best_t = tb; }
+  // RD_DF64: the triangle kernels without and with block barriers between phases
+  const int o0 = b->p.precision == RD_DF64 ? 2 : b->df_occ, o1 = b->p.precision == RD_DF64 ? 3 : b->df_occ;
+  for (int o = o0; o <= o1 && rc == RD_OK; ++o) {
+    b->df_occ = o;
+    for (int tb : tri_c) {
+      if ((rc = time_step(tb, VTX_BLOCK, ms)) != RD_OK) break;
+      if (ms < best) { best = ms; best_t = tb; best_o = o; }
+    }
   }
+  b->df_occ = best_o;
   best = 1e30f;
   for (int vb : vtx_c) {
     if (rc != RD_OK || (rc = time_step(best_t, vb, ms)) != RD_OK) break;
@@ -460,9 +522,10 @@ extern "C" void rd_batch_destroy(rd_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   destroy_graph(b);
   DevBuf* bufs[] = {&b->tri, &b->ptr, &b->ent, &b->vmesh, &b->tmesh, &b->Ws, &b->Zs, &b->R1, &b->share,
-                    &b->rec, &b->cfl, &b->ctl, &b->mmin, &b->dtm, &b->tm, &b->stepsm, &b->stage};
+                    &b->rec, &b->cfl, &b->ctl, &b->mmin, &b->dtm, &b->tm, &b->stepsm, &b->stage, &b->dWdf};
   for (DevBuf* d : bufs) dev_free(*d);
   for (int k = 0; k < 6; ++k) dev_free(b->geo[k]);
+  for (int k = 0; k < 4; ++k) dev_free(b->geo_df[k]);
   for (int k = 0; k < 2; ++k) {
     dev_free(b->W[k]);
     dev_free(b->Z[k]);

@@ -180,7 +180,8 @@ template <int SCHEME, int OCC, bool SYNC>
 __global__ void __launch_bounds__(256, OCC)
     k_tri_stage2_df(int nt, const int* __restrict__ tri, DevGeoDF g, const double* __restrict__ Zs,
                     const float2* __restrict__ dw, const dfloat* __restrict__ rec, Gas<dfloat> gas, dfloat eps,
-                    double* __restrict__ share, DevCtl* ctl, BlendArgs<double> ba) {
+                    double* __restrict__ share, DevCtl* ctl, BlendArgs<double> ba,
+                    const double* __restrict__ dtm, const uint16_t* __restrict__ tmesh) {
   const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (SYNC) {
     if (block_stop(ctl)) return;
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(256, OCC)
   dfloat Zb[4], dZ[3][4];
   split_nodal(Zc, Zb, dZ);
   dfloat out[3][4];
-  const dfloat dt = to_df(ctl->dt);
+  const dfloat dt = to_df(dtm ? __ldg(dtm + __ldg(tmesh + t)) : ctl->dt);  // batched form: each mesh's dt
   int st;
   if (SYNC) {
     TriLin<dfloat> L;
@@ -311,12 +312,13 @@ int stage2_df_occ(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba
   const dfloat* rec = (const dfloat*)a.rec;
   if (p.scheme == RD_LDA2)
     k_tri_stage2_df<RD_LDA2, OCC, SYNC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.dw, rec, gas, eps, a.share,
-                                                          a.ctl, ba);
+                                                                a.ctl, ba, a.dtm, a.tmesh);
   else if (p.scheme == RD_B2 && p.lumping == RD_LUMP_GLOBAL)
     k_tri_stage2_df<RD_B2, OCC, SYNC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.dw, rec, gas, eps, a.share,
-                                                        a.ctl, ba);
+                                                              a.ctl, ba, a.dtm, a.tmesh);
   else
-    k_tri_stage2_df<RD_BMAX2, OCC, SYNC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.dw, rec, gas, eps, a.share, a.ctl, ba);
+    k_tri_stage2_df<RD_BMAX2, OCC, SYNC><<<grid, block, 0, st>>>(a.nt, a.tri, a.g, a.Z, a.dw, rec, gas, eps,
+                                                                 a.share, a.ctl, ba, a.dtm, a.tmesh);
   CU(cudaGetLastError());
   return RD_OK;
 }

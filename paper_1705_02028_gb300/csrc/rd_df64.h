@@ -30,6 +30,8 @@ struct TriArraysDF {
   double* cfl = nullptr;
   DevCtl* ctl = nullptr;
   int occ = 2;  // kernel variant: 2 (128 registers), 3 (128, block barriers between phases)
+  const double* dtm = nullptr;      // batched form: per-mesh dt, indexed by tmesh[t]
+  const uint16_t* tmesh = nullptr;
 };
 int launch_tri_stage1_df(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
                          cudaStream_t st);

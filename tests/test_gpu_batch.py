@@ -158,3 +158,27 @@ def test_benchmark_batch_sampled_meshes(rd):
     b.close()
     for m in meshes:
         m.close()
+
+
+@pytest.mark.parametrize("scheme", ["B2", "N1", "LDA2"])
+def test_batch_df64_matches_plain_df64_and_oracle(rd, scheme):
+    """The batched form in RD_DF64 (FP64 state, double-float triangle algebra): every
+    mesh bitwise equal to its single-mesh RD_DF64 state (each kernel variant the
+    autotuner may pick) and within 1e-12 of the long-double oracle."""
+    torch, binding = rd
+    stream = torch.cuda.Stream()
+    cases = [make_case(N, kind, 60 + k) for k, (N, kind) in enumerate(CASES)]
+    meshes = [binding.Mesh(m, stream=stream) for m, _ in cases]
+    b = binding.Batch(meshes, [W for _, W in cases], scheme=scheme, precision="df64")
+    b.autotune()
+    steps = 20
+    b.run(steps)
+    for k, (mesh, W0) in enumerate(cases):
+        Wb = b.get(k)
+        Wo, _ = oracle.run(mesh, W0, scheme, nsteps=steps, long_double=True)
+        assert rel_max_err(Wb, Wo) < 1e-12, k
+        s = binding.State(meshes[k], W0, scheme=scheme, precision="df64")
+        s.run(steps)
+        assert np.array_equal(s.get(), Wb), k
+        s.close()
+    b.close()
