@@ -488,6 +488,12 @@ def ours(args, ws, rank, local):
     if not args.no_batched and args.workload != "batch64_B2":
         bt = batched(args, ws, args.steps)
         bt["vs_plain_step"] = bt["value"] / value
+        if "df64" in bt and "df64" in line:
+            bt["df64"]["vs_plain_step"] = bt["df64"]["value"] / line["df64"]["value"]
+        if "fp32" in bt and "fp32" in line:
+            bt["fp32"]["vs_plain_step"] = bt["fp32"]["value"] / line["fp32"]["value"]
+        if ws == 1 and args.precision == "fp64":
+            bt["small_meshes"] = batched_small(args, ws, args.steps)
         line["batched"] = bt
     if not args.no_adjoint and args.precision == "fp64":
         line["adjoint"] = adjoint_measure(args, ws)
@@ -573,22 +579,14 @@ def accuracy_leg(binding, m, W0, scheme, nt, mesh, steps=20):
     return out
 
 
-def batched(args, ws, steps):
-    """64 independent periodic meshes, sides ~ U{128..1024} (seed 2), vortex or shear state
-    (50/50), B2 FP64, each with its own dt, `steps` steps as ONE CUDA-graph launch."""
-    import torch
-
-    from paper_1705_02028_gb300 import binding, inputs
-    work_all = inputs.batch_workload(n_mesh=64, seed=2)
-    nt_all = sum(m.nt for m, _, _ in work_all)
-    rank = int(os.environ.get("RANK", "0"))
-    work = work_all[rank::ws]          # whole meshes per rank: independent units, no collective
-    stream = torch.cuda.Stream()
-    meshes = [binding.Mesh(m, stream=stream) for m, _, _ in work]
-    b = binding.Batch(meshes, [W for _, W, _ in work], scheme="B2", precision=args.precision)
+def _time_batch(binding, torch, meshes, states, scheme, precision, warmup, steps, ws, autotune=True):
+    """One batch on the given meshes: autotune, warm up, then `steps` steps as ONE
+    graph launch timed with CUDA events; per-kernel ms of two profiled steps."""
+    stream = meshes[0].stream
+    b = binding.Batch(meshes, states, scheme=scheme, precision=precision)
     nv, nt = b.sizes()
-    shapes = b.autotune() if not args.no_autotune else None
-    b.run(args.warmup)
+    shapes = b.autotune() if autotune else None
+    b.run(warmup)
     torch.cuda.synchronize()
     barrier(ws)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -600,17 +598,91 @@ def batched(args, ws, steps):
     barrier(ws)
     ms = max_over_ranks(e0.elapsed_time(e1) / steps, ws)
     pk = b.profile(2)
-    t, n = b.time()
     dts = b.dt()
     b.close()
+    return {"ms_per_step": ms, "triangles_rank0": nt, "vertices_rank0": nv, "per_kernel_ms": pk,
+            "dt_min": float(dts.min()), "dt_max": float(dts.max()),
+            "launch_shapes": {"tri_block": shapes[0], "vtx_block": shapes[1], "source": "rd_batch_autotune"}
+            if shapes else None}
+
+
+def batched(args, ws, steps):
+    """64 independent periodic meshes, sides ~ U{128..1024} (seed 2), vortex or shear state
+    (50/50), B2, each with its own dt, `steps` steps as ONE CUDA-graph launch: FP64 (the
+    line's numbers), RD_DF64 and FP32 on the same meshes."""
+    import torch
+
+    from paper_1705_02028_gb300 import binding, inputs
+    work_all = inputs.batch_workload(n_mesh=64, seed=2)
+    nt_all = sum(m.nt for m, _, _ in work_all)
+    rank = int(os.environ.get("RANK", "0"))
+    work = work_all[rank::ws]          # whole meshes per rank: independent units, no collective
+    stream = torch.cuda.Stream()
+    meshes = [binding.Mesh(m, stream=stream) for m, _, _ in work]
+    states = [W for _, W, _ in work]
+    out = {}
+    for prec in ("fp64", "df64", "fp32"):
+        if prec != "fp64" and args.precision != "fp64":
+            continue
+        r = _time_batch(binding, torch, meshes, states, "B2", prec if args.precision == "fp64" else args.precision,
+                        args.warmup, steps, ws, autotune=not args.no_autotune)
+        r["value"] = nt_all / (r["ms_per_step"] * 1e-3)
+        out[prec] = r
     for mm in meshes:
         mm.close()
-    return {"value": nt_all / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "meshes": len(work_all),
-            "meshes_per_rank": len(work), "triangles": nt_all, "triangles_rank0": nt, "vertices_rank0": nv,
-            "steps_per_graph_launch": steps,
-            "sides": [int(mm.Nx) for mm, _, _ in work], "dt_min": float(dts.min()), "dt_max": float(dts.max()),
-            "launch_shapes": {"tri_block": shapes[0], "vtx_block": shapes[1], "source": "rd_batch_autotune"}
-            if shapes else None, "per_kernel_ms": pk, "precision": args.precision}
+    main = out["fp64"]
+    line = {"value": main["value"], "unit": UNIT, "ms_per_step": main["ms_per_step"], "meshes": len(work_all),
+            "meshes_per_rank": len(work), "triangles": nt_all, "triangles_rank0": main["triangles_rank0"],
+            "vertices_rank0": main["vertices_rank0"], "steps_per_graph_launch": steps,
+            "sides": [int(mm.Nx) for mm, _, _ in work], "dt_min": main["dt_min"], "dt_max": main["dt_max"],
+            "launch_shapes": main["launch_shapes"], "per_kernel_ms": main["per_kernel_ms"],
+            "precision": args.precision}
+    if "df64" in out:
+        line["df64"] = {k: out["df64"][k] for k in ("value", "ms_per_step", "per_kernel_ms", "launch_shapes")}
+    if "fp32" in out:
+        line["fp32"] = {k: out["fp32"][k] for k in ("value", "ms_per_step", "per_kernel_ms", "launch_shapes")}
+    return line
+
+
+def batched_small(args, ws, steps, n_mesh=512, smin=32, smax=128):
+    """Many small meshes, where launch overhead matters: 512 periodic meshes of sides
+    U{32..128} (seed 5), B2 FP64.  The batched form (`steps` steps as one graph
+    launch) against the same meshes advanced one by one through their own states
+    (rd_run per mesh, each replaying its own two-step graph), and the graph's step
+    time against the sum of its kernels' times (the launch overhead left to a
+    persistent kernel)."""
+    import torch
+
+    from paper_1705_02028_gb300 import binding, inputs
+    work = inputs.batch_workload(n_mesh=n_mesh, seed=5, smin=smin, smax=smax)
+    nt_all = sum(m.nt for m, _, _ in work)
+    stream = torch.cuda.Stream()
+    meshes = [binding.Mesh(m, stream=stream) for m, _, _ in work]
+    states = [W for _, W, _ in work]
+    r = _time_batch(binding, torch, meshes, states, "B2", "fp64", args.warmup, steps, ws,
+                    autotune=not args.no_autotune)
+    kern = sum(v for k, v in r["per_kernel_ms"].items())
+    plain = [binding.State(mm, W, scheme="B2") for mm, W in zip(meshes, states)]
+    for s in plain:
+        s.run(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in plain:
+        s.run(steps)
+    torch.cuda.synchronize()
+    t_plain = (time.perf_counter() - t0) / steps
+    for s in plain:
+        s.close()
+    for mm in meshes:
+        mm.close()
+    return {"meshes": n_mesh, "sides": [smin, smax], "triangles": nt_all, "precision": "fp64",
+            "ms_per_step": r["ms_per_step"], "value": nt_all / (r["ms_per_step"] * 1e-3),
+            "sum_of_kernel_ms_per_step": kern, "graph_overhead_ms_per_step": r["ms_per_step"] - kern,
+            "per_mesh_states_ms_per_step": t_plain * 1e3,
+            "per_mesh_states_value": nt_all / t_plain,
+            "vs_per_mesh_states": (t_plain * 1e3) / r["ms_per_step"],
+            "note": "per-mesh states: rd_run(steps) on each of the 512 states in turn (host wall clock); "
+                    "graph overhead = graph-timed step minus the sum of its kernels' event-timed durations"}
 
 
 def meshgen_measure(args, R=7.3e-4):
