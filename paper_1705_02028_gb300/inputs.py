@@ -536,6 +536,51 @@ def sound_wave_state(mesh: Mesh, amp=1e-4, t=0.0, gamma=GAMMA) -> np.ndarray:
     return conserved(1.0 + d, c * d, 0.0, p0 + c * c * d, gamma)
 
 
+def blast_state(mesh: Mesh, dim: int, gamma: float = 5.0 / 3.0, rho0: float = 1.0, p0: float = 1e-6,
+                h: float | None = None) -> np.ndarray:
+    """Strong blast waves (Secs. 5.1.3 and 5.2.3): gas at rest, rho0, p0, plus a
+    Gaussian pressure pulse at the centre of the box.
+    dim = 1 (planar, about the line x = Lx / 2):
+        p1 = (gamma - 1) / (500 h sqrt(pi)) exp(-x^2 / (100 h^2)), total energy 1/50
+        per unit length of the line;
+    dim = 2 (cylindrical, about the centre point):
+        p1 = (gamma - 1) (0.004 / h)^2 exp(-(x^2 + y^2) / (6.25 h^2)), total energy
+        6.25 pi 0.004^2.
+    h is the cell size (default: the x spacing of the mesh's vertex grid, Lx / Nx)."""
+    if h is None:
+        h = mesh.Lx / mesh.Nx
+    x = mesh.xy[:, 0] - 0.5 * mesh.Lx
+    y = mesh.xy[:, 1] - 0.5 * mesh.Ly
+    if dim == 1:
+        p1 = (gamma - 1.0) / (500.0 * h * np.sqrt(np.pi)) * np.exp(-x * x / (100.0 * h * h))
+    elif dim == 2:
+        p1 = (gamma - 1.0) * (0.004 / h) ** 2 * np.exp(-(x * x + y * y) / (6.25 * h * h))
+    else:
+        raise ValueError("dim must be 1 or 2")
+    return conserved(np.full(mesh.nv, rho0), 0.0, 0.0, p0 + p1, gamma)
+
+
+# four constant states of the two-dimensional Riemann problem (Sec. 5.2.4):
+# (rho, u, v, p) in the quadrants x <= 0.8 / > 0.8 by y > 0.8 / <= 0.8
+RIEMANN2D_STATES = {
+    "UL": (0.5322581, 1.2060454, 0.0, 0.3),
+    "UR": (1.5, 0.0, 0.0, 1.5),
+    "LL": (0.1379928, 1.2060454, 1.2060454, 0.0290323),
+    "LR": (0.5322581, 0.0, 1.2060454, 0.3),
+}
+
+
+def riemann2d_state(mesh: Mesh, gamma: float = GAMMA, xc: float = 0.8, yc: float = 0.8) -> np.ndarray:
+    """Two-dimensional Riemann problem of Sec. 5.2.4 on [0, 1]^2: U1 for x <= 0.8 < y,
+    U2 for x, y > 0.8, U3 for x, y <= 0.8, U4 for y <= 0.8 < x (primitive states)."""
+    x, y = mesh.xy[:, 0], mesh.xy[:, 1]
+    q = np.empty((mesh.nv, 4))
+    top, right = y > yc, x > xc
+    for key, sel in (("UL", ~right & top), ("UR", right & top), ("LL", ~right & ~top), ("LR", right & ~top)):
+        q[sel] = RIEMANN2D_STATES[key]
+    return conserved(q[:, 0], q[:, 1], q[:, 2], q[:, 3], gamma)
+
+
 def batch_workload(n_mesh=64, seed=2, smin=128, smax=1024, relabel_seed=None):
     """64 periodic meshes with sides ~ U{smin..smax}; each gets a vortex or shear state (50/50)."""
     rng = np.random.default_rng(seed)
