@@ -289,6 +289,7 @@ def run_state_timing(binding, mesh_dev, W0, scheme, precision, steps, warmup, ws
         tt, bt = (int(x) for x in tiling.lower().rstrip("g").split("x"))
         s.set_tiling(tt, bt, stage_geometry=gs)
     s.tiles = s.tiling()
+    s.tflags = s.tiling_flags()
     s.run(warmup)
     st = mesh_dev.stream
     torch.cuda.synchronize()
@@ -434,7 +435,7 @@ def ours(args, ws, rank, local):
             "ms_per_step_graph": ms_graph, "per_kernel_ms": per_kernel,
             "launch_shapes": {"tri_block": shapes[0], "vtx_block": shapes[1], "source": "rd_state_autotune"}
             if shapes else None,
-            "tiling": tiling_info(s.tiles, s.tiling_flags()),
+            "tiling": tiling_info(s.tiles, s.tflags),
             "roofline": roof, "step_hbm": step_hbm, "e2e": e2e,
             "gpu_launches": launches * args.steps + 1,
             "clocks": clk}
@@ -450,7 +451,7 @@ def ours(args, ws, rank, local):
         a32 = b32 * nt / (pk32[d32] * 1e-3) / 1e9 if b32 else None
         sb32 = ALG_BYTES_STEP.get((alg_scheme(scheme), 4))
         line["fp32"] = {"value": ws * nt / (ms32 * 1e-3), "ms_per_step": ms32, "per_kernel_ms": pk32,
-                        "tiling": tiling_info(s32.tiles, s32.tiling_flags()),
+                        "tiling": tiling_info(s32.tiles, s32.tflags),
                         "roofline": {"bound": "hbm", "kernel": d32, "achieved": a32, "peak": hbm, "unit": "GB/s",
                                      "frac": a32 / hbm if a32 else None, "bytes_per_triangle": b32,
                                      "traffic": (ncu_traffic(args.workload, "fp32", d32, nt) or {}).get(
