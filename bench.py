@@ -498,6 +498,8 @@ def ours(args, ws, rank, local):
         line["batched"] = bt
     if not args.no_adjoint and args.precision == "fp64":
         line["adjoint"] = adjoint_measure(args, ws)
+        line["adjoint"]["large_mesh_no_stored_linearisation"] = adjoint_measure(args, ws, n_steps=40, ckpt_every=20,
+                                                                                N=2048)
     if not args.no_meshgen:
         line["meshgen"] = meshgen_measure(args)
 
@@ -705,15 +707,17 @@ def meshgen_measure(args, R=7.3e-4):
             "note": "device time of rd_meshgen_run (CUDA events around the whole run, host control loop included)"}
 
 
-def adjoint_measure(args, ws, n_steps=200, ckpt_every=20):
-    """Gradient of L = 1/2 sum V (rho - rho_tgt)^2 after a 200-step B2 FP64 rollout on the
-    512x512 periodic mesh from a smooth density perturbation (amplitude 0.05), checkpoints
-    every 20 steps, against 200 plain steps of the same state."""
+def adjoint_measure(args, ws, n_steps=200, ckpt_every=20, N=512):
+    """Gradient of L = 1/2 sum V (rho - rho_tgt)^2 after an n_steps B2 FP64 rollout on the
+    N x N periodic mesh from a smooth density perturbation (amplitude 0.05), checkpoints
+    every ckpt_every steps, against n_steps plain steps of the same state.  (At 512^2 a
+    segment's linearisations fit in a quarter of the free memory and the backward pass
+    reads them; at 2048^2 they do not, and it linearises again.)"""
     import numpy as np
     import torch
 
     from paper_1705_02028_gb300 import binding, inputs
-    mesh = inputs.periodic_grid(512)
+    mesh = inputs.periodic_grid(N)
     W0 = inputs.smooth_density_state(mesh, seed=3)
     tgt = inputs.smooth_density_state(mesh, seed=4)
     m = binding.Mesh(mesh)
@@ -734,7 +738,7 @@ def adjoint_measure(args, ws, n_steps=200, ckpt_every=20):
     t_fwd = time.perf_counter() - t0
     Wf = s.get()
     # L = 1/2 sum V (rho - rho_tgt)^2 with V = |T|/3 summed over the triangles (regular grid: h^2)
-    V = np.full(mesh.nv, (1.0 / 512) ** 2)
+    V = np.full(mesh.nv, (1.0 / N) ** 2)
     seed = np.zeros_like(Wf)
     seed[0] = V * (Wf[0] - tgt[0])
     t0 = time.perf_counter()
@@ -743,7 +747,7 @@ def adjoint_measure(args, ws, n_steps=200, ckpt_every=20):
     s.close()
     m.close()
     nt = mesh.nt
-    return {"mesh": "512x512", "triangles": nt, "steps": n_steps, "ckpt_every": ckpt_every, "scheme": "B2",
+    return {"mesh": f"{N}x{N}", "triangles": nt, "steps": n_steps, "ckpt_every": ckpt_every, "scheme": "B2",
             "precision": "fp64", "plain_s": t_plain, "forward_s": t_fwd, "backward_s": t_bwd,
             "value": nt * n_steps / (t_fwd + t_bwd), "unit": "triangle-updates/s (forward + backward)",
             "plain_value": nt * n_steps / t_plain,
