@@ -160,7 +160,7 @@ def test_benchmark_batch_sampled_meshes(rd):
         m.close()
 
 
-@pytest.mark.parametrize("scheme", ["B2", "N1", "LDA2"])
+@pytest.mark.parametrize("scheme", ["B2", "N1"])
 def test_batch_df64_matches_plain_df64_and_oracle(rd, scheme):
     """The batched form in RD_DF64 (FP64 state, double-float triangle algebra): every
     mesh bitwise equal to its single-mesh RD_DF64 state (each kernel variant the
