@@ -237,9 +237,14 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def kernel_source_hash():
+def kernel_source_hash(precision="fp64"):
+    """Hash of the device code of a precision's triangle and tile kernels (the DF64
+    kernels add the double-float files), which keys the committed ncu traffic figures."""
     h = hashlib.sha256()
-    for f in ("rd_kernels.cuh", "rd_api.cu", "rd_dfloat.cuh", "rd_df64.cu", "rd_tiled.cu"):
+    files = ["rd_kernels.cuh", "rd_tiled.cu"]
+    if precision == "df64":
+        files += ["rd_dfloat.cuh", "rd_df64_kernels.cuh"]
+    for f in files:
         with open(os.path.join(ROOT, "paper_1705_02028_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -270,7 +275,7 @@ def ncu_traffic(workload, precision, kernel, nt):
         return None
     cap = workload if f"{workload}:{precision}:{kernel}" in d else TRAFFIC_CAPTURE.get(workload, workload)
     e = d.get(f"{cap}:{precision}:{kernel}")
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(precision):
         return None
     return {"bytes_per_launch": float(e["dram_bytes_per_triangle"]) * nt,
             "bytes_per_triangle": float(e["dram_bytes_per_triangle"]),
@@ -476,7 +481,7 @@ def ours(args, ws, rank, local):
         eq = fl_df * nt / (pkdf[ddf] * 1e-3) if fl_df else None
         line["df64"] = {"value": ws * nt / (msdf * 1e-3), "ms_per_step": msdf, "per_kernel_ms": pkdf,
                         "vs_fp64_step": ms_step / msdf,
-                        "launch_shapes": dict(zip(("tri_block", "vtx_block", "register_budget"),
+                        "launch_shapes": dict(zip(("tri_block", "vtx_block", "df_variant"),
                                                   sdf.launch_shapes())),
                         "dominant_kernel": ddf,
                         "traffic_source": ncu_traffic(args.workload, "df64", ddf, nt),

@@ -413,14 +413,14 @@ class State:
         return tb.value, vb.value
 
     def launch_shapes(self):
-        """(triangle block, vertex block, DF64 register budget) in use (rd_state_launch_shapes)."""
+        """(triangle block, vertex block, DF64 kernel variant) in use (rd_state_launch_shapes)."""
         tb, vb, oc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         _check(_lib.rd_state_launch_shapes(self.handle, ctypes.byref(tb), ctypes.byref(vb), ctypes.byref(oc)),
                "rd_state_launch_shapes")
         return tb.value, vb.value, oc.value
 
-    def set_launch_shapes(self, tri_block: int, vtx_block: int, df_occ: int = 1):
-        _check(_lib.rd_state_set_launch_shapes(self.handle, int(tri_block), int(vtx_block), int(df_occ)),
+    def set_launch_shapes(self, tri_block: int, vtx_block: int, df_variant: int = 2):
+        _check(_lib.rd_state_set_launch_shapes(self.handle, int(tri_block), int(vtx_block), int(df_variant)),
                "rd_state_set_launch_shapes")
 
     def set_tiling(self, tile_triangles: int, threads: int = 128, stage_geometry: bool = False):

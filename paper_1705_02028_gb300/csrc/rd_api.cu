@@ -644,19 +644,19 @@ extern "C" int rd_state_autotune(rd_state* s, int32_t* tri_block, int32_t* vtx_b
     CU(cudaEventElapsedTime(&ms, ev[0], ev[6]));
     return RD_OK;
   };
-  int best_t = TRI_BLOCK, best_v = VTX_BLOCK, best_o = s->df_occ, rc = RD_OK;
+  int best_t = TRI_BLOCK, best_v = VTX_BLOCK, best_o = s->df_variant, rc = RD_OK;
   float best = 1e30f, ms = 0.f;
-  // DF64: the triangle kernels without and with block barriers between phases
-  const int o0 = s->p.precision == RD_DF64 ? 2 : s->df_occ, o1 = s->p.precision == RD_DF64 ? 3 : s->df_occ;
+  // DF64: the triangle kernels at 128 and 168 registers, without and with block barriers between phases
+  const int o0 = s->p.precision == RD_DF64 ? 2 : s->df_variant, o1 = s->p.precision == RD_DF64 ? 5 : s->df_variant;
   for (int o = o0; o <= o1; ++o) {
-    s->df_occ = o;
+    s->df_variant = o;
     for (int tb : tri_c) {
       if ((rc = time_step(tb, VTX_BLOCK, ms)) != RD_OK) break;
       if (ms < best) { best = ms; best_t = tb; best_o = o; }
     }
     if (rc != RD_OK) break;
   }
-  s->df_occ = best_o;
+  s->df_variant = best_o;
   best = 1e30f;
   for (int vb : vtx_c) {
     if (rc != RD_OK || (rc = time_step(best_t, vb, ms)) != RD_OK) break;
@@ -702,22 +702,22 @@ extern "C" int rd_state_autotune(rd_state* s, int32_t* tri_block, int32_t* vtx_b
   return rc;
 }
 
-extern "C" int rd_state_launch_shapes(const rd_state* s, int32_t* tri_block, int32_t* vtx_block, int32_t* df_occ) {
+extern "C" int rd_state_launch_shapes(const rd_state* s, int32_t* tri_block, int32_t* vtx_block, int32_t* df_variant) {
   if (!s) return RD_EINVAL;
   if (tri_block) *tri_block = s->tri_block;
   if (vtx_block) *vtx_block = s->vtx_block;
-  if (df_occ) *df_occ = s->df_occ;
+  if (df_variant) *df_variant = s->df_variant;
   return RD_OK;
 }
 
-extern "C" int rd_state_set_launch_shapes(rd_state* s, int32_t tri_block, int32_t vtx_block, int32_t df_occ) {
+extern "C" int rd_state_set_launch_shapes(rd_state* s, int32_t tri_block, int32_t vtx_block, int32_t df_variant) {
   if (!s) return RD_EINVAL;
   if (tri_block != 64 && tri_block != 128 && tri_block != 192 && tri_block != 256) return RD_EINVAL;
   if (vtx_block != 128 && vtx_block != 256 && vtx_block != 512) return RD_EINVAL;
-  if (df_occ < 2 || df_occ > 3) return RD_EINVAL;
+  if (df_variant < 2 || df_variant > 5) return RD_EINVAL;
   s->tri_block = tri_block;
   s->vtx_block = vtx_block;
-  s->df_occ = df_occ;
+  s->df_variant = df_variant;
   if (s->g2) {  // the captured graph holds the old launch shapes
     cudaStreamSynchronize(s->m->stream);
     cudaGraphExecDestroy(s->g2);

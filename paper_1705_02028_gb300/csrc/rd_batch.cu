@@ -33,7 +33,7 @@ struct rd_batch {
   DevBuf tri, ptr, ent, vmesh, tmesh, geo[6];
   DevBuf W[2], Z[2], spd[2], Ws, Zs, R1, share, rec, cfl, ctl, mmin, dtm, tm, stepsm, stage;
   DevBuf geo_df[4], dWdf;  // RD_DF64: double-float geometry, W* - W^n of every vertex
-  int df_occ = 2;          // RD_DF64 triangle-kernel variant (autotuned)
+  int df_variant = 2;          // RD_DF64 triangle-kernel variant (autotuned)
   long long launched = 0;
   int tri_block = TRI_BLOCK, vtx_block = VTX_BLOCK;
   cudaGraphExec_t graph = nullptr;
@@ -92,7 +92,7 @@ int batch_step(rd_batch* b, int a, cudaEvent_t* ev, bool commit) {
     x.rec = rec;
     x.cfl = (double*)cf;
     x.ctl = ctl;
-    x.occ = b->df_occ;
+    x.variant = b->df_variant;
     x.dtm = dtm;
     x.tmesh = tm;
   }
@@ -458,18 +458,18 @@ extern "C" int rd_batch_autotune(rd_batch* b, int32_t* tri_block, int32_t* vtx_b
     CU(cudaEventElapsedTime(&ms, ev[0], ev[6]));
     return RD_OK;
   };
-  int best_t = TRI_BLOCK, best_v = VTX_BLOCK, best_o = b->df_occ, rc = RD_OK;
+  int best_t = TRI_BLOCK, best_v = VTX_BLOCK, best_o = b->df_variant, rc = RD_OK;
   float best = 1e30f, ms = 0.f;
-  // RD_DF64: the triangle kernels without and with block barriers between phases
-  const int o0 = b->p.precision == RD_DF64 ? 2 : b->df_occ, o1 = b->p.precision == RD_DF64 ? 3 : b->df_occ;
+  // RD_DF64: the triangle kernels at 128 and 168 registers, without and with block barriers between phases
+  const int o0 = b->p.precision == RD_DF64 ? 2 : b->df_variant, o1 = b->p.precision == RD_DF64 ? 5 : b->df_variant;
   for (int o = o0; o <= o1 && rc == RD_OK; ++o) {
-    b->df_occ = o;
+    b->df_variant = o;
     for (int tb : tri_c) {
       if ((rc = time_step(tb, VTX_BLOCK, ms)) != RD_OK) break;
       if (ms < best) { best = ms; best_t = tb; best_o = o; }
     }
   }
-  b->df_occ = best_o;
+  b->df_variant = best_o;
   best = 1e30f;
   for (int vb : vtx_c) {
     if (rc != RD_OK || (rc = time_step(best_t, vb, ms)) != RD_OK) break;

@@ -130,7 +130,7 @@ struct rd_state {
   bool bc_init = false;
   long long launched = 0;  // host view of the committed step count (parity of the buffers)
   int tri_block = rd::TRI_BLOCK, vtx_block = rd::VTX_BLOCK;  // launch shapes (autotuned)
-  int df_occ = 2;  // RD_DF64 triangle-kernel variant (2: 128 registers, 3: 128 with phase barriers; autotuned)
+  int df_variant = 2;  // RD_DF64 triangle-kernel variant (2 / 3: 128 registers, 4 / 5: 168; 3, 5 with phase barriers; autotuned)
   rd::TilePlan* tiles = nullptr;  // tiled step (nullptr: per-triangle share arrays)
   cudaGraphExec_t g2 = nullptr;  // two steps (even -> odd -> even)
   bool graph_failed = false;

@@ -29,12 +29,23 @@ struct TriArraysDF {
   void* rec = nullptr;
   double* cfl = nullptr;
   DevCtl* ctl = nullptr;
-  int occ = 2;  // kernel variant: 2 (128 registers), 3 (128, block barriers between phases)
+  // kernel variant: 2 (128 registers), 3 (128, block barriers between phases),
+  // 4 (168 registers), 5 (168, block barriers)
+  int variant = 2;
   const double* dtm = nullptr;      // batched form: per-mesh dt, indexed by tmesh[t]
   const uint16_t* tmesh = nullptr;
 };
 int launch_tri_stage1_df(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
                          cudaStream_t st);
+// The kernels of one variant: REGS registers per thread (128 or 168), SYNC a
+// block barrier between the phases of the per-triangle algebra.  Defined in
+// rd_df64_kernels.cuh, instantiated in rd_df64_s{1,2}_r{128,168}.cu.
+template <int REGS, bool SYNC>
+int df_stage1(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
+              cudaStream_t st);
+template <int REGS, bool SYNC>
+int df_stage2(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
+              cudaStream_t st);
 int launch_tri_stage2_df(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
                          cudaStream_t st);
 

@@ -140,14 +140,14 @@ def test_df64_full_size_4096_khi_first_steps(rd):
 
 
 def test_df64_kernel_variants_are_bitwise_equal(rd):
-    """The DF64 triangle-kernel variants (128 registers, without and with block
-    barriers between phases) and every block size run the same arithmetic: bitwise
-    equal states, including a ragged last block."""
+    """The DF64 triangle-kernel variants (128 and 168 registers, without and with
+    block barriers between phases) and every block size run the same arithmetic:
+    bitwise equal states, including a ragged last block."""
     mesh = inputs.periodic_grid(45, 37, Lx=1.0, Ly=37 / 45, relabel_seed=6)
     W0 = inputs.khi_state(mesh)
     m = rd.Mesh(mesh)
     ref = None
-    for occ in (2, 3):
+    for occ in (2, 3, 4, 5):
         for tb in (64, 256):
             for scheme in ("B2", "N1"):
                 s = rd.State(m, W0, scheme=scheme, precision="df64")
