@@ -295,6 +295,7 @@ def run_state_timing(binding, mesh_dev, W0, scheme, precision, steps, warmup, ws
         s.set_tiling(tt, bt, stage_geometry=gs)
     s.tiles = s.tiling()
     s.tflags = s.tiling_flags()
+    s.sshapes = {f"stage{k}": dict(zip(("tri_block", "df_variant"), s.stage_shapes(k))) for k in (1, 2)}
     s.run(warmup)
     st = mesh_dev.stream
     torch.cuda.synchronize()
@@ -442,8 +443,8 @@ def ours(args, ws, rank, local):
                        "l2": "inputs larger than L2 (%.0f MB vertex state)" % (4 * nv * s_bytes / 1e6),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "ms_per_step_graph": ms_graph, "per_kernel_ms": per_kernel,
-            "launch_shapes": {"tri_block": shapes[0], "vtx_block": shapes[1], "source": "rd_state_autotune"}
-            if shapes else None,
+            "launch_shapes": {"tri_block": shapes[0], "vtx_block": shapes[1], "per_stage": s.sshapes,
+                              "source": "rd_state_autotune"} if shapes else None,
             "tiling": tiling_info(s.tiles, s.tflags),
             "roofline": roof, "step_hbm": step_hbm, "e2e": e2e,
             "gpu_launches": launches * args.steps + 1,
@@ -481,8 +482,7 @@ def ours(args, ws, rank, local):
         eq = fl_df * nt / (pkdf[ddf] * 1e-3) if fl_df else None
         line["df64"] = {"value": ws * nt / (msdf * 1e-3), "ms_per_step": msdf, "per_kernel_ms": pkdf,
                         "vs_fp64_step": ms_step / msdf,
-                        "launch_shapes": dict(zip(("tri_block", "vtx_block", "df_variant"),
-                                                  sdf.launch_shapes())),
+                        "launch_shapes": {"vtx_block": sdf.launch_shapes()[1], "per_stage": sdf.sshapes},
                         "dominant_kernel": ddf,
                         "traffic_source": ncu_traffic(args.workload, "df64", ddf, nt),
                         "counted_fp64_equivalent_tflops": eq / 1e12 if eq else None,

@@ -435,19 +435,25 @@ int rd_math_eval(int32_t fn, int64_t n, const double *x, double *out, void *cuda
  * be NULL; the tiling is read with rd_state_get_tiling).  Results do not
  * depend on the launch shape (every sum has a fixed order). */
 int rd_state_autotune(rd_state *s, int32_t *tri_block, int32_t *vtx_block);
-/* Launch shapes a state uses (after rd_state_autotune): triangle and vertex
- * block sizes and, for RD_DF64, the variant of its triangle kernels: 2: 128
- * registers per thread (four warps per SM sub-partition, some spills);
- * 3: 128 registers with a block barrier between the phases of the
- * per-triangle algebra, so that a block's warps fetch the long straight-line
- * code together; 4: 168 registers (three warps per sub-partition, few or no
- * spills); 5: 168 registers with the barriers.  The autotuner times all four
- * for RD_DF64 states.  Any pointer may be NULL. */
+/* Launch shapes a state uses (after rd_state_autotune): the stage-1 triangle
+ * block size, the vertex block size and, for RD_DF64, the variant of the
+ * stage-1 triangle kernel (rd_state_stage_shapes gives each stage's).  The
+ * RD_DF64 variants: 2: 128 registers per thread; 3: 128 registers with a block
+ * barrier between the phases of the per-triangle algebra, so that a block's
+ * warps fetch the long straight-line code together; 4: 96 registers with the
+ * barriers; 5: 80 registers with the barriers (fewer registers: more resident
+ * warps, more spills).  The autotuner times every variant and triangle block
+ * size and keeps the fastest for each stage.  Any pointer may be NULL. */
 int rd_state_launch_shapes(const rd_state *s, int32_t *tri_block, int32_t *vtx_block, int32_t *df_variant);
-/* Set the launch shapes by hand: tri_block in {64, 128, 192, 256}, vtx_block in
- * {128, 256, 512}, df_variant in {2, 3, 4, 5} (ignored unless RD_DF64); RD_EINVAL
- * otherwise.  Results do not depend on them. */
+/* Set the launch shapes by hand, the same for both stages: tri_block in {64,
+ * 128, 192, 256}, vtx_block in {128, 256, 512}, df_variant in {2, 3, 4, 5}
+ * (ignored unless RD_DF64); RD_EINVAL otherwise.  Results do not depend on them. */
 int rd_state_set_launch_shapes(rd_state *s, int32_t tri_block, int32_t vtx_block, int32_t df_variant);
+/* Triangle block size and RD_DF64 kernel variant of one stage (1 or 2) of the
+ * two-stage step: read (pointers may be NULL) and set (same ranges as above;
+ * RD_EINVAL otherwise).  Results do not depend on them. */
+int rd_state_stage_shapes(const rd_state *s, int32_t stage, int32_t *tri_block, int32_t *df_variant);
+int rd_state_set_stage_shapes(rd_state *s, int32_t stage, int32_t tri_block, int32_t df_variant);
 
 /* Tiled step (Sec. 3.3-3.4 and Eqs. eqRK1/eqRK2 computed as in rd_step; the
  * distribution of Sec. 4.2.1 done on chip).  The triangles, in the mesh

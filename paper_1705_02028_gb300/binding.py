@@ -98,6 +98,8 @@ _SIGS = {
     "rd_state_autotune": (ctypes.c_int, [_vp, _i32p, _i32p]),
     "rd_state_launch_shapes": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p]),
     "rd_state_set_launch_shapes": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "rd_state_stage_shapes": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _i32p]),
+    "rd_state_set_stage_shapes": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "rd_state_set_tiling": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
     "rd_state_set_tiling_ex": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "rd_state_get_tiling_flags": (ctypes.c_int, [_vp, _i32p]),
@@ -420,8 +422,20 @@ class State:
         return tb.value, vb.value, oc.value
 
     def set_launch_shapes(self, tri_block: int, vtx_block: int, df_variant: int = 2):
+        """The same triangle block and DF64 variant for both stages (rd_state_set_launch_shapes)."""
         _check(_lib.rd_state_set_launch_shapes(self.handle, int(tri_block), int(vtx_block), int(df_variant)),
                "rd_state_set_launch_shapes")
+
+    def stage_shapes(self, stage: int):
+        """(triangle block, DF64 kernel variant) of stage 1 or 2 (rd_state_stage_shapes)."""
+        tb, oc = ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.rd_state_stage_shapes(self.handle, int(stage), ctypes.byref(tb), ctypes.byref(oc)),
+               "rd_state_stage_shapes")
+        return tb.value, oc.value
+
+    def set_stage_shapes(self, stage: int, tri_block: int, df_variant: int = 2):
+        _check(_lib.rd_state_set_stage_shapes(self.handle, int(stage), int(tri_block), int(df_variant)),
+               "rd_state_set_stage_shapes")
 
     def set_tiling(self, tile_triangles: int, threads: int = 128, stage_geometry: bool = False):
         """Tiled step with tiles of `tile_triangles` triangles (0: untiled); rd_state_set_tiling_ex,

@@ -26,10 +26,12 @@ typedef unsigned long long Mask;
 template <class T>
 RD_HD Mask node_mask(const TriLin<T>& L, const T hl[3], T eps) {
   Mask m = 0;
+#pragma unroll
   for (int i = 0; i < 3; ++i) {
     const NodeSys<T>& n = L.nd[i];
     T delta = eps * L.r.c * hl[i];
     T la[3] = {(n.w + L.r.c) * hl[i], (n.w - L.r.c) * hl[i], n.w * hl[i]};
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
       if (fabs(la[k]) < delta) m |= 1ull << (3 * i + k);
       if (la[k] < T(0)) m |= 1ull << (9 + 3 * i + k);
@@ -41,6 +43,7 @@ RD_HD Mask node_mask(const TriLin<T>& L, const T hl[3], T eps) {
 template <class T>
 RD_HD Mask blend_mask(const T tot[4], const T N[3][4]) {
   Mask m = 0;
+#pragma unroll
   for (int k = 0; k < 4; ++k) {
     T num = fabs(tot[k]);
     T D = fabs(N[0][k]) + fabs(N[1][k]) + fabs(N[2][k]);
@@ -49,6 +52,7 @@ RD_HD Mask blend_mask(const T tot[4], const T N[3][4]) {
     if (tot[k] == T(0)) m |= 1ull << (22 + k);
     if (D > num) m |= 1ull << (26 + k);
     if (den > T(0)) m |= 1ull << (30 + k);
+#pragma unroll
     for (int i = 0; i < 3; ++i) {
       if (N[i][k] < T(0)) m |= 1ull << (34 + 4 * i + k);
       if (N[i][k] == T(0)) m |= 1ull << (46 + 4 * i + k);
@@ -90,6 +94,7 @@ RD_HD void Kpm_rev(const RoeState<T>& r, const NodeSys<T>& n, const T v[4], cons
   T Q = n.s2[j] * A + n.hp[j] * B;
   T l3 = n.l3[j];
   nb.l3[j] += ob[0] * v[0] + ob[1] * v[1] + ob[2] * v[2] + ob[3] * v[3];
+#pragma unroll
   for (int k = 0; k < 4; ++k) vb[k] += l3 * ob[k];
   T Pb = ob[0] + r.u * ob[1] + r.v * ob[2] + r.h * ob[3];
   T Qb = n.nx * ob[1] + n.ny * ob[2] + n.w * ob[3];
@@ -117,8 +122,10 @@ template <class T>
 RD_HD void solve_rev(const LU4<T>& lu, const T x[4], const T xb[4], T bb[4], T Mb[4][4]) {
   T z[4];
   lu.solve_t(xb, z);
+#pragma unroll
   for (int r = 0; r < 4; ++r) {
     bb[r] += z[r];
+#pragma unroll
     for (int c = 0; c < 4; ++c) Mb[r][c] -= z[r] * x[c];
   }
 }
@@ -127,6 +134,7 @@ RD_HD void solve_rev(const LU4<T>& lu, const T x[4], const T xb[4], T bb[4], T M
 template <class T>
 RD_HD void blend_rev(const T tot[4], const T N[3][4], const T lda[3][4], const T ob[3][4], Mask m, T totb[4],
                      T Nb[3][4], T ldab[3][4]) {
+#pragma unroll
   for (int k = 0; k < 4; ++k) {
     T num = fabs(tot[k]);
     T D = fabs(N[0][k]) + fabs(N[1][k]) + fabs(N[2][k]);
@@ -134,6 +142,7 @@ RD_HD void blend_rev(const T tot[4], const T N[3][4], const T lda[3][4], const T
     const T iden = rcp(den);
     T th = mbit(m, 30 + k) ? num * iden : T(0);
     T thb = T(0);
+#pragma unroll
     for (int i = 0; i < 3; ++i) {
       thb += ob[i][k] * (N[i][k] - lda[i][k]);
       Nb[i][k] += th * ob[i][k];
@@ -145,6 +154,7 @@ RD_HD void blend_rev(const T tot[4], const T N[3][4], const T lda[3][4], const T
     T Db = T(0);
     if (mbit(m, 26 + k)) Db = denb;
     else numb += denb;
+#pragma unroll
     for (int i = 0; i < 3; ++i) Nb[i][k] += Db * msign<T>(m, 34 + 4 * i + k, 46 + 4 * i + k);
     totb[k] += numb * msign<T>(m, 18 + k, 22 + k);
   }
@@ -155,6 +165,7 @@ template <class T>
 RD_HD void lda_rev(const TriLin<T>& L, const T y[4], const T ldab[3][4], T xb[4], T Mb[4][4], RoeBar<T>& rb,
                    NodeBar<T> nb[3]) {
   T yb[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
   for (int i = 0; i < 3; ++i) {
     T ob[4] = {-ldab[i][0], -ldab[i][1], -ldab[i][2], -ldab[i][3]};
     Kpm_rev<T, true>(L.r, L.nd[i], y, ob, yb, rb, nb[i]);
@@ -173,13 +184,18 @@ RD_HD void linearise_rev(const T Z[3][4], const T nx[3], const T ny[3], const T 
   const T* Zb = L.Zb;
   const T g = r.g1 / gamma, ig = T(1) / gamma, third = T(1) / T(3);
   T Whb[3][4], winb[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
   for (int i = 0; i < 3; ++i)
+#pragma unroll
     for (int k = 0; k < 4; ++k) Whb[i][k] = T(0);
   // phi^N_i = K_i^+ (W^_i - win)
+#pragma unroll
   for (int i = 0; i < 3; ++i) {
     T d[4], db[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
     for (int k = 0; k < 4; ++k) d[k] = L.Wh[i][k] - L.win[k];
     Kpm_rev<T, true>(r, L.nd[i], d, phiNb[i], db, rb, nb[i]);
+#pragma unroll
     for (int k = 0; k < 4; ++k) {
       Whb[i][k] += db[k];
       winb[k] -= db[k];
@@ -189,9 +205,11 @@ RD_HD void linearise_rev(const T Z[3][4], const T nx[3], const T ny[3], const T 
   T Sb[4] = {T(0), T(0), T(0), T(0)};
   solve_rev(L.lu, L.win, winb, Sb, Mb);
   // S = sum_i K_i^- W^_i
+#pragma unroll
   for (int i = 0; i < 3; ++i) Kpm_rev<T, false>(r, L.nd[i], L.Wh[i], Sb, Whb[i], rb, nb[i]);
   // W^_i = dW/dZ(Zbar) Z_i
   T Zbb[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
   for (int i = 0; i < 3; ++i) {
     const T* w = Whb[i];
     const T* z = Z[i];
@@ -208,6 +226,7 @@ RD_HD void linearise_rev(const T Z[3][4], const T nx[3], const T ny[3], const T 
   {
     T L3b = Mb[0][0] + Mb[1][1] + Mb[2][2] + Mb[3][3];
     T S1 = T(0), Pw = T(0), Px = T(0), Py = T(0);
+#pragma unroll
     for (int j = 0; j < 3; ++j) {
       S1 += L.nd[j].s1[1];
       Pw += L.nd[j].s2[1] * L.nd[j].w;
@@ -216,6 +235,7 @@ RD_HD void linearise_rev(const T Z[3][4], const T nx[3], const T ny[3], const T 
     }
     T P[4] = {S1 * r.alpha - Pw, Px - S1 * r.g1u, Py - S1 * r.g1v, S1 * r.g1};
     T Pb[4];
+#pragma unroll
     for (int c = 0; c < 4; ++c) {
       Pb[c] = Mb[0][c] + r.u * Mb[1][c] + r.v * Mb[2][c] + r.h * Mb[3][c];
       rb.u += Mb[1][c] * P[c];
@@ -227,11 +247,13 @@ RD_HD void linearise_rev(const T Z[3][4], const T nx[3], const T ny[3], const T 
     rb.g1u -= Pb[1] * S1;
     rb.g1v -= Pb[2] * S1;
     T Pwb = -Pb[0], Pxb = Pb[1], Pyb = Pb[2];
+#pragma unroll
     for (int j = 0; j < 3; ++j) {
       const NodeSys<T>& n = L.nd[j];
       T s2 = n.s2[1], hp = n.hp[1];
       T q[4] = {s2 * r.alpha - hp * n.w, hp * n.nx - s2 * r.g1u, hp * n.ny - s2 * r.g1v, s2 * r.g1};
       T qb[4];
+#pragma unroll
       for (int c = 0; c < 4; ++c) {
         qb[c] = n.nx * Mb[1][c] + n.ny * Mb[2][c] + n.w * Mb[3][c];
         nb[j].w += Mb[3][c] * q[c];
@@ -249,6 +271,7 @@ RD_HD void linearise_rev(const T Z[3][4], const T nx[3], const T ny[3], const T 
     }
   }
   // node eigen-split -> (u, v, c, ic2h, i2c)
+#pragma unroll
   for (int i = 0; i < 3; ++i) {
     const NodeSys<T>& n = L.nd[i];
     T delta = eps * r.c * hl[i];
@@ -256,9 +279,11 @@ RD_HD void linearise_rev(const T Z[3][4], const T nx[3], const T ny[3], const T 
     const bool reg = mbit(mask, 3 * i) || mbit(mask, 3 * i + 1) || mbit(mask, 3 * i + 2);
     const T idelta = reg ? rcp(delta) : T(0);
     T ab[3];
+#pragma unroll
     for (int k = 0; k < 3; ++k)
       ab[k] = mbit(mask, 3 * i + k) ? (la[k] * la[k] + delta * delta) * (T(0.5) * idelta) : fabs(la[k]);
     T lab[3] = {T(0), T(0), T(0)}, abb[3] = {T(0), T(0), T(0)};
+#pragma unroll
     for (int j = 0; j < 2; ++j) {
       T sg = j == 0 ? T(0.5) : T(-0.5);
       T l1 = la[0] * T(0.5) + sg * ab[0];
@@ -272,12 +297,14 @@ RD_HD void linearise_rev(const T Z[3][4], const T nx[3], const T ny[3], const T 
       rb.i2c += nb[i].s2[j] * sm;
       T mu1b = spb + smb, mu2b = spb - smb;
       T lb[3] = {mu1b, mu2b, nb[i].l3[j] - mu1b - mu2b};
+#pragma unroll
       for (int k = 0; k < 3; ++k) {
         lab[k] += T(0.5) * lb[k];
         abb[k] += sg * lb[k];
       }
     }
     T deltab = T(0);
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
       if (mbit(mask, 3 * i + k)) {
         lab[k] += abb[k] * la[k] * idelta;
@@ -304,8 +331,10 @@ RD_HD void linearise_rev(const T Z[3][4], const T nx[3], const T ny[3], const T 
     Zbb[1] += gx[0] * p[0] + ((T(2) - g) * gx[1] + gy[2]) * p[1] + (gx[2] - g * gy[1]) * p[2] + gx[3] * p[3];
     Zbb[2] += gy[0] * p[0] + (gy[1] - g * gx[2]) * p[1] + (gx[1] + (T(2) - g) * gy[2]) * p[2] + gy[3] * p[3];
     Zbb[3] += g * gx[0] * p[1] + g * gy[0] * p[2] + (gx[1] + gy[2]) * p[3];
+#pragma unroll
     for (int i = 0; i < 3; ++i) {
       T ax = nx[i] * hl[i], ay = ny[i] * hl[i];
+#pragma unroll
       for (int k = 0; k < 4; ++k) Zb_out[i][k] += ax * gxb[k] + ay * gyb[k];
     }
   }
@@ -328,7 +357,9 @@ RD_HD void linearise_rev(const T Z[3][4], const T nx[3], const T ny[3], const T 
     T izb = Zb[1] * ub + Zb[2] * vb + Zb[3] * hb;
     Zbb[0] -= iz * iz * izb;
   }
+#pragma unroll
   for (int i = 0; i < 3; ++i)
+#pragma unroll
     for (int k = 0; k < 4; ++k) Zb_out[i][k] += third * Zbb[k];
 }
 
@@ -343,37 +374,53 @@ RD_HD int stage1_rev_lin(const TriLin<T>& L, const T Z[3][4], const T nx[3], con
   RoeBar<T> rb;
   rb.zero();
   NodeBar<T> nb[3];
+#pragma unroll
   for (int i = 0; i < 3; ++i) nb[i].zero();
+#pragma unroll
   for (int r = 0; r < 4; ++r)
+#pragma unroll
     for (int c = 0; c < 4; ++c) Mb[r][c] = T(0);
+#pragma unroll
   for (int i = 0; i < 3; ++i)
+#pragma unroll
     for (int k = 0; k < 4; ++k) phiNb[i][k] = T(0);
   if (SCHEME == RD_N1) {
+#pragma unroll
     for (int i = 0; i < 3; ++i)
+#pragma unroll
       for (int k = 0; k < 4; ++k) phiNb[i][k] = outb[i][k];
   } else {
     T y[4], lda[3][4], ldab[3][4];
     L.lu.solve(L.phiT, y);
+#pragma unroll
     for (int i = 0; i < 3; ++i) {
       T o[4];
       Kpm_apply<T, true>(L.r, L.nd[i], y, o);
+#pragma unroll
       for (int k = 0; k < 4; ++k) {
         lda[i][k] = -o[k];
         ldab[i][k] = T(0);
       }
     }
     if (SCHEME == RD_LDA2) {
+#pragma unroll
       for (int i = 0; i < 3; ++i)
+#pragma unroll
         for (int k = 0; k < 4; ++k) ldab[i][k] = outb[i][k];
     } else {
       blend_rev(L.phiT, L.phiN, lda, outb, mask, phiTb, phiNb, ldab);
     }
+#pragma unroll
     for (int i = 0; i < 3; ++i)
+#pragma unroll
       for (int k = 0; k < 4; ++k) phiNb[i][k] += recb[4 * i + k];
+#pragma unroll
     for (int k = 0; k < 4; ++k) phiTb[k] += recb[12 + k];
     lda_rev(L, y, ldab, phiTb, Mb, rb, nb);
   }
+#pragma unroll
   for (int i = 0; i < 3; ++i)
+#pragma unroll
     for (int k = 0; k < 4; ++k) Zbar[i][k] = T(0);
   linearise_rev(Z, nx, ny, hl, gamma, eps, L, mask, phiNb, phiTb, Mb, rb, nb, Zbar);
   return 0;
@@ -389,6 +436,13 @@ RD_HD int stage1_rev(const T Z[3][4], const T nx[3], const T ny[3], const T hl[3
 
 // Reverse of the stage-2 body: outputs the adjoints of Z*, W^n, W* (3x4 each)
 // and of the stage-1 record (16).
+// stage2_rev_tot takes the stage-2 totals Phi^N_i, Phi^T (stage2_totals) and
+// the mass factor q = |T| / (3 dt) as given; stage2_rev_lin forms them from
+// W^n, W* and the record.
+template <class T, int SCHEME>
+RD_HD int stage2_rev_tot(const TriLin<T>& L, const T PhiN[3][4], const T PhiT[4], T q, const T Zs[3][4],
+                         const T nx[3], const T ny[3], const T hl[3], T gamma, T eps, Mask mask, const T outb[3][4],
+                         T Zsb[3][4], T Wnb[3][4], T Wsb[3][4], T recb[16]);
 template <class T, int SCHEME>
 RD_HD int stage2_rev_lin(const TriLin<T>& L, const T Zs[3][4], const T Wn[3][4], const T Ws[3][4], const T rec[16],
                          const T nx[3], const T ny[3], const T hl[3], T area, T dt, T gamma, T eps, Mask mask,
@@ -396,23 +450,37 @@ RD_HD int stage2_rev_lin(const TriLin<T>& L, const T Zs[3][4], const T Wn[3][4],
   const T q = area * (T(1) / T(3)) * rcp(dt);  // |T| / (3 dt), as in stage2_totals
   T PhiN[3][4], PhiT[4];
   stage2_totals(L, Wn, Ws, rec, area, rcp(dt), PhiN, PhiT);
+  return stage2_rev_tot<T, SCHEME>(L, PhiN, PhiT, q, Zs, nx, ny, hl, gamma, eps, mask, outb, Zsb, Wnb, Wsb, recb);
+}
+template <class T, int SCHEME>
+RD_HD int stage2_rev_tot(const TriLin<T>& L, const T PhiN[3][4], const T PhiT[4], T q, const T Zs[3][4],
+                         const T nx[3], const T ny[3], const T hl[3], T gamma, T eps, Mask mask, const T outb[3][4],
+                         T Zsb[3][4], T Wnb[3][4], T Wsb[3][4], T recb[16]) {
   T y[4], lda[3][4], ldab[3][4];
   L.lu.solve(PhiT, y);
+#pragma unroll
   for (int i = 0; i < 3; ++i) {
     T o[4];
     Kpm_apply<T, true>(L.r, L.nd[i], y, o);
+#pragma unroll
     for (int k = 0; k < 4; ++k) {
       lda[i][k] = -o[k];
       ldab[i][k] = T(0);
     }
   }
   T PhiNb[3][4], PhiTb[4] = {T(0), T(0), T(0), T(0)}, Mb[4][4];
+#pragma unroll
   for (int i = 0; i < 3; ++i)
+#pragma unroll
     for (int k = 0; k < 4; ++k) PhiNb[i][k] = T(0);
+#pragma unroll
   for (int r = 0; r < 4; ++r)
+#pragma unroll
     for (int c = 0; c < 4; ++c) Mb[r][c] = T(0);
   if (SCHEME == RD_LDA2) {
+#pragma unroll
     for (int i = 0; i < 3; ++i)
+#pragma unroll
       for (int k = 0; k < 4; ++k) ldab[i][k] = outb[i][k];
   } else {
     blend_rev(PhiT, PhiN, lda, outb, mask, PhiTb, PhiNb, ldab);
@@ -420,14 +488,18 @@ RD_HD int stage2_rev_lin(const TriLin<T>& L, const T Zs[3][4], const T Wn[3][4],
   RoeBar<T> rb;
   rb.zero();
   NodeBar<T> nb[3];
+#pragma unroll
   for (int i = 0; i < 3; ++i) nb[i].zero();
   lda_rev(L, y, ldab, PhiTb, Mb, rb, nb);
   T phiNb[3][4], phiTb[4];
+#pragma unroll
   for (int k = 0; k < 4; ++k) {
     phiTb[k] = T(0.5) * PhiTb[k];
     recb[12 + k] = T(0.5) * PhiTb[k];
   }
+#pragma unroll
   for (int i = 0; i < 3; ++i)
+#pragma unroll
     for (int k = 0; k < 4; ++k) {
       T mb = PhiNb[i][k] + PhiTb[k];
       phiNb[i][k] = T(0.5) * PhiNb[i][k];

@@ -249,8 +249,8 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
   T* share = (T*)s->share.p;
   T* rec = (T*)s->rec.p;
   T* cf = (T*)s->cfl.p;
-  const int TB = s->tri_block, VB = s->vtx_block;
-  unsigned gt = nblk(nt, TB), gv = nblk(nv, VB);
+  const int TB = s->tri_block, TB2 = s->tri_block2, VB = s->vtx_block;
+  unsigned gt = nblk(nt, TB), gt2 = nblk(nt, TB2), gv = nblk(nv, VB);
   const T* Za = (const T*)s->Z[a].p;
   const T* Sa = (const T*)s->spd[a].p;
   auto mark = [&](int k) {
@@ -323,16 +323,16 @@ int launch_step(rd_state* s, int a, cudaEvent_t* ev = nullptr, bool commit = tru
                                           GhostArgs<T>(), df ? (float2*)s->dWdf.p : nullptr);
     mark(3);
     if (df)
-      CK(launch_tri_stage2_df(s, a, gt, TB, st));
+      CK(launch_tri_stage2_df(s, a, gt2, TB2, st));
     else if (s->p.scheme == RD_LDA2)
-      k_tri_stage2<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
+      k_tri_stage2<T, RD_LDA2><<<gt2, TB2, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
                                                   (const T*)s->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl,
                                                   nullptr, nullptr, ba2);
     else if (s->p.scheme == RD_B2 && s->p.lumping == RD_LUMP_GLOBAL)
-      k_tri_stage2<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
+      k_tri_stage2<T, RD_B2><<<gt2, TB2, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
                                                 (const T*)s->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl);
     else
-      k_tri_stage2<T, RD_BMAX2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
+      k_tri_stage2<T, RD_BMAX2><<<gt2, TB2, 0, st>>>(nt, nv, tri, g, (const T*)s->Zs.p, (const T*)s->W[a].p,
                                                    (const T*)s->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl,
                                                    nullptr, nullptr, ba2);
     mark(4);
@@ -634,41 +634,51 @@ extern "C" int rd_state_autotune(rd_state* s, int32_t* tri_block, int32_t* vtx_b
   const int vtx_c[] = {128, 256, 512};
   cudaEvent_t ev[7];
   for (auto& e : ev) cudaEventCreate(&e);
-  auto time_step = [&](int tb, int vb, float& ms) -> int {
-    s->tri_block = tb;
-    s->vtx_block = vb;
+  // One untimed and one timed step with the shapes set on the state: ms the whole
+  // step, ms1 / ms2 the stage-1 / stage-2 triangle kernels (events 0-1 and 3-4).
+  auto time_step = [&](float& ms, float& ms1, float& ms2) -> int {
     k_begin<<<1, 1, 0, st>>>((DevCtl*)s->ctl.p, 0.0);
     CK(launch_step_any(s, a, nullptr, false));  // warm
     CK(launch_step_any(s, a, ev, false));
     CU(cudaStreamSynchronize(st));
     CU(cudaEventElapsedTime(&ms, ev[0], ev[6]));
+    CU(cudaEventElapsedTime(&ms1, ev[0], ev[1]));
+    CU(cudaEventElapsedTime(&ms2, ev[3], ev[4]));
     return RD_OK;
   };
-  int best_t = TRI_BLOCK, best_v = VTX_BLOCK, best_o = s->df_variant, rc = RD_OK;
-  float best = 1e30f, ms = 0.f;
-  // DF64: the triangle kernels at 128 and 168 registers, without and with block barriers between phases
-  const int o0 = s->p.precision == RD_DF64 ? 2 : s->df_variant, o1 = s->p.precision == RD_DF64 ? 5 : s->df_variant;
-  for (int o = o0; o <= o1; ++o) {
-    s->df_variant = o;
+  int best_t = TRI_BLOCK, best_t2 = TRI_BLOCK, best_v = VTX_BLOCK, rc = RD_OK;
+  int best_o = s->df_variant, best_o2 = s->df_variant2;
+  float best = 1e30f, best1 = 1e30f, best2 = 1e30f, ms = 0.f, ms1 = 0.f, ms2 = 0.f;
+  // Triangle block size (and for RD_DF64 the kernel variant: 128 registers
+  // without and with phase barriers, 96 and 80 with barriers) chosen per stage
+  // from each stage's own kernel time; the two stages are independent kernels.
+  const bool df = s->p.precision == RD_DF64;
+  const int o0 = df ? 2 : s->df_variant, o1 = df ? 5 : s->df_variant;
+  s->vtx_block = VTX_BLOCK;
+  for (int o = o0; o <= o1 && rc == RD_OK; ++o) {
+    s->df_variant = s->df_variant2 = o;
     for (int tb : tri_c) {
-      if ((rc = time_step(tb, VTX_BLOCK, ms)) != RD_OK) break;
-      if (ms < best) { best = ms; best_t = tb; best_o = o; }
+      s->tri_block = s->tri_block2 = tb;
+      if ((rc = time_step(ms, ms1, ms2)) != RD_OK) break;
+      if (ms1 < best1) { best1 = ms1; best_t = tb; best_o = o; }
+      if (ms2 < best2) { best2 = ms2; best_t2 = tb; best_o2 = o; }
     }
-    if (rc != RD_OK) break;
   }
   s->df_variant = best_o;
-  best = 1e30f;
+  s->df_variant2 = best_o2;
+  s->tri_block = best_t;
+  s->tri_block2 = best_t2;
   for (int vb : vtx_c) {
-    if (rc != RD_OK || (rc = time_step(best_t, vb, ms)) != RD_OK) break;
+    s->vtx_block = vb;
+    if (rc != RD_OK || (rc = time_step(ms, ms1, ms2)) != RD_OK) break;
     if (ms < best) { best = ms; best_v = vb; }
   }
-  s->tri_block = best_t;
   s->vtx_block = best_v;
   // tiled step: a few tile sizes against the untiled step with the shapes above
   if (rc == RD_OK && s->m->h.nt >= 4096 && s->p.precision != RD_DF64) {
     float untiled = 1e30f;
     rc = rd_state_set_tiling(s, 0, 0);
-    if (rc == RD_OK) rc = time_step(best_t, best_v, untiled);
+    if (rc == RD_OK) rc = time_step(untiled, ms1, ms2);
     // (tile triangles, threads, flags)
     // (Staging the tile geometry in shared memory, RD_TILE_STAGE_GEOMETRY, measured
     // no faster at 4096^2 -- the tile kernels are issue-bound, not waiting on the
@@ -682,7 +692,7 @@ extern "C" int rd_state_autotune(rd_state* s, int32_t* tri_block, int32_t* vtx_b
       const int* c = s->pi == 0 ? c64[k] : c32[k];
       int r = rd_state_set_tiling_ex(s, c[0], c[1], c[2]);
       if (r == RD_ENOTSUP) continue;  // no tile plan for this mesh, or not enough shared memory
-      if ((rc = r) != RD_OK || (rc = time_step(best_t, best_v, ms)) != RD_OK) break;
+      if ((rc = r) != RD_OK || (rc = time_step(ms, ms1, ms2)) != RD_OK) break;
       if (ms < best_tiled) { best_tiled = ms; best_tt = c[0]; best_bt = c[1]; best_fl = c[2]; }
     }
     if (best_tt && !(best_tiled < 0.98f * untiled)) {  // keep the untiled step unless tiling wins clearly
@@ -715,9 +725,30 @@ extern "C" int rd_state_set_launch_shapes(rd_state* s, int32_t tri_block, int32_
   if (tri_block != 64 && tri_block != 128 && tri_block != 192 && tri_block != 256) return RD_EINVAL;
   if (vtx_block != 128 && vtx_block != 256 && vtx_block != 512) return RD_EINVAL;
   if (df_variant < 2 || df_variant > 5) return RD_EINVAL;
-  s->tri_block = tri_block;
+  s->tri_block = s->tri_block2 = tri_block;
   s->vtx_block = vtx_block;
-  s->df_variant = df_variant;
+  s->df_variant = s->df_variant2 = df_variant;
+  if (s->g2) {  // the captured graph holds the old launch shapes
+    cudaStreamSynchronize(s->m->stream);
+    cudaGraphExecDestroy(s->g2);
+    s->g2 = nullptr;
+  }
+  return RD_OK;
+}
+
+extern "C" int rd_state_stage_shapes(const rd_state* s, int32_t stage, int32_t* tri_block, int32_t* df_variant) {
+  if (!s || (stage != 1 && stage != 2)) return RD_EINVAL;
+  if (tri_block) *tri_block = stage == 1 ? s->tri_block : s->tri_block2;
+  if (df_variant) *df_variant = stage == 1 ? s->df_variant : s->df_variant2;
+  return RD_OK;
+}
+
+extern "C" int rd_state_set_stage_shapes(rd_state* s, int32_t stage, int32_t tri_block, int32_t df_variant) {
+  if (!s || (stage != 1 && stage != 2)) return RD_EINVAL;
+  if (tri_block != 64 && tri_block != 128 && tri_block != 192 && tri_block != 256) return RD_EINVAL;
+  if (df_variant < 2 || df_variant > 5) return RD_EINVAL;
+  (stage == 1 ? s->tri_block : s->tri_block2) = tri_block;
+  (stage == 1 ? s->df_variant : s->df_variant2) = df_variant;
   if (s->g2) {  // the captured graph holds the old launch shapes
     cudaStreamSynchronize(s->m->stream);
     cudaGraphExecDestroy(s->g2);

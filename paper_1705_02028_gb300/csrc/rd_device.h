@@ -129,8 +129,12 @@ struct rd_state {
   int bc_version = 0;      // mesh boundary version the state was set up for
   bool bc_init = false;
   long long launched = 0;  // host view of the committed step count (parity of the buffers)
-  int tri_block = rd::TRI_BLOCK, vtx_block = rd::VTX_BLOCK;  // launch shapes (autotuned)
-  int df_variant = 2;  // RD_DF64 triangle-kernel variant (2 / 3: 128 registers, 4 / 5: 168; 3, 5 with phase barriers; autotuned)
+  int tri_block = rd::TRI_BLOCK, vtx_block = rd::VTX_BLOCK;  // launch shapes (autotuned); tri_block: stage 1
+  int tri_block2 = rd::TRI_BLOCK;                             // stage-2 triangle kernel
+  // RD_DF64 triangle-kernel variant of stage 1 and stage 2 (2: 128 registers;
+  // 3: 128 with phase barriers; 4: 96 with phase barriers; 5: 80 with phase
+  // barriers; autotuned per stage)
+  int df_variant = 2, df_variant2 = 2;
   rd::TilePlan* tiles = nullptr;  // tiled step (nullptr: per-triangle share arrays)
   cudaGraphExec_t g2 = nullptr;  // two steps (even -> odd -> even)
   bool graph_failed = false;

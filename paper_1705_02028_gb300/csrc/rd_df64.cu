@@ -17,8 +17,8 @@ int launch_tri_stage1_df(const rd_params& p, const TriArraysDF& a, BlendArgs<dou
                          cudaStream_t st) {
   switch (a.variant) {
     case 3: return df_stage1<128, true>(p, a, ba, grid, block, st);
-    case 4: return df_stage1<168, false>(p, a, ba, grid, block, st);
-    case 5: return df_stage1<168, true>(p, a, ba, grid, block, st);
+    case 4: return df_stage1<96, true>(p, a, ba, grid, block, st);
+    case 5: return df_stage1<80, true>(p, a, ba, grid, block, st);
     default: return df_stage1<128, false>(p, a, ba, grid, block, st);
   }
 }
@@ -27,8 +27,8 @@ int launch_tri_stage2_df(const rd_params& p, const TriArraysDF& a, BlendArgs<dou
                          cudaStream_t st) {
   switch (a.variant) {
     case 3: return df_stage2<128, true>(p, a, ba, grid, block, st);
-    case 4: return df_stage2<168, false>(p, a, ba, grid, block, st);
-    case 5: return df_stage2<168, true>(p, a, ba, grid, block, st);
+    case 4: return df_stage2<96, true>(p, a, ba, grid, block, st);
+    case 5: return df_stage2<80, true>(p, a, ba, grid, block, st);
     default: return df_stage2<128, false>(p, a, ba, grid, block, st);
   }
 }
@@ -48,7 +48,7 @@ static TriArraysDF state_arrays(const rd_state* s) {
   a.rec = s->rec.p;
   a.cfl = (double*)s->cfl.p;
   a.ctl = (DevCtl*)s->ctl.p;
-  a.variant = s->df_variant;
+  a.variant = s->df_variant;  // stage 1's; stage 2 sets its own
   return a;
 }
 
@@ -65,6 +65,7 @@ int launch_tri_stage2_df(const rd_state* s, int a, unsigned grid, int block, cud
   TriArraysDF x = state_arrays(s);
   x.Z = (const double*)s->Zs.p;
   x.dw = (const float2*)s->dWdf.p;
+  x.variant = s->df_variant2;
   BlendArgs<double> ba = tile_blend_args<double>(s);
   unsigned long long* vr0 = (unsigned long long*)s->vr.p;
   ba.vr = vr0 ? vr0 + 2 : nullptr;

@@ -30,16 +30,17 @@ struct TriArraysDF {
   double* cfl = nullptr;
   DevCtl* ctl = nullptr;
   // kernel variant: 2 (128 registers), 3 (128, block barriers between phases),
-  // 4 (168 registers), 5 (168, block barriers)
+  // 4 (96 registers, barriers), 5 (80 registers, barriers)
   int variant = 2;
   const double* dtm = nullptr;      // batched form: per-mesh dt, indexed by tmesh[t]
   const uint16_t* tmesh = nullptr;
 };
 int launch_tri_stage1_df(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
                          cudaStream_t st);
-// The kernels of one variant: REGS registers per thread (128 or 168), SYNC a
+// The kernels of one variant: REGS registers per thread (128, 96 or 80), SYNC a
 // block barrier between the phases of the per-triangle algebra.  Defined in
-// rd_df64_kernels.cuh, instantiated in rd_df64_s{1,2}_r{128,168}.cu.
+// rd_df64_kernels.cuh, instantiated in rd_df64_s{1,2}_r128.cu and
+// rd_df64_s{1,2}_r96_80.cu.
 template <int REGS, bool SYNC>
 int df_stage1(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, unsigned grid, int block,
               cudaStream_t st);

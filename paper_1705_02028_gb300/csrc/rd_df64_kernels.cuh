@@ -2,8 +2,8 @@
 // state, FP64 vertex kernels, per-triangle algebra (Sec. 3.2-3.4) in
 // double-float.  The launchers df_stage1 / df_stage2 (declared in rd_df64.h)
 // take a register budget and a barrier setting; each rd_df64_s*_r*.cu
-// translation unit instantiates one stage at one budget, so that the large
-// straight-line kernels compile in parallel.
+// translation unit instantiates one stage at one or two budgets, so that the
+// large straight-line kernels compile in parallel.
 //
 // GB300 runs FP64 at 1/64 of its FP32 rate and the FP64 triangle kernels keep
 // the FP64 pipe ~90 % busy.  These kernels form, in double precision, only
@@ -96,13 +96,14 @@ __device__ __forceinline__ void ld_rec(const dfloat* p, dfloat r[16]) {
   }
 }
 
-// REGS: register budget per thread.  128 leaves four warps per SM
-// sub-partition and spills a few hundred bytes (measured 1.4-1.7x faster than
-// the spill-free 255-register build, whose two warps cannot hide the
-// double-float dependency chains); 168 is the largest budget that still
-// leaves three.  At the N-scheme solve the 4x4 LU, the three node systems, the
-// Roe state and the linearised states are live together, which 128 registers
-// cannot hold.  SYNC: a block barrier between the
+// REGS: register budget per thread (128, 96 or 80: four, five or six warps per
+// SM sub-partition).  The kernel is latency-bound on its double-float
+// dependency chains, so resident warps matter more than spills: 128 registers
+// (a few hundred bytes of spills) measured 1.4-1.7x faster than the spill-free
+// 255-register build, and 168 (three warps, almost no spills) 1.2x slower
+// than 128.  Below 128 the spills grow (at the N-scheme solve the 4x4 LU, the
+// three node systems, the Roe state and the linearised states are live
+// together), and only the barrier variant gains.  SYNC: a block barrier between the
 // phases of the per-triangle algebra.  The body is ~10^4 instructions of
 // straight-line code, far more than the instruction caches hold, and warps
 // that drift apart miss in them (ncu: "no instruction" is the leading stall);
@@ -347,9 +348,8 @@ int df_stage2(const rd_params& p, const TriArraysDF& a, BlendArgs<double> ba, un
 
 }  // namespace rd
 
-// Explicit instantiation of one stage's launcher for both barrier settings.
-#define RD_DF64_INSTANTIATE(STAGE, REGS)                                                                   \
-  template int rd::df_stage##STAGE<REGS, false>(const rd_params&, const rd::TriArraysDF&,                    \
-                                                rd::BlendArgs<double>, unsigned, int, cudaStream_t);          \
-  template int rd::df_stage##STAGE<REGS, true>(const rd_params&, const rd::TriArraysDF&,                     \
+// Explicit instantiation of one stage's launcher at one register budget and
+// barrier setting.
+#define RD_DF64_INSTANTIATE(STAGE, REGS, SYNC)                                                     \
+  template int rd::df_stage##STAGE<REGS, SYNC>(const rd_params&, const rd::TriArraysDF&,              \
                                                rd::BlendArgs<double>, unsigned, int, cudaStream_t);

@@ -2,4 +2,5 @@
 // with phase barriers (one translation unit per stage and budget).
 #include "rd_df64_kernels.cuh"
 
-RD_DF64_INSTANTIATE(1, 128)
+RD_DF64_INSTANTIATE(1, 128, false)
+RD_DF64_INSTANTIATE(1, 128, true)

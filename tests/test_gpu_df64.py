@@ -140,9 +140,10 @@ def test_df64_full_size_4096_khi_first_steps(rd):
 
 
 def test_df64_kernel_variants_are_bitwise_equal(rd):
-    """The DF64 triangle-kernel variants (128 and 168 registers, without and with
-    block barriers between phases) and every block size run the same arithmetic:
-    bitwise equal states, including a ragged last block."""
+    """The DF64 triangle-kernel variants (128 registers without and with block
+    barriers between phases, 96 and 80 with barriers), every block size and
+    different shapes per stage run the same arithmetic: bitwise equal states,
+    including a ragged last block."""
     mesh = inputs.periodic_grid(45, 37, Lx=1.0, Ly=37 / 45, relabel_seed=6)
     W0 = inputs.khi_state(mesh)
     m = rd.Mesh(mesh)
@@ -161,3 +162,11 @@ def test_df64_kernel_variants_are_bitwise_equal(rd):
                 if key not in ref:
                     ref[key] = W
                 assert np.array_equal(W, ref[key]), (occ, tb, scheme)
+    for (tb1, o1), (tb2, o2) in (((256, 5), (128, 4)), ((64, 2), (192, 3))):
+        s = rd.State(m, W0, scheme="B2", precision="df64")
+        s.set_stage_shapes(1, tb1, o1)
+        s.set_stage_shapes(2, tb2, o2)
+        assert s.stage_shapes(1) == (tb1, o1) and s.stage_shapes(2) == (tb2, o2)
+        s.run(6)
+        assert np.array_equal(s.get(), ref[("B2",)]), (tb1, o1, tb2, o2)
+        s.close()
