@@ -133,7 +133,13 @@ def parse():
     ap.add_argument("--tiling", default="auto",
                     help="tiled step: 'auto' (the autotuner's choice), 'none', or TRIANGLESxTHREADS, e.g. 512x128 "
                          "(suffix g: geometry staged in shared memory, e.g. 512x128g)")
+    ap.add_argument("--stage-shapes", default=None,
+                    help="triangle block and DF64 kernel variant of each stage instead of the autotuner's, "
+                         "e.g. 256:5,128:4 (stage 1, stage 2; rd_state_set_stage_shapes)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-rollout companion measurement")
+    ap.add_argument("--adjoint-only", default=None, metavar="N,STEPS,CKPT",
+                    help="run only the adjoint measurement on an N x N mesh with STEPS steps and checkpoints every "
+                         "CKPT steps (e.g. 320,8,4 for a profile of the reverse kernels) and print its JSON")
     ap.add_argument("--no-meshgen", action="store_true", help="skip the mesh-generation companion measurement")
     ap.add_argument("--multi", choices=["partition", "replicas"], default="partition",
                     help="with N > 1 ranks: one mesh split into N vertex parts with NCCL ghost exchange "
@@ -283,10 +289,14 @@ def ncu_traffic(workload, precision, kernel, nt):
 
 
 def run_state_timing(binding, mesh_dev, W0, scheme, precision, steps, warmup, ws, clocks=None, autotune=True,
-                     tiling="auto"):
+                     tiling="auto", stage_shapes=None):
     import torch
     s = binding.State(mesh_dev, W0, scheme=scheme, precision=precision)
     s.shapes = s.autotune() if autotune else None
+    if stage_shapes:
+        for k, spec in enumerate(stage_shapes.split(","), start=1):
+            tb, var = (int(x) for x in spec.split(":"))
+            s.set_stage_shapes(k, tb, var)
     if tiling == "none":
         s.set_tiling(0)
     elif tiling != "auto":
@@ -351,7 +361,8 @@ def ours(args, ws, rank, local):
     clocks = ClockSampler(local)
     s, ms_total, per_kernel, launches = run_state_timing(binding, m, W0, scheme, args.precision,
                                                          args.steps, args.warmup, ws, clocks,
-                                                         autotune=not args.no_autotune, tiling=args.tiling)
+                                                         autotune=not args.no_autotune, tiling=args.tiling,
+                                                         stage_shapes=args.stage_shapes)
     clk = clocks.result
     shapes = s.shapes
     ms_step = max_over_ranks(ms_total / args.steps, ws)
@@ -862,6 +873,9 @@ def main():
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         line = reference(args, ws, rank)
+    elif args.adjoint_only:
+        n, steps, ckpt = (int(x) for x in args.adjoint_only.split(","))
+        line = adjoint_measure(args, ws, n_steps=steps, ckpt_every=ckpt, N=n)
     else:
         line = ours(args, ws, rank, local)
     if rank == 0 and line is not None:

@@ -506,7 +506,9 @@ int rd_batch_get_dt(const rd_batch *b, double *dt_out);
 /* Simulation time and step count of each mesh ([n_mesh] each, nullable). */
 int rd_batch_get_time(const rd_batch *b, double *t_out, int64_t *steps_out);
 int rd_batch_sizes(const rd_batch *b, int64_t *n_vertex, int64_t *n_tri);
-/* Launch-shape autotuner of a batch (as rd_state_autotune). */
+/* Launch-shape autotuner of a batch (as rd_state_autotune: triangle block and
+ * RD_DF64 kernel variant per stage, then the vertex block; tri_block returns
+ * stage 1's). */
 int rd_batch_autotune(rd_batch *b, int32_t *tri_block, int32_t *vtx_block);
 /* As rd_state_profile, for a batch (the steps advance the batch). */
 int rd_batch_profile(rd_batch *b, int32_t n_steps, double *ms_per_launch);

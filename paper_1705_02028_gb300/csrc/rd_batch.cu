@@ -33,9 +33,9 @@ struct rd_batch {
   DevBuf tri, ptr, ent, vmesh, tmesh, geo[6];
   DevBuf W[2], Z[2], spd[2], Ws, Zs, R1, share, rec, cfl, ctl, mmin, dtm, tm, stepsm, stage;
   DevBuf geo_df[4], dWdf;  // RD_DF64: double-float geometry, W* - W^n of every vertex
-  int df_variant = 2;          // RD_DF64 triangle-kernel variant (autotuned)
+  int df_variant = 2, df_variant2 = 2;  // RD_DF64 triangle-kernel variant of stage 1 / 2 (autotuned)
   long long launched = 0;
-  int tri_block = TRI_BLOCK, vtx_block = VTX_BLOCK;
+  int tri_block = TRI_BLOCK, tri_block2 = TRI_BLOCK, vtx_block = VTX_BLOCK;  // tri_block: stage 1
   cudaGraphExec_t graph = nullptr;
   int32_t graph_steps = -1;
   int graph_parity = -1;
@@ -53,8 +53,8 @@ template <class T>
 int batch_step(rd_batch* b, int a, cudaEvent_t* ev, bool commit) {
   const int nt = (int)b->nt, nv = (int)b->nv, c = 1 - a;
   cudaStream_t st = b->stream;
-  const int TB = b->tri_block, VB = b->vtx_block;
-  unsigned gt = nblk(nt, TB), gv = nblk(nv, VB);
+  const int TB = b->tri_block, TB2 = b->tri_block2, VB = b->vtx_block;
+  unsigned gt = nblk(nt, TB), gt2 = nblk(nt, TB2), gv = nblk(nv, VB);
   DevGeo<T> g{(const T*)b->geo[0].p, (const T*)b->geo[1].p, (const T*)b->geo[2].p, (const T*)b->geo[3].p,
               (const T*)b->geo[4].p};
   const T* V = (const T*)b->geo[5].p;
@@ -136,16 +136,17 @@ int batch_step(rd_batch* b, int a, cudaEvent_t* ev, bool commit) {
     if (df) {
       x.Z = (const double*)b->Zs.p;
       x.dw = (const float2*)b->dWdf.p;
-      CK(launch_tri_stage2_df(b->p, x, *reinterpret_cast<const BlendArgs<double>*>(&ba), gt, TB, st));
+      x.variant = b->df_variant2;
+      CK(launch_tri_stage2_df(b->p, x, *reinterpret_cast<const BlendArgs<double>*>(&ba), gt2, TB2, st));
     } else if (b->p.scheme == RD_LDA2)
-      k_tri_stage2<T, RD_LDA2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)b->Zs.p, (const T*)b->W[a].p,
+      k_tri_stage2<T, RD_LDA2><<<gt2, TB2, 0, st>>>(nt, nv, tri, g, (const T*)b->Zs.p, (const T*)b->W[a].p,
                                                   (const T*)b->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl, dtm, tm,
                                                   ba);
     else if (b->p.scheme == RD_B2 && b->p.lumping == RD_LUMP_GLOBAL)
-      k_tri_stage2<T, RD_B2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)b->Zs.p, (const T*)b->W[a].p,
+      k_tri_stage2<T, RD_B2><<<gt2, TB2, 0, st>>>(nt, nv, tri, g, (const T*)b->Zs.p, (const T*)b->W[a].p,
                                                 (const T*)b->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl, dtm, tm);
     else
-      k_tri_stage2<T, RD_BMAX2><<<gt, TB, 0, st>>>(nt, nv, tri, g, (const T*)b->Zs.p, (const T*)b->W[a].p,
+      k_tri_stage2<T, RD_BMAX2><<<gt2, TB2, 0, st>>>(nt, nv, tri, g, (const T*)b->Zs.p, (const T*)b->W[a].p,
                                                    (const T*)b->Ws.p, rec, Gas<T>::of(gamma), eps, share, ctl, dtm,
                                                    tm, ba);
     mark(4);
@@ -447,36 +448,45 @@ extern "C" int rd_batch_autotune(rd_batch* b, int32_t* tri_block, int32_t* vtx_b
   const int vtx_c[] = {128, 256, 512};
   cudaEvent_t ev[7];
   for (auto& e : ev) cudaEventCreate(&e);
-  auto time_step = [&](int tb, int vb, float& ms) -> int {
-    b->tri_block = tb;
-    b->vtx_block = vb;
+  // one untimed and one timed step: ms the whole step, ms1 / ms2 the stage-1 /
+  // stage-2 triangle kernels (events 0-1 and 3-4)
+  auto time_step = [&](float& ms, float& ms1, float& ms2) -> int {
     k_batch_begin<<<1, 256, 0, b->stream>>>((DevCtl*)b->ctl.p, b->n_mesh, (unsigned long long*)b->mmin.p);
     CK(batch_step_any(b, a, nullptr, false));  // warm
     k_batch_begin<<<1, 256, 0, b->stream>>>((DevCtl*)b->ctl.p, b->n_mesh, (unsigned long long*)b->mmin.p);
     CK(batch_step_any(b, a, ev, false));
     CU(cudaStreamSynchronize(b->stream));
     CU(cudaEventElapsedTime(&ms, ev[0], ev[6]));
+    CU(cudaEventElapsedTime(&ms1, ev[0], ev[1]));
+    CU(cudaEventElapsedTime(&ms2, ev[3], ev[4]));
     return RD_OK;
   };
-  int best_t = TRI_BLOCK, best_v = VTX_BLOCK, best_o = b->df_variant, rc = RD_OK;
-  float best = 1e30f, ms = 0.f;
-  // RD_DF64: the triangle kernels at 128 and 168 registers, without and with block barriers between phases
+  int best_t = TRI_BLOCK, best_t2 = TRI_BLOCK, best_v = VTX_BLOCK, rc = RD_OK;
+  int best_o = b->df_variant, best_o2 = b->df_variant2;
+  float best = 1e30f, best1 = 1e30f, best2 = 1e30f, ms = 0.f, ms1 = 0.f, ms2 = 0.f;
+  // triangle block size (and for RD_DF64 the kernel variant) per stage, from each
+  // stage's own kernel time
   const int o0 = b->p.precision == RD_DF64 ? 2 : b->df_variant, o1 = b->p.precision == RD_DF64 ? 5 : b->df_variant;
+  b->vtx_block = VTX_BLOCK;
   for (int o = o0; o <= o1 && rc == RD_OK; ++o) {
-    b->df_variant = o;
+    b->df_variant = b->df_variant2 = o;
     for (int tb : tri_c) {
-      if ((rc = time_step(tb, VTX_BLOCK, ms)) != RD_OK) break;
-      if (ms < best) { best = ms; best_t = tb; best_o = o; }
+      b->tri_block = b->tri_block2 = tb;
+      if ((rc = time_step(ms, ms1, ms2)) != RD_OK) break;
+      if (ms1 < best1) { best1 = ms1; best_t = tb; best_o = o; }
+      if (ms2 < best2) { best2 = ms2; best_t2 = tb; best_o2 = o; }
     }
   }
   b->df_variant = best_o;
-  best = 1e30f;
+  b->df_variant2 = best_o2;
+  b->tri_block = best_t;
+  b->tri_block2 = best_t2;
   for (int vb : vtx_c) {
-    if (rc != RD_OK || (rc = time_step(best_t, vb, ms)) != RD_OK) break;
+    b->vtx_block = vb;
+    if (rc != RD_OK || (rc = time_step(ms, ms1, ms2)) != RD_OK) break;
     if (ms < best) { best = ms; best_v = vb; }
   }
   for (auto& e : ev) cudaEventDestroy(e);
-  b->tri_block = best_t;
   b->vtx_block = best_v;
   destroy_graph(b);
   if (tri_block) *tri_block = best_t;
