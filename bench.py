@@ -270,17 +270,19 @@ def tiling_info(t, flags=0):
 TRAFFIC_CAPTURE = {"khi4096_B2": "khi2048_B2", "khi4096j_B2": "khi2048j_B2"}
 
 
-def ncu_traffic(workload, precision, kernel, nt):
+def ncu_traffic(workload, precision, kernel, nt, variant=None):
     """DRAM bytes per launch of a kernel from the committed ncu summary, scaled to nt
     triangles, with the workload it was captured on; None when missing or taken on a
-    different kernel source."""
+    different kernel source.  DF64 kernels are looked up by their variant too (the
+    register budgets spill, and spills change the traffic)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         d = json.load(open(path))
     except Exception:
         return None
-    cap = workload if f"{workload}:{precision}:{kernel}" in d else TRAFFIC_CAPTURE.get(workload, workload)
-    e = d.get(f"{cap}:{precision}:{kernel}")
+    name = f"{kernel}:v{variant}" if variant is not None else kernel
+    cap = workload if f"{workload}:{precision}:{name}" in d else TRAFFIC_CAPTURE.get(workload, workload)
+    e = d.get(f"{cap}:{precision}:{name}")
     if not e or e.get("source_hash") != kernel_source_hash(precision):
         return None
     return {"bytes_per_launch": float(e["dram_bytes_per_triangle"]) * nt,
@@ -394,7 +396,8 @@ def ours(args, ws, rank, local):
             roof["note"] = ("FP64-equivalent counted flops against the FP64 FMA peak; the per-triangle algebra "
                             "runs in double-float on the FP32 pipe, so frac can exceed 1")
             roof["measured_fp32_fma_peak_tflops"] = binding.probe_fma_peak("fp32") / 1e12
-        tr = ncu_traffic(args.workload, args.precision, dom, nt)
+        var = s.sshapes[f"stage{stage}"]["df_variant"] if args.precision == "df64" else None
+        tr = ncu_traffic(args.workload, args.precision, dom, nt, var)
         roof["traffic"] = tr["bytes_per_launch"] if tr else None
         roof["traffic_source"] = tr
     else:
@@ -495,7 +498,8 @@ def ours(args, ws, rank, local):
                         "vs_fp64_step": ms_step / msdf,
                         "launch_shapes": {"vtx_block": sdf.launch_shapes()[1], "per_stage": sdf.sshapes},
                         "dominant_kernel": ddf,
-                        "traffic_source": ncu_traffic(args.workload, "df64", ddf, nt),
+                        "traffic_source": ncu_traffic(args.workload, "df64", ddf, nt,
+                                                      sdf.sshapes[f"stage{stage_df}"]["df_variant"]),
                         "counted_fp64_equivalent_tflops": eq / 1e12 if eq else None,
                         "vs_measured_fp64_fma_peak": eq / fp64_peak if eq else None,
                         "measured_fp32_fma_peak_tflops": fp32_peak / 1e12,
