@@ -2,7 +2,7 @@
 // CUDA kernels run, compiled for the CPU), for the CPU test that holds them to
 // the oracle's per-triangle shares without a GPU.  Scheme codes + 16 select the
 // double-float bodies of the RD_DF64 kernels (Zbar, Z_i - Zbar and W*_i - W^n_i
-// formed in double, the rest in double-float), as rd_df64.cu calls them.
+// formed in double, the rest in double-float), as rd_df64_kernels.cuh calls them.
 //
 // Input (binary): nv, nt, Lx, Ly, has_shift, xy, tri, shift as in
 // tile_plan_check.cpp, then gamma, eps, dt (double), scheme (int32: 0 N1,
