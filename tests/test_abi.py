@@ -80,6 +80,11 @@ def test_null_and_parameter_checks(lib):
     assert lib.rd_step(None, None) == binding.RD_EINVAL
     assert lib.rd_run(None, 3, 0.0, None) == binding.RD_EINVAL
     assert lib.rd_batch_run(None, 3) != binding.RD_OK
+    # launch shapes: a null state is rejected before any range check or device work
+    assert lib.rd_state_launch_shapes(None, None, None, None) == binding.RD_EINVAL
+    assert lib.rd_state_set_launch_shapes(None, 128, 256, 2) == binding.RD_EINVAL
+    assert lib.rd_state_stage_shapes(None, 1, None, None) == binding.RD_EINVAL
+    assert lib.rd_state_set_stage_shapes(None, 2, 128, 4) == binding.RD_EINVAL
     assert lib.rd_set_allocator(binding.ALLOC_FN(lambda a, b, c: None), ctypes.cast(None, binding.FREE_FN),
                                 None) == binding.RD_EINVAL
 

@@ -170,3 +170,9 @@ def test_df64_kernel_variants_are_bitwise_equal(rd):
         s.run(6)
         assert np.array_equal(s.get(), ref[("B2",)]), (tb1, o1, tb2, o2)
         s.close()
+    s = rd.State(m, W0, scheme="B2", precision="df64")
+    for stage, tb, var in ((3, 128, 2), (0, 128, 2), (1, 100, 2), (2, 128, 6), (1, 128, 1)):
+        with pytest.raises(rd.RDError):
+            s.set_stage_shapes(stage, tb, var)
+    assert s.stage_shapes(1) == s.stage_shapes(2)   # unchanged by the rejected calls
+    s.close()
