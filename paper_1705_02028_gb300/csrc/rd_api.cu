@@ -135,6 +135,7 @@ extern "C" int rd_mesh_create(int32_t n_vertex, const double* xy, int32_t n_tri,
   if (st == RD_OK) st = up_int(m->ptr, m->h.csr_ptr);
   if (st == RD_OK) st = up_int(m->ent, m->h.csr_ent);
   if (st == RD_OK) st = up_int(m->vperm, m->h.vperm);
+  if (st == RD_OK) st = up_int(m->vinv, m->h.vinv);
   if (st == RD_OK && cudaStreamSynchronize(m->stream) != cudaSuccess) {
     cudaGetLastError();
     st = RD_ECUDA;
@@ -154,6 +155,7 @@ extern "C" void rd_mesh_destroy(rd_mesh* m) {
   dev_free(m->ptr);
   dev_free(m->ent);
   dev_free(m->vperm);
+  dev_free(m->vinv);
   for (int p = 0; p < 2; ++p)
     for (int k = 0; k < 6; ++k) dev_free(m->geo[p][k]);
   for (int k = 0; k < 4; ++k) dev_free(m->geo_df[k]);
@@ -371,15 +373,34 @@ int read_ctl(const rd_state* s, DevCtl& c) {
 int status_to_rd(int st) { return st ? RD_ENONPHYSICAL : RD_OK; }
 
 // Host (caller order, double) -> device staging -> internal order in T, then Z and |v|+c.
+// Device address of a caller's host array when it is page-locked and mapped
+// into the device's address space (cudaHostAlloc / cudaHostRegister memory, as
+// PyTorch's pinned tensors are), so that the state kernels can read or write it
+// in place over the host link instead of through a staging copy; NULL for
+// pageable memory, which takes the staging copy.
+static const double* mapped_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  return (const double*)a.devicePointer;
+}
+
 template <class T>
 int upload_state(rd_state* s, const double* W, int buf) {
   rd_mesh* m = s->m;
   const int nv = m->h.nv;
   cudaStream_t st = m->stream;
   DevCtl* ctl = (DevCtl*)s->ctl.p;
-  CU(cudaMemcpyAsync(s->stage.p, W, 4 * (size_t)nv * sizeof(double), cudaMemcpyHostToDevice, st));
-  k_permute_in<T><<<nblk(nv, VTX_BLOCK), VTX_BLOCK, 0, st>>>(nv, (const int*)m->vperm.p, (const double*)s->stage.p,
-                                                             (T*)s->W[buf].p, ctl);
+  if (const double* Wd = mapped_host(W)) {  // page-locked caller array: read it in place
+    k_host_in<T><<<nblk(nv, VTX_BLOCK), VTX_BLOCK, 0, st>>>(nv, (const int*)m->vinv.p, Wd, (T*)s->W[buf].p, ctl);
+  } else {
+    CU(cudaMemcpyAsync(s->stage.p, W, 4 * (size_t)nv * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_permute_in<T><<<nblk(nv, VTX_BLOCK), VTX_BLOCK, 0, st>>>(nv, (const int*)m->vperm.p,
+                                                               (const double*)s->stage.p, (T*)s->W[buf].p, ctl);
+  }
   // boundary data for this state: wall geometry in T and the ghosts' initial state
   if (!s->bc_init || s->bc_version != m->bc_version) {
     CK(mesh_wall_geometry<T>(m));
@@ -411,10 +432,15 @@ int download_state(const rd_state* s, int buf, double* W_out) {
   rd_mesh* m = s->m;
   const int nv = m->h.nv;
   cudaStream_t st = m->stream;
-  k_permute_out<T><<<nblk(nv, VTX_BLOCK), VTX_BLOCK, 0, st>>>(nv, (const int*)m->vperm.p, (const T*)s->W[buf].p,
-                                                              (double*)s->stage.p);
-  CU(cudaGetLastError());
-  CU(cudaMemcpyAsync(W_out, s->stage.p, 4 * (size_t)nv * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (double* Wd = const_cast<double*>(mapped_host(W_out))) {  // page-locked caller array: write it in place
+    k_host_out<T><<<nblk(nv, VTX_BLOCK), VTX_BLOCK, 0, st>>>(nv, (const int*)m->vinv.p, (const T*)s->W[buf].p, Wd);
+    CU(cudaGetLastError());
+  } else {
+    k_permute_out<T><<<nblk(nv, VTX_BLOCK), VTX_BLOCK, 0, st>>>(nv, (const int*)m->vperm.p, (const T*)s->W[buf].p,
+                                                                (double*)s->stage.p);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(W_out, s->stage.p, 4 * (size_t)nv * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
   CU(cudaStreamSynchronize(st));
   return RD_OK;
 }

@@ -86,7 +86,7 @@ struct rd_mesh {
   rd::HostMesh h;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  rd::DevBuf tri, ptr, ent, vperm;
+  rd::DevBuf tri, ptr, ent, vperm, vinv;  // vperm: internal -> caller vertex, vinv: caller -> internal
   // geometry per precision (0: double, 1: float): nx, ny, hl, area, lmax, V
   rd::DevBuf geo[2][6];
   bool geo_ready[2] = {false, false};

@@ -1601,6 +1601,39 @@ __global__ void k_permute_in(int nv, const int* __restrict__ vperm, const double
   if (!ok) atomicOr(&ctl->status, ST_NONPHYS_VERTEX);
 }
 
+// Caller order (component-major doubles, page-locked host memory read in place
+// over the host link) -> internal order in T.  Thread j walks the caller's
+// array contiguously, so every host read is coalesced; the writes scatter on
+// the device through vinv (caller -> internal vertex).
+template <class T>
+__global__ void k_host_in(int nv, const int* __restrict__ vinv, const double* __restrict__ src, T* __restrict__ dst,
+                          DevCtl* ctl) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nv) return;
+  const int i = __ldg(vinv + j);
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double x = src[(size_t)k * nv + j];
+    ok = ok && isfinite(x);
+    dst[4 * (size_t)i + k] = (T)x;
+  }
+  if (!ok) atomicOr(&ctl->status, ST_NONPHYS_VERTEX);
+}
+
+// Internal order in T -> caller order in page-locked host memory, written in
+// place with coalesced host writes (the gathers are on the device).
+template <class T>
+__global__ void k_host_out(int nv, const int* __restrict__ vinv, const T* __restrict__ src, double* __restrict__ dst) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nv) return;
+  const int i = __ldg(vinv + j);
+  T w[4];
+  load_vec4(src, i, w);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) dst[(size_t)k * nv + j] = (double)w[k];
+}
+
 template <class T>
 __global__ void k_permute_out(int nv, const int* __restrict__ vperm, const T* __restrict__ src,
                               double* __restrict__ dst) {
