@@ -221,7 +221,12 @@ void rd_meshgen_destroy(rd_meshgen *g);
  * component-major, caller order).  Errors: RD_EINVAL (bad params),
  * RD_ENONPHYSICAL (rho<=0 or p<=0 or non-finite in W), RD_ENOMEM, RD_ECUDA. */
 int rd_state_init(rd_mesh *m, const double *W, const rd_params *p, rd_state **out);
-/* Replace the state by W (host); time and step counters are kept. */
+/* Replace the state by W (host, component-major, caller order); time and step
+ * counters are kept.  A page-locked W (cudaHostAlloc / cudaHostRegister, e.g.
+ * a pinned PyTorch tensor) is read in place by a kernel over the host link; a
+ * pageable W is copied to a device staging buffer first.  Both give the same
+ * state.  The call synchronises.  Errors: RD_ENONPHYSICAL (rho<=0, p<=0 or
+ * non-finite in W), RD_EINVAL, RD_ECUDA. */
 int rd_state_set(rd_state *s, const double *W);
 /* One full time step (both stages for RD_B2 / RD_LDA2).  dt_out (nullable):
  * if non-NULL the call synchronises and returns the step's dt. */
@@ -231,7 +236,9 @@ int rd_step(rd_state *s, double *dt_out);
  * exactly and stops there.  steps_done (nullable) receives the number of
  * steps completed; the call synchronises once at the end. */
 int rd_run(rd_state *s, int32_t n_steps, double t_end, int32_t *steps_done);
-/* Device -> host copy of the current state in caller order. */
+/* Device -> host copy of the current state (component-major, caller order);
+ * a page-locked W_out is written in place by a kernel, a pageable one through
+ * a device staging buffer.  The call synchronises. */
 int rd_get_state(const rd_state *s, double *W_out);
 /* sum_i V_i W_i per component, accumulated in double in a fixed order. */
 int rd_conserved_totals(const rd_state *s, double out[4]);
